@@ -1,0 +1,271 @@
+// TensorACO CPU oracle -- TEST INFRASTRUCTURE ONLY (see oracle.h).
+//
+// The per-iteration ACO path, step by step, in the paper's order:
+//   Sec. 2.1 (Eq. 1)  M_p from M_tau^alpha and eta^beta
+//   Sec. 2.2          T_start, then each ant walks n-1 steps
+//   Sec. 2.4          each step: v = argmax(r (.) p_u) over unvisited cities
+//   Eq. 3             fitness f = closed tour length
+//   Sec. 2.3 (Eq. 2/3) index matrix I, increment A, Delta M_tau = sum of A
+// plus Ant System evaporation before the deposit.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "oracle.h"
+
+extern "C" {
+
+// d_ij = sqrt(dx^2 + dy^2) in fp64 from fp32 coordinates (x_i, y_i) = xy[2i], xy[2i+1].
+void orc_distances(const float* xy, int n, double* D) {
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      double dx = (double)xy[2 * i] - (double)xy[2 * j];
+      double dy = (double)xy[2 * i + 1] - (double)xy[2 * j + 1];
+      D[(size_t)i * n + j] = std::sqrt(dx * dx + dy * dy);
+    }
+  }
+}
+
+// eta^beta (Sec. 2.1): eta_ij = 1 / max(d_ij, 1e-9), raised to the integer beta
+// in fp64, rounded once to fp32.  The diagonal is never a candidate: 0.
+void orc_heuristic(const double* D, int n, int beta, float* H) {
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      if (i == j) {
+        H[(size_t)i * n + j] = 0.0f;
+        continue;
+      }
+      double d = D[(size_t)i * n + j];
+      double eta = 1.0 / (d > 1e-9 ? d : 1e-9);
+      H[(size_t)i * n + j] = (float)orc_powi_f64(eta, beta);
+    }
+  }
+}
+
+// M_p (Eq. 1) without row normalisation: X_ij = fl32(tau_ij^alpha * eta_ij^beta);
+// under AdaIR X_ij <- X_ij^(1/gamma); then stored at the chosen precision.
+// FP16 storage divides row i by 2^e_i, e_i = clamp(floor(log2(max_j X_ij)) - 14,
+// -126, 113) (0 for an all-zero row), so that the row maximum lies in [2^14, 2^15).
+void orc_build_P(const float* tau, const float* H, int n, int alpha, float inv_gamma,
+                 int prec, float* P_val, uint16_t* P_bits, int32_t* row_exp) {
+  std::vector<float> X((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    float rowmax = 0.0f;
+    for (int j = 0; j < n; ++j) {
+      float x = 0.0f;
+      if (j != i) {
+        x = orc_powi_f32(tau[(size_t)i * n + j], alpha) * H[(size_t)i * n + j];
+        if (inv_gamma != 1.0f) x = orc_pow_own(x, inv_gamma);
+      }
+      X[j] = x;
+      if (x > rowmax) rowmax = x;
+    }
+    int e = 0;
+    if (prec == ORC_FP16 && rowmax > 0.0f) {
+      uint32_t b;
+      std::memcpy(&b, &rowmax, 4);
+      int ef = (int)((b >> 23) & 0xFF);
+      int fl2 = (ef == 0) ? -127 : ef - 127;
+      e = fl2 - 14;
+      if (e < -126) e = -126;
+      if (e > 113) e = 113;
+    }
+    if (row_exp) row_exp[i] = e;
+    // 2^-e as an exact fp32 power of two (-e in [-113, 126])
+    uint32_t sb = (uint32_t)(127 - e) << 23;
+    float scale;
+    std::memcpy(&scale, &sb, 4);
+    for (int j = 0; j < n; ++j) {
+      size_t idx = (size_t)i * n + j;
+      if (prec == ORC_FP32) {
+        P_val[idx] = X[j];
+        if (P_bits) P_bits[idx] = 0;
+      } else if (prec == ORC_BF16) {
+        uint16_t h = orc_to_bf16(X[j]);
+        P_val[idx] = orc_from_bf16(h);
+        if (P_bits) P_bits[idx] = h;
+      } else {
+        uint16_t h = orc_to_fp16(X[j] * scale);
+        P_val[idx] = orc_from_fp16(h);
+        if (P_bits) P_bits[idx] = h;
+      }
+    }
+  }
+}
+
+// One IR selection (Sec. 2.4): v = argmax over unvisited j of r_j * p_j with
+// r_j the Philox deviate of (it, k, t, j).  Ties go to the lowest j.
+int32_t orc_select(const float* row, const uint8_t* visited, int n, uint64_t seed,
+                   uint32_t it, uint32_t k, uint32_t t) {
+  int32_t best_j = -1;
+  float best = 0.0f;
+  for (int j = 0; j < n; ++j) {
+    if (visited[j]) continue;
+    float r = orc_uniform(orc_draw(seed, it, k, t, (uint32_t)j));
+    float score = r * row[j];
+    if (best_j < 0 || score > best || (score == best && j < best_j)) {
+      best = score;
+      best_j = j;
+    }
+  }
+  return best_j;
+}
+
+// The literal AdaIR step of Eq. 4 in fp64: argmax over unvisited j of r_j^gamma * p_j.
+int32_t orc_select_literal_adair(const float* row, const uint8_t* visited, int n,
+                                 uint64_t seed, uint32_t it, uint32_t k, uint32_t t,
+                                 double gamma) {
+  int32_t best_j = -1;
+  double best = 0.0;
+  for (int j = 0; j < n; ++j) {
+    if (visited[j]) continue;
+    double r = (double)orc_uniform(orc_draw(seed, it, k, t, (uint32_t)j));
+    double score = std::pow(r, gamma) * (double)row[j];
+    if (best_j < 0 || score > best || (score == best && j < best_j)) {
+      best = score;
+      best_j = j;
+    }
+  }
+  return best_j;
+}
+
+// Sec. 2.2: ant k starts at T_start[k] and takes n-1 IR steps over M_p.
+static void construct_one(const float* P_val, int n, uint64_t seed, uint32_t it, int k,
+                          int32_t* tour) {
+  std::vector<uint8_t> visited((size_t)n, 0);
+  int32_t cur = orc_start_city(seed, it, (uint32_t)k, n);
+  tour[0] = cur;
+  visited[cur] = 1;
+  for (int t = 1; t < n; ++t) {
+    int32_t v = orc_select(P_val + (size_t)cur * n, visited.data(), n, seed, it,
+                           (uint32_t)k, (uint32_t)t);
+    tour[t] = v;
+    visited[v] = 1;
+    cur = v;
+  }
+}
+
+void orc_construct(const float* P_val, int n, uint64_t seed, uint32_t it, int k_begin,
+                   int k_end, int32_t* tours, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int k = k_begin; k < k_end; ++k)
+    construct_one(P_val, n, seed, it, k, tours + (size_t)(k - k_begin) * n);
+  (void)nthreads;
+}
+
+// f(s) (Eq. 3): closed tour length, sum over t = 0..n-1 of d(p_t, p_{t+1 mod n}),
+// accumulated in fp64 in that order.
+void orc_tour_lengths(const double* D, int n, const int32_t* tours, int m, double* L) {
+  for (int k = 0; k < m; ++k) {
+    const int32_t* p = tours + (size_t)k * n;
+    double s = 0.0;
+    for (int t = 0; t < n; ++t) {
+      int32_t a = p[t], b = p[(t + 1) % n];
+      s = s + D[(size_t)a * n + b];
+    }
+    L[k] = s;
+  }
+}
+
+// Eq. 2: the path and its one-step cyclic shift side by side, row t = (p_t, p_{t-1}).
+void orc_index_matrix(const int32_t* tour, int n, int32_t* I) {
+  for (int t = 0; t < n; ++t) {
+    I[2 * t] = tour[t];
+    I[2 * t + 1] = tour[(t + n - 1) % n];
+  }
+}
+
+// Evaporation then deposit (Sec. 2.3, Eq. 3 with weight Q / f):
+//   A^(k)_ij = Q / L_k if (i,j) or (j,i) is a row of I^(k), else 0;
+//   Delta = sum_k A^(k) in fp64, ants in ascending order;
+//   tau_ij <- fl32( fl64((1 - rho) * tau_ij) + Delta_ij ).
+void orc_deposit(float* tau, int n, const int32_t* tours, const double* L, int m,
+                 float rho, float Q) {
+  std::vector<double> delta((size_t)n * n, 0.0);
+  std::vector<int32_t> I((size_t)2 * n);
+  for (int k = 0; k < m; ++k) {
+    double c = (double)Q / L[k];
+    orc_index_matrix(tours + (size_t)k * n, n, I.data());
+    for (int t = 0; t < n; ++t) {
+      int32_t a = I[2 * t], b = I[2 * t + 1];
+      delta[(size_t)a * n + b] = delta[(size_t)a * n + b] + c;
+      delta[(size_t)b * n + a] = delta[(size_t)b * n + a] + c;
+    }
+  }
+  double keep = 1.0 - (double)rho;
+  for (size_t e = 0; e < (size_t)n * n; ++e) {
+    double v = keep * (double)tau[e];
+    tau[e] = (float)(v + delta[e]);
+  }
+}
+
+void orc_deposit_fp32_order(float* tau, int n, const int32_t* tours, const double* L,
+                            int m, float rho, float Q, const int64_t* perm) {
+  double keep = 1.0 - (double)rho;
+  for (size_t e = 0; e < (size_t)n * n; ++e) tau[e] = (float)(keep * (double)tau[e]);
+  int64_t total = (int64_t)2 * m * n;
+  for (int64_t q = 0; q < total; ++q) {
+    int64_t id = perm ? perm[q] : q;
+    int64_t k = id / (2 * (int64_t)n);
+    int64_t rest = id % (2 * (int64_t)n);
+    int64_t t = rest / 2;
+    int dir = (int)(rest % 2);
+    const int32_t* p = tours + (size_t)k * n;
+    int32_t a = p[t], b = p[(t + n - 1) % n];
+    if (dir) {
+      int32_t tmp = a;
+      a = b;
+      b = tmp;
+    }
+    float c = (float)((double)Q / L[k]);
+    tau[(size_t)a * n + b] = tau[(size_t)a * n + b] + c;
+  }
+}
+
+void orc_init_tau(float* tau, int n, float tau0) {
+  for (size_t e = 0; e < (size_t)n * n; ++e) tau[e] = tau0;
+}
+
+// Iterations it0 .. it0+iters-1 of the whole path.  The iteration best is the
+// shortest tour (lowest ant index on ties); the global best is replaced only
+// by a strictly shorter tour.
+void orc_run(const orc_params* prm, const double* D, const float* H, float* tau,
+             uint32_t it0, int iters, int32_t* best_tour, double* best_len,
+             int32_t* last_tours, double* last_L, int nthreads) {
+  const int n = prm->n, m = prm->m;
+  std::vector<float> P((size_t)n * n);
+  std::vector<int32_t> tours((size_t)m * n);
+  std::vector<double> L((size_t)m);
+  for (int q = 0; q < iters; ++q) {
+    uint32_t it = it0 + (uint32_t)q;
+    float inv_gamma = 1.0f;
+    if (prm->adair) {
+      float g = orc_gamma((int)it, prm->gamma_T, prm->gamma_max, prm->gamma_min);
+      inv_gamma = orc_inv_gamma(g);
+    }
+    orc_build_P(tau, H, n, prm->alpha, inv_gamma, prm->prec, P.data(), nullptr, nullptr);
+    orc_construct(P.data(), n, prm->seed, it, 0, m, tours.data(), nthreads);
+    orc_tour_lengths(D, n, tours.data(), m, L.data());
+    int kb = 0;
+    for (int k = 1; k < m; ++k)
+      if (L[k] < L[kb]) kb = k;
+    if (L[kb] < *best_len) {
+      *best_len = L[kb];
+      std::memcpy(best_tour, tours.data() + (size_t)kb * n, sizeof(int32_t) * n);
+    }
+    orc_deposit(tau, n, tours.data(), L.data(), m, prm->rho, prm->Q);
+  }
+  if (last_tours) std::memcpy(last_tours, tours.data(), sizeof(int32_t) * tours.size());
+  if (last_L) std::memcpy(last_L, L.data(), sizeof(double) * L.size());
+}
+
+}  // extern "C"
