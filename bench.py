@@ -1,0 +1,441 @@
+#!/usr/bin/env python3
+"""TensorACO benchmark: one JSON line per run.
+
+A step is one whole ACO iteration on the GPU -- build M_p, construct all m
+tours, tour lengths + best, evaporate + deposit -- on a synthetic instance
+shaped like the paper's workloads.  Default workload: 5000 clustered cities
+(50 Gaussian clusters, sigma 0.02), m = 1024 ants, alpha 1, beta 2, rho 0.1,
+fp32 M_p, independent roulette, deterministic deposit.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 (under torchrun): every rank solves its own instance (replicas; weak
+scaling), the time is the max over ranks, value sums the ranks' ant-steps.
+--impl reference times the CPU oracle (the plain C++ restatement of the
+method) on the host cores, on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2404_04895_gb300 import instances  # noqa: E402
+
+METRIC = "ant-steps/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="n5000_clustered", choices=sorted(instances.WORKLOADS))
+    ap.add_argument("--prec", default=None, choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--no-variants", action="store_true", help="skip the bf16/fp16 comparison")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gap-seeds", type=int, default=5)
+    return ap.parse_args()
+
+
+def workload(args):
+    w = dict(instances.WORKLOADS[args.workload])
+    if args.prec:
+        w["prec"] = args.prec
+    return w
+
+
+def solver_kwargs(w, seed):
+    kw = dict(m=w["m"], alpha=w["alpha"], beta=w["beta"], rho=w["rho"], Q=w["Q"], seed=seed,
+              prec=w["prec"], roulette="adair" if w["adair"] else "ir")
+    if w["adair"]:
+        kw.update(gamma_max=1.5, gamma_min=0.5, gamma_T=w["iters"])
+    return kw
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def construct_source_hash():
+    h = hashlib.sha256()
+    for f in ("construct.cuh", "shapes.h", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2404_04895_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel_hash, workload_name, prec):
+    """dram bytes per construct launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "construct_dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(f"{workload_name}:{prec}")
+    if not e or e.get("kernel_hash") != kernel_hash:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- distributed
+class Dist:
+    def __init__(self, args):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl" if args.impl == "native" else "gloo"
+            dist.init_process_group(backend)
+            self.dist = dist
+            self.pg = True
+
+    def barrier(self):
+        if self.pg:
+            self.dist.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64,
+                         device="cuda" if self.dist.get_backend() == "nccl" else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def oracle_sample(w, coords, seed, budget_s=10.0, min_ants=None):
+    """Construct tours with the CPU oracle for a sample of the workload's ants
+    at iteration 0 (the dominant step), on all host cores."""
+    import oracle
+    threads = oracle.default_threads()
+    n, m = w["n"], w["m"]
+    D = oracle.distances(coords)
+    H = oracle.heuristic(D, w["beta"])
+    inv = oracle.inv_gamma(oracle.gamma(0, w["iters"], 1.5, 0.5)) if w["adair"] else 1.0
+    prec = {"fp32": oracle.FP32, "bf16": oracle.BF16, "fp16": oracle.FP16}[w["prec"]]
+    P, _, _ = oracle.build_P(oracle.init_tau(n), H, w["alpha"], inv, prec)
+    ants, secs = 0, 0.0
+    batch = min_ants or threads
+    while True:
+        k0 = ants % m
+        k1 = min(m, k0 + batch)
+        t0 = time.perf_counter()
+        oracle.construct(P, seed, 0, k0, k1, threads)
+        secs += time.perf_counter() - t0
+        ants += k1 - k0
+        if secs >= budget_s or ants >= 4 * m:
+            break
+        per_ant = secs / ants
+        batch = max(threads, int(min((budget_s - secs) / per_ant, 4 * m - ants)))
+    return {"value": ants * (n - 1) / secs, "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": f"{ants} ant tours (of m={m}) of iteration 0 on n={n}, {secs:.1f} s"}
+
+
+# ---------------------------------------------------------------- native leg
+def run_native(args, w, dist):
+    import torch
+    from paper_2404_04895_gb300 import binding as B
+
+    torch.cuda.set_device(dist.local)
+    B.lib()
+    coords = instances.coords_for(w)
+    n, m = w["n"], w["m"]
+    seed = w["seed"] + dist.rank
+    st = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed_run(prec, steps, warmup, profile=True):
+        kw = solver_kwargs(dict(w, prec=prec), seed)
+        s = B.Solver(coords, stream=st, **kw)
+        if profile:
+            s.set_profiling(True)
+        s.iterate(warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        total = 0.0
+        kern = np.zeros(5)
+        for q in range(steps):
+            with torch.cuda.stream(st):
+                flush.fill_(q & 0xFF)          # L2 flush, outside the timed region
+                e0.record(st)
+                s.iterate(1)
+                e1.record(st)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            if profile:
+                kern += s.kernel_ms()
+        torch.cuda.synchronize()
+        best = s.best()[1]
+        s.close()
+        return total, kern, best
+
+    tuned = {}
+    for prec in ([w["prec"]] if args.no_variants else ["fp32", "bf16", "fp16"]):
+        tuned[prec] = autotune(B, torch, w, coords, prec, seed)
+    dist.barrier()
+    clk = ClockSampler(dist.local)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk.start()
+    total_ms, kern, best_len = timed_run(w["prec"], args.steps, args.warmup)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = clk.stop()
+    t_max = dist.max(total_ms)
+    ms_per_step = t_max / args.steps
+    ant_steps = m * (n - 1)
+    value = ant_steps * dist.world / (ms_per_step / 1e3)
+
+    # roofline of the construction kernel (the dominant one)
+    bp = 4 if w["prec"] == "fp32" else 2
+    construct_ms = kern[1] / args.steps
+    alg_bytes = m * n * (n - 1) / 2 * bp
+    achieved = alg_bytes / (construct_ms / 1e3) / 1e9
+    peak, peak_src = peaks()
+    khash = construct_source_hash()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                "traffic": traffic_from_profile(khash, args.workload, w["prec"]),
+                "kernel": "construct_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": round(construct_ms, 4), "kernel_source_hash": khash}
+    roofline["construct_shape"] = {"warps_per_ant": tuned[w["prec"]][0][0],
+                                   "chunks_per_lane": tuned[w["prec"]][0][1]}
+    kernel_ms = dict(zip(["build_P", "construct", "tour_length", "best", "deposit"],
+                         [round(x / args.steps, 4) for x in kern]))
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[w["prec"]],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "kind": w["kind"], "n": n, "m": m, "alpha": w["alpha"],
+                   "beta": w["beta"], "rho": w["rho"], "Q": w["Q"],
+                   "roulette": "adair" if w["adair"] else "ir", "deposit": "deterministic",
+                   "P_dtype": w["prec"], "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU",
+                   "iters_per_s": round(1e3 / ms_per_step, 2)},
+        "roofline": roofline,
+        "kernel_ms": kernel_ms,
+        "gpu_launches": args.steps * 5,
+        "clocks": clocks,
+        "best_len_after_steps": best_len,
+    }
+
+    if dist.rank == 0 and not args.no_variants:
+        # BF16 / FP16 M_p against fp32 on the same GPU: throughput and best-length gap
+        variants = {}
+        gaps = {}
+        for prec in ("fp32", "bf16", "fp16"):
+            if prec != w["prec"]:
+                t, kv, _ = timed_run(prec, min(args.steps, 30), 3)
+                steps_v = min(args.steps, 30)
+                cms = kv[1] / steps_v
+                bpv = 4 if prec == "fp32" else 2
+                ach = m * n * (n - 1) / 2 * bpv / (cms / 1e3) / 1e9
+                variants[prec] = {"ms_per_step": round(t / steps_v, 4),
+                                  "value": round(ant_steps / (t / steps_v / 1e3), 1),
+                                  "construct_ms": round(cms, 4), "construct_GBps": round(ach, 1),
+                                  "frac_of_hbm": round(ach / peak, 4)}
+            # best length after the workload's full iteration budget, mean over seeds
+            lens = []
+            for sd in range(args.gap_seeds):
+                s = B.Solver(coords, stream=st, **solver_kwargs(dict(w, prec=prec), sd))
+                s.iterate(w["iters"])
+                lens.append(s.best()[1])
+                s.close()
+            gaps[prec] = float(np.mean(lens))
+        for prec in gaps:
+            if prec != "fp32":
+                variants.setdefault(prec, {})["best_len_gap_vs_fp32"] = round(gaps[prec] / gaps["fp32"] - 1, 5)
+        out["variants"] = variants
+        out["best_len_mean"] = {k: round(v, 6) for k, v in gaps.items()}
+        out["best_len_protocol"] = f"mean over seeds 0..{args.gap_seeds - 1} after {w['iters']} iterations"
+
+    if dist.rank == 0 and not args.no_e2e:
+        out["e2e"] = run_e2e(args, w, coords, seed)
+    if dist.rank == 0 and not args.no_cpu_baseline and dist.world == 1:
+        out["cpu_baseline"] = oracle_sample(w, coords, seed)
+    return out
+
+
+def autotune(B, torch, w, coords, prec, seed):
+    """Pick the construct launch shape on the iteration-0 M_p of the workload
+    (untimed); the library keeps it as the default for (n, m, precision)."""
+    n, m = w["n"], w["m"]
+    ld = B.ld_of(n)
+    H = torch.empty((n, ld), dtype=torch.float32, device="cuda")
+    tau = torch.empty_like(H)
+    P = torch.empty_like(H)
+    xy = torch.from_numpy(np.ascontiguousarray(coords)).cuda()
+    B.op_heuristic(xy, n, w["beta"], None, H, ld)
+    B.op_fill(tau, n, ld, 1.0)
+    inv = B.inv_gamma(B.gamma(0, w["iters"], 1.5, 0.5)) if w["adair"] else 1.0
+    B.op_build_P(tau, H, n, ld, w["alpha"], inv, B.PREC[prec], P)
+    tours = torch.empty((m, n), dtype=torch.int32, device="cuda")
+    shape, ms = B.autotune_construct(P, B.PREC[prec], n, ld, m, seed, tours, reps=2)
+    torch.cuda.synchronize()
+    return shape, ms
+
+
+def run_e2e(args, w, coords, seed):
+    """Same metric through the public C ABI with host buffers: aco_init copies
+    the coordinates in, each step is aco_iterate(1) followed by aco_best()
+    reading the best tour and length back to host memory."""
+    import torch
+    from paper_2404_04895_gb300 import binding as B
+    L = B.lib()
+    n, m = w["n"], w["m"]
+    xy = torch.from_numpy(np.ascontiguousarray(coords)).pin_memory()
+    tour = torch.empty(n, dtype=torch.int32).pin_memory()
+    blen = torch.empty(1, dtype=torch.float64).pin_memory()
+    B.check(L.aco_bind(None, 0, None))
+    B.check(L.aco_set_precision(B.PREC[w["prec"]]))
+    B.check(L.aco_set_variant(B.ADAIR if w["adair"] else B.IR, 1.5, 0.5, w["iters"]))
+    B.check(L.aco_set_deposit(B.DEPOSIT_DET))
+
+    def job(steps):
+        B.check(L.aco_init(xy.data_ptr(), n, m, float(w["alpha"]), float(w["beta"]), w["rho"], w["Q"], seed))
+        for _ in range(steps):
+            B.check(L.aco_iterate(1))
+            B.check(L.aco_best(tour.data_ptr(), blen.data_ptr()))
+        B.check(L.aco_free())
+
+    job(2)  # warm-up: module load, graph instantiation
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    job(args.steps)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    return {"value": round(args.steps * m * (n - 1) / secs, 1), "unit": METRIC,
+            "h2d_bytes_per_step": round(n * 8 / args.steps, 2), "d2h_bytes_per_step": n * 4 + 8,
+            "note": "one job = aco_init (coords host->device, distances, eta^beta) + steps x "
+                    "(aco_iterate(1) + aco_best to host); h2d is the job's coordinates spread over its steps"}
+
+
+# ---------------------------------------------------------------- reference leg
+def run_reference(args, w, dist):
+    coords = instances.coords_for(w)
+    if dist.rank != 0:
+        return None
+    per_step_budget = max(0.5, min(8.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(w, coords, w["seed"], budget_s=per_step_budget * 0.25)
+    tot_ants_steps, tot_s, samples = 0.0, 0.0, []
+    for _ in range(args.steps):
+        r = oracle_sample(w, coords, w["seed"], budget_s=per_step_budget)
+        secs = float(r["sample"].split(", ")[-1].split(" s")[0])
+        tot_s += secs
+        tot_ants_steps += r["value"] * secs
+        samples.append(r)
+    value = tot_ants_steps / tot_s
+    ms_per_step = (w["m"] * (w["n"] - 1)) / value * 1e3
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": METRIC,
+        "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[w["prec"]],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "kind": w["kind"], "n": w["n"], "m": w["m"],
+                   "P_dtype": w["prec"], "roulette": "adair" if w["adair"] else "ir"},
+        "cpu_baseline": {"value": round(value, 1), "unit": METRIC, "cores": samples[0]["cores"],
+                         "kind": "oracle",
+                         "sample": f"each step: ant tours of iteration 0 for ~{per_step_budget:.1f} s; "
+                                   f"ms_per_step extrapolates one full iteration's m*(n-1) ant-steps"},
+        "e2e": {"value": round(value, 1), "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    w = workload(args)
+    dist = Dist(args)
+    try:
+        out = run_reference(args, w, dist) if args.impl == "reference" else run_native(args, w, dist)
+        if dist.rank == 0 and out is not None:
+            print(json.dumps(out), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,252 @@
+/*
+ * tensoraco.h -- C ABI of the GB300 (sm_103a) TensorACO library.
+ *
+ * The per-iteration path of "Tensorized Ant Colony Optimization for GPU
+ * Acceleration" (Yang, Jiang, Cheng, GECCO'24 Companion) for the Euclidean
+ * TSP, every step a hand-written CUDA kernel:
+ *   (a) M_p = tau^alpha * eta^beta, eta = 1/d               Sec. 2.1, Eq. 1
+ *   (b) all m tours by independent roulette (IR) or AdaIR    Sec. 2.2, 2.4, Eq. 4
+ *   (c) tour lengths f(s)                                    Eq. 3
+ *   (d) evaporate, then deposit Q/f(s) by index mapping      Sec. 2.3, Eq. 2-3
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status (ACO_OK = 0, negative on error)
+ *     and never aborts; aco_last_error() returns a text for the last error of
+ *     the calling thread.
+ *   - Sizes are element counts.  n = cities (3 <= n <= ACO_MAX_N),
+ *     m = ants (1 <= m <= ACO_MAX_M).
+ *   - Arguments named *_host are host pointers, *_dev device pointers.
+ *   - Matrices are row-major.  n x n fp32/bf16/fp16 matrices on the device
+ *     have a leading dimension `ld` (elements): ld >= n, ld % 8 == 0, base
+ *     address 16-byte aligned.  Padding columns j >= n are never read as
+ *     candidates.  Distance matrices are fp64 n x n with leading dimension n.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device-
+ *     pointer calls are asynchronous on that stream; host-pointer calls
+ *     synchronise it before returning.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed
+ *     (low word, high word), counter (j>>2, t, k, it), word j&3 for candidate
+ *     j at step t of ant k in iteration it; deviate ((x>>8)|1) * 2^-24.
+ *     Start city of ant k: (x*n)>>32, x = word 0 of counter (0, 0, k, it).
+ *   - alpha and beta must be integers in [0, 8] (integer powers by repeated
+ *     multiplication keep every result reproducible bit for bit).
+ */
+#ifndef TENSORACO_H
+#define TENSORACO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ACO_OK 0
+#define ACO_ERR_ARG (-1)         /* invalid argument */
+#define ACO_ERR_OOM (-2)         /* device allocation failed / workspace too small */
+#define ACO_ERR_CUDA (-3)        /* a CUDA runtime call or kernel failed */
+#define ACO_ERR_STATE (-4)       /* call out of order (e.g. best before any iteration) */
+#define ACO_ERR_UNSUPPORTED (-5) /* valid request this build does not support */
+#define ACO_ERR_TIMEOUT (-6)     /* a bounded device-side wait ran out */
+
+#define ACO_MAX_N 65536
+#define ACO_MAX_M 1048576
+
+enum { ACO_FP32 = 0, ACO_BF16 = 1, ACO_FP16 = 2 };           /* storage of M_p */
+enum { ACO_IR = 0, ACO_ADAIR = 1 };                          /* selection, Sec. 2.4 */
+enum { ACO_DEPOSIT_DET = 0, ACO_DEPOSIT_ATOMIC = 1 };        /* Delta M_tau summation */
+
+/* Text of the calling thread's last error ("" if none). Never NULL. */
+const char* aco_last_error(void);
+
+/* ======================================================================
+ * Single-instance API.  One global solver, not thread-safe; the handle API
+ * below gives independent solvers.
+ * ==================================================================== */
+
+/* Create the global solver on the current device: copies coords_host
+ * (n x 2 fp32, (x, y) per city) to the device, builds the fp64 distance
+ * matrix and eta^beta, sets tau = 1 (Sec. 2.1).  rho in [0,1], Q >= 0,
+ * alpha/beta integers in [0,8].  Replaces a previous global solver.
+ * Uses the workspace given to aco_bind() when one is bound, else allocates. */
+int aco_init(const float* coords_host, int n, int m, float alpha, float beta, float rho,
+             float Q, uint64_t seed);
+
+/* Selection mechanism (Sec. 2.4).  ACO_IR ignores the gammas.  ACO_ADAIR
+ * anneals gamma from gamma_max to gamma_min over T iterations by a cosine
+ * schedule (gamma_t = gmin + (gmax-gmin)/2 (1 + cos(pi t / T)), gmin after T)
+ * and selects argmax(r^gamma p) in the equivalent form argmax(r p^(1/gamma)).
+ * gamma_* in (0, 16], T >= 1.  Takes effect at the next iteration. */
+int aco_set_variant(int roulette, float gamma_max, float gamma_min, int T);
+
+/* Storage precision of M_p: ACO_FP32, ACO_BF16 (RNE), ACO_FP16 (RNE after a
+ * per-row power-of-two scale 2^-e_i placing the row maximum in [2^14, 2^15)).
+ * Scores are always fp32, tau always fp32.  Takes effect at the next iteration. */
+int aco_set_precision(int prec);
+
+/* Deposit summation: ACO_DEPOSIT_DET sums Delta in fp64 in ascending ant
+ * order (reproducible bit for bit); ACO_DEPOSIT_ATOMIC adds fl32(Q/L_k) with
+ * fp32 atomics in hardware order (not reproducible). */
+int aco_set_deposit(int mode);
+
+/* Run k >= 0 iterations (a)-(d).  Iterations are numbered from 0 across calls.
+ * Asynchronous on the bound stream. */
+int aco_iterate(int k);
+
+/* Best tour so far (n city indices into tour_host) and its length.  The best
+ * is replaced only by a strictly shorter tour; within an iteration the lowest
+ * ant index wins ties.  ACO_ERR_STATE before the first iteration. */
+int aco_best(int32_t* tour_host, double* len_host);
+
+/* Copies of the current state to host memory: tau (n x n, dense),
+ * last iteration's tours (m x n) and lengths (m). */
+int aco_get_tau(float* tau_host);
+int aco_get_tours(int32_t* tours_host);
+int aco_get_lengths(double* lengths_host);
+
+/* Release the global solver (and its workspace if the library allocated it). */
+int aco_free(void);
+
+/* Device bytes one solver of (n, m) needs, whatever the precision. */
+int aco_workspace_bytes(int n, int m, int prec, size_t* bytes);
+
+/* Give the next aco_init a caller-owned device workspace (e.g. a torch
+ * tensor) of `bytes` >= aco_workspace_bytes(), 256-byte aligned, and the
+ * stream all its work is issued on.  The caller keeps ownership and must keep
+ * the memory alive until aco_free().  dev_workspace NULL unbinds. */
+int aco_bind(void* dev_workspace, size_t bytes, void* stream);
+
+/* ======================================================================
+ * Handle API: independent solvers (used by the batch and serving layers).
+ * ==================================================================== */
+typedef struct aco_solver aco_solver;
+
+typedef struct {
+  int n, m;
+  int alpha, beta;          /* integers in [0, 8] */
+  float rho, Q, tau0;       /* rho in [0,1], Q >= 0, tau0 > 0 */
+  uint64_t seed;
+  int prec;                 /* ACO_FP32 / ACO_BF16 / ACO_FP16 */
+  int roulette;             /* ACO_IR / ACO_ADAIR */
+  int deposit;              /* ACO_DEPOSIT_DET / ACO_DEPOSIT_ATOMIC */
+  float gamma_max, gamma_min;
+  int gamma_T;
+} aco_params;
+
+/* Fill *p with defaults: alpha 1, beta 2, rho 0.5, Q 1, tau0 1, seed 0, FP32,
+ * IR, deterministic deposit, gamma 1.5 -> 0.5 over 100 iterations. */
+int aco_params_default(aco_params* p);
+
+/* Create a solver for p->n cities given coords_host (n x 2 fp32).  Workspace:
+ * dev_workspace/ws_bytes as for aco_bind (NULL: the library allocates).
+ * stream: the solver's stream (NULL: legacy default stream). */
+int aco_create(aco_solver** out, const float* coords_host, const aco_params* p,
+               void* dev_workspace, size_t ws_bytes, void* stream);
+int aco_destroy(aco_solver* s);
+int aco_solver_iterate(aco_solver* s, int k);
+int aco_solver_best(aco_solver* s, int32_t* tour_host, double* len_host);
+int aco_solver_get_tau(aco_solver* s, float* tau_host);
+int aco_solver_get_tours(aco_solver* s, int32_t* tours_host);
+int aco_solver_get_lengths(aco_solver* s, double* lengths_host);
+/* Device pointers into the solver's state (borrowed, valid until destroy):
+ * tau (fp32, leading dimension *ld), tours (int32 m x n), lengths (fp64 m),
+ * best tour (int32 n), best length (fp64 1). */
+int aco_solver_device_state(aco_solver* s, float** tau, int* ld, int32_t** tours,
+                            double** lengths, int32_t** best_tour, double** best_len);
+/* Iterations completed so far. */
+int aco_solver_iteration(aco_solver* s, uint32_t* it);
+
+/* Kernel timing probes.  When on, the solver records CUDA events around each
+ * kernel of every iteration (inside its CUDA graph as well).  After an
+ * iteration has been issued, aco_solver_kernel_ms() waits for it and writes
+ * the durations in milliseconds of its kernels, in order: build_P, construct,
+ * tour_length, best, deposit (evaporation + deposit for the atomic mode). */
+int aco_solver_set_profiling(aco_solver* s, int on);
+int aco_solver_kernel_ms(aco_solver* s, float* ms5);
+
+/* Choose the construct launch shape for this solver: warps = chunks = 0
+ * restores the default (autotuned if aco_autotune_construct ran for its
+ * n, m and precision). */
+int aco_solver_set_shape(aco_solver* s, int warps, int chunks);
+
+/* ======================================================================
+ * Step-level API on caller-owned device buffers (one kernel family each),
+ * asynchronous on `stream`.  The solvers above are built from these.
+ * ==================================================================== */
+
+/* Sec. 2.1: D_ij = sqrt(dx^2 + dy^2) in fp64 (D_dev n x n, nullable) and
+ * H_ij = fl32(powi_f64(1 / max(D_ij, 1e-9), beta)), H_ii = 0 (H_dev n x ld),
+ * from coords_dev (n x 2 fp32). */
+int aco_op_heuristic(const float* coords_dev, int n, int beta, double* D_dev, float* H_dev,
+                     int ld, void* stream);
+
+/* Fill an n x ld fp32 matrix with `value` (tau initialisation). */
+int aco_op_fill(float* dev, int n, int ld, float value, void* stream);
+
+/* Eq. 1 (unnormalised): X_ij = fl32(powi_f32(tau_ij, alpha) * H_ij), X_ii = 0;
+ * AdaIR (inv_gamma != 1): X_ij <- pow_own(X_ij, inv_gamma); then stored at
+ * `prec` into P_dev (n x ld; 4 bytes per element for ACO_FP32, 2 otherwise).
+ * Padding columns are written as 0. */
+int aco_op_build_P(const float* tau_dev, const float* H_dev, int n, int ld, int alpha,
+                   float inv_gamma, int prec, void* P_dev, void* stream);
+
+/* Sec. 2.2 + 2.4: tours of ants 0..m-1 at iteration `it` over M_p (P_dev,
+ * n x ld at `prec`) into tours_dev (m x n int32).  Each step selects
+ * argmax over unvisited j of fl32(r_j * P[cur, j]), lowest j on ties.
+ * err_dev (nullable, int32) is set non-zero if a kernel-side check failed. */
+int aco_op_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed,
+                     uint32_t it, int32_t* tours_dev, int32_t* err_dev, void* stream);
+
+/* Same, with an explicit launch shape: warps per ant and 16-byte chunks per
+ * lane (32*warps*chunks*(16/elem bytes) >= n).  ACO_ERR_UNSUPPORTED when the
+ * shape is not compiled in.  Used by the autotuner. */
+int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed,
+                           uint32_t it, int32_t* tours_dev, int32_t* err_dev, int warps,
+                           int chunks, void* stream);
+
+/* Eq. 3 and the index mapping of Eq. 2: L_k = sum_t D[p_t][p_{t+1 mod n}] in
+ * fp64 in t order (L_dev, m), c_k = fl64(Q / L_k) (c_dev, m), and for every
+ * city a the neighbours of a in tour k: nbr_dev[(a*m + k)*2 + {0,1}] =
+ * (predecessor, successor) (nbr_dev: n*m*2 int32, nullable). */
+int aco_op_tour_length(const double* D_dev, int n, const int32_t* tours_dev, int m, float Q,
+                       double* L_dev, double* c_dev, int32_t* nbr_dev, void* stream);
+
+/* Iteration best (argmin L, lowest k on ties) merged into the running best:
+ * replaced only if strictly shorter.  best_len_dev starts at +inf. */
+int aco_op_best(const double* L_dev, const int32_t* tours_dev, int n, int m,
+                int32_t* best_tour_dev, double* best_len_dev, void* stream);
+
+/* Sec. 2.3, deterministic: Delta_ab = sum over ants k ascending whose tour
+ * has edge {a,b} of c_k, in fp64; tau_ab <- fl32(fl64((1-rho) tau_ab) + Delta_ab).
+ * Input: nbr/c from aco_op_tour_length.  tau_dev n x ld, updated in place. */
+int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const double* c_dev,
+                   int m, float rho, void* stream);
+
+/* Sec. 2.3, float-atomic: tau <- fl32(fl64(1-rho) tau), then for every
+ * directed tour edge (a,b) of ant k: atomicAdd(tau_ab, fl32(c_k)). */
+int aco_op_deposit_atomic(float* tau_dev, int n, int ld, const int32_t* tours_dev,
+                          const double* c_dev, int m, float rho, void* stream);
+
+/* Autotuner: times every compiled construct shape that covers n on the
+ * given M_p (reps launches each, after one warm-up) and registers the fastest
+ * as the default for (n, m, prec) in this process.  tours_scratch_dev: m x n
+ * int32.  Outputs the chosen shape and its mean time in ms (nullable). */
+int aco_autotune_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed,
+                           int32_t* tours_scratch_dev, int reps, int* warps_out, int* chunks_out,
+                           float* ms_out, void* stream);
+
+/* Test utilities: Philox4x32-10 blocks for count counters (ctr_dev 4*count
+ * u32, out_dev 4*count u32) under key (seed lo, hi); and the device pow_own
+ * used by AdaIR on count fp32 values. */
+int aco_op_philox(const uint32_t* ctr_dev, uint64_t seed, uint32_t* out_dev, int count,
+                  void* stream);
+int aco_op_pow_own(const float* x_dev, float e, float* out_dev, int count, void* stream);
+
+/* Cosine-annealed gamma of iteration it (host, fp64 rounded to fp32) and
+ * fl32(1/gamma); the same values the solvers use. */
+float aco_gamma(int it, int T, float gamma_max, float gamma_min);
+float aco_inv_gamma(float gamma);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TENSORACO_H */

@@ -4,7 +4,7 @@ import math
 
 import numpy as np
 
-from .build import build
+from .build import build as _build_lib
 
 FP32, BF16, FP16 = 0, 1, 2
 
@@ -25,7 +25,7 @@ def _p(a):
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
+        L = C.CDLL(_build_lib())
         v, u32, u64, i32, f32, f64 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32, C.c_float, C.c_double
         sig = {
             "orc_philox4x32_10": (None, [v, v, v]),

@@ -1,0 +1,285 @@
+// Tour construction (Sec. 2.2 + 2.4): every ant walks n-1 independent-roulette
+// steps over the shared transition matrix M_p.
+//
+// Layout of the work (one CTA = one ant, W warps, TPA = 32*W threads):
+//   - Row P[cur] is cut into 16-byte chunks (V = 4 fp32 or 8 bf16/fp16
+//     elements).  Thread g owns chunks c*TPA + g, c = 0..KC-1, for the whole
+//     walk, and keeps the visited bits of its KC*V columns in registers.
+//   - A step copies the thread's not-yet-fully-visited chunks of the row into
+//     shared memory with 16-byte cp.async (coalesced: the warp moves 512
+//     contiguous bytes per chunk index; every copy of the step is in flight
+//     at once, whatever the register budget), waits for its own copies, then
+//     reduces each 4-column group to its largest raw P.  Shared slot of chunk
+//     c*TPA + g is its column-chunk index, so the row copy is dense.
+//   - Exact pruning: a score is fl32(r * p) <= p because r < 1, so a column
+//     whose p is below some candidate's exact score cannot win.  Each thread
+//     first scores its largest group exactly (one Philox4x32-10 block covers
+//     the group's 4 columns); the warp maximum of those scores is the
+//     threshold, and only groups whose raw maximum reaches it are scored.
+//     Skipping a counter-based draw changes no other draw, so the selected
+//     city is exactly argmax over unvisited j of fl32(r_j * p_j), lowest j
+//     on ties -- the same city a full scan selects.
+//   - Warp shuffle argmax, then (W > 1) a shared-memory combine across warps.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+
+namespace aco {
+
+// 16-byte global -> shared copy (L2 only), issued only when `pred` holds.  A
+// predicated instruction keeps all of a step's copies in one basic block.
+__device__ __forceinline__ void cp_async16_pred(void* smem_dst, const void* gmem_src, bool pred) {
+  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t"
+      "@p cp.async.cg.shared.global [%0], [%1], 16;\n\t}" ::"r"(dst),
+      "l"(gmem_src), "r"((int)pred)
+      : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+template <int PREC>
+struct Elem;
+
+template <>
+struct Elem<ACO_FP32> {
+  static constexpr int V = 4;      // elements per 16-byte chunk
+  static constexpr int BYTES = 4;
+  // fp32 bits of the largest element of group g (4 elements) of chunk d;
+  // elements are >= 0, so unsigned order is numeric order.
+  __device__ __forceinline__ static uint32_t group_max_bits(const uint4& d, int) {
+    return max(max(d.x, d.y), max(d.z, d.w));
+  }
+  // the 4 values of group g of a 16-byte chunk
+  __device__ __forceinline__ static float4 group_values(const uint4& d, int) {
+    return make_float4(__uint_as_float(d.x), __uint_as_float(d.y), __uint_as_float(d.z),
+                       __uint_as_float(d.w));
+  }
+};
+
+__device__ __forceinline__ uint32_t vmax_u16x2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t swap_halves(uint32_t a) { return __byte_perm(a, 0, 0x1032); }
+
+template <>
+struct Elem<ACO_BF16> {
+  static constexpr int V = 8;
+  static constexpr int BYTES = 2;
+  __device__ __forceinline__ static uint32_t group_max_bits(const uint4& d, int g) {
+    const uint32_t m = g == 0 ? vmax_u16x2(d.x, d.y) : vmax_u16x2(d.z, d.w);
+    return vmax_u16x2(m, swap_halves(m)) & 0xFFFF0000u;  // bf16 in the high half = fp32 bits
+  }
+  __device__ __forceinline__ static float4 group_values(const uint4& d, int g) {
+    const uint32_t a = g == 0 ? d.x : d.z, b = g == 0 ? d.y : d.w;
+    return make_float4(__uint_as_float(a << 16), __uint_as_float(a & 0xFFFF0000u),
+                       __uint_as_float(b << 16), __uint_as_float(b & 0xFFFF0000u));
+  }
+};
+
+template <>
+struct Elem<ACO_FP16> {
+  static constexpr int V = 8;
+  static constexpr int BYTES = 2;
+  __device__ __forceinline__ static float h2f(uint32_t h) {
+    return __half2float(__ushort_as_half((unsigned short)(h & 0xFFFFu)));
+  }
+  __device__ __forceinline__ static uint32_t group_max_bits(const uint4& d, int g) {
+    const uint32_t m = g == 0 ? vmax_u16x2(d.x, d.y) : vmax_u16x2(d.z, d.w);
+    return __float_as_uint(h2f(vmax_u16x2(m, swap_halves(m))));
+  }
+  __device__ __forceinline__ static float4 group_values(const uint4& d, int g) {
+    const uint32_t a = g == 0 ? d.x : d.z, b = g == 0 ? d.y : d.w;
+    return make_float4(h2f(a), h2f(a >> 16), h2f(b), h2f(b >> 16));
+  }
+};
+
+// Running argmax update with the lowest-index tie-break.
+__device__ __forceinline__ void better(float s, int j, float& bs, int& bj) {
+  if (s > bs || (s == bs && j < bj)) {
+    bs = s;
+    bj = j;
+  }
+}
+
+template <int PREC, int W, int KC>
+__global__ void __launch_bounds__(32 * W) construct_kernel(
+    const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it_arg,
+    const uint32_t* __restrict__ it_dev, int32_t* __restrict__ tours, int32_t* __restrict__ err) {
+  using E = Elem<PREC>;
+  constexpr int V = E::V;
+  constexpr int G = V / 4;                // 4-column groups per chunk (one Philox block each)
+  constexpr int NG = KC * G;              // groups per thread
+  constexpr int MW = (KC * V + 31) / 32;  // visited-bit words per thread
+  constexpr int TPA = 32 * W;             // threads per ant
+  constexpr uint32_t CMASK = (1u << V) - 1u;
+  static_assert(NG <= 64, "survivor mask is 64 bits");
+  static_assert(NG <= 255, "group index packs into 8 bits");
+
+  const int k = blockIdx.x;
+  if (k >= m) return;
+  const int gl = threadIdx.x;
+  const int lane = gl & 31;
+  const int wi = gl >> 5;
+  const uint32_t it = it_dev ? *it_dev : it_arg;
+  const char* __restrict__ P = static_cast<const char*>(Pv);
+  const size_t row_bytes = (size_t)ld * E::BYTES;
+
+  __shared__ float red_s[2][W];
+  __shared__ int red_j[2][W];
+  extern __shared__ __align__(16) uint4 srow[];  // [KC * TPA] chunks of the current row
+
+  // visited bits: bit c*V + e  <->  column (c*TPA + gl)*V + e
+  uint32_t vis[MW];
+#pragma unroll
+  for (int q = 0; q < MW; ++q) vis[q] = 0u;
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    const int j0 = (c * TPA + gl) * V;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      if (j0 + e >= n) vis[(c * V + e) >> 5] |= 1u << ((c * V + e) & 31);
+    }
+  }
+  auto mark = [&](int v) {
+    const int cg = v / V;
+    const int bit = (cg / TPA) * V + (v - cg * V);
+    if (cg % TPA == gl) {
+#pragma unroll
+      for (int q = 0; q < MW; ++q)
+        if (q == (bit >> 5)) vis[q] |= 1u << (bit & 31);
+    }
+  };
+
+  int cur = start_city(key, it, (uint32_t)k, n);
+  if (gl == 0) tours[(size_t)k * n] = cur;
+  mark(cur);
+
+  for (int t = 1; t < n; ++t) {
+    const char* __restrict__ row = P + (size_t)cur * row_bytes;
+
+    // 1. stage the row: every chunk with an unvisited column, 16 bytes each
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const bool full = ((vis[(c * V) >> 5] >> ((c * V) & 31)) & CMASK) == CMASK;
+      cp_async16_pred(srow + c * TPA + gl, reinterpret_cast<const uint4*>(row) + (c * TPA + gl), !full);
+    }
+    cp_async_wait_all();  // this thread's copies only: it reads nothing else
+
+    // 2. per group: raw maximum packed with the group index; the thread's top group
+    int gkey[NG];
+    int top = -1;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int gi = c * G + g;
+        const int bp = c * V + g * 4;
+        const bool empty = ((vis[bp >> 5] >> (bp & 31)) & 0xFu) == 0xFu;
+        const uint32_t mb = E::group_max_bits(srow[c * TPA + gl], g);
+        const int kk = empty ? -1 : (int)((mb & ~0xFFu) | (uint32_t)(0xFF - gi));
+        gkey[gi] = kk;
+        top = max(top, kk);
+      }
+    }
+
+    float bs = -1.0f;
+    int bj = 0x7FFFFFFF;
+    auto score_group = [&](int gi) {
+      const int c = gi / G, g = gi - c * G;
+      const int bp = c * V + g * 4;
+      uint32_t w = 0u;
+#pragma unroll
+      for (int q = 0; q < MW; ++q)
+        if (q == (bp >> 5)) w = vis[q];
+      const uint32_t nib = (w >> (bp & 31)) & 0xFu;
+      if (nib == 0xFu) return;
+      const int j0 = (c * TPA + gl) * V + g * 4;
+      const float4 p = E::group_values(srow[c * TPA + gl], g);
+      const uint4 x = philox(make_uint4((uint32_t)(j0 >> 2), (uint32_t)t, (uint32_t)k, it), key);
+      if (!(nib & 1u)) better(__fmul_rn(uniform01(x.x), p.x), j0, bs, bj);
+      if (!(nib & 2u)) better(__fmul_rn(uniform01(x.y), p.y), j0 + 1, bs, bj);
+      if (!(nib & 4u)) better(__fmul_rn(uniform01(x.z), p.z), j0 + 2, bs, bj);
+      if (!(nib & 8u)) better(__fmul_rn(uniform01(x.w), p.w), j0 + 3, bs, bj);
+    };
+
+    // 3. exact score of the top group; the warp's best exact score is the threshold
+    const int top_gi = top >= 0 ? 0xFF - (top & 0xFF) : -1;
+    if (top_gi >= 0) score_group(top_gi);
+    float thr = bs;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) thr = fmaxf(thr, __shfl_xor_sync(ACO_FULL_MASK, thr, off));
+    const int thr_key = thr >= 0.0f ? (int)(__float_as_uint(thr) & ~0xFFu) : 0;
+
+    // 4. groups that can still reach the threshold
+    uint64_t surv = 0ull;
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi)
+      if (gkey[gi] >= thr_key && gi != top_gi) surv |= 1ull << gi;
+    while (__any_sync(ACO_FULL_MASK, surv != 0ull)) {
+      if (surv) {
+        const int gi = __ffsll((long long)surv) - 1;
+        surv &= surv - 1ull;
+        score_group(gi);
+      }
+    }
+
+    // 5. argmax across the warp, then across the ant's warps
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float os = __shfl_xor_sync(ACO_FULL_MASK, bs, off);
+      const int oj = __shfl_xor_sync(ACO_FULL_MASK, bj, off);
+      better(os, oj, bs, bj);
+    }
+    if (W > 1) {
+      if (lane == 0) {
+        red_s[t & 1][wi] = bs;
+        red_j[t & 1][wi] = bj;
+      }
+      __syncthreads();
+      bs = red_s[t & 1][0];
+      bj = red_j[t & 1][0];
+#pragma unroll
+      for (int w = 1; w < W; ++w) better(red_s[t & 1][w], red_j[t & 1][w], bs, bj);
+    }
+
+    const int next = bj;
+    if (next < 0 || next >= n) {  // no unvisited city found: cannot happen for valid input
+      if (gl == 0 && err) atomicExch(err, 1);
+      break;
+    }
+    if (gl == 0) tours[(size_t)k * n + t] = next;
+    mark(next);
+    cur = next;
+  }
+}
+
+// Host launcher body for one precision: dispatch over the compiled shapes.
+// The row buffer is KC * 32 * W * 16 bytes of dynamic shared memory.
+#define ACO_CONSTRUCT_CASE(PREC, W, KC)                                                    \
+  if (warps == W && chunks == KC) {                                                        \
+    construct_kernel<PREC, W, KC><<<m, 32 * W, (size_t)KC * 32 * W * 16, st>>>(             \
+        P, n, ld, m, key, it, it_dev, tours, err);                                         \
+    const cudaError_t e_ = cudaGetLastError();                                             \
+    return e_ == cudaSuccess ? ACO_OK : cuda_error(e_, "construct_kernel launch");         \
+  }
+
+}  // namespace aco
+
+namespace aco {
+// Opt every compiled shape in to its dynamic shared-memory size (once).
+#define ACO_CONSTRUCT_PREPARE(PREC, W, KC)                                                  \
+  {                                                                                        \
+    const cudaError_t e_ = cudaFuncSetAttribute(construct_kernel<PREC, W, KC>,             \
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                KC * 32 * W * 16);                          \
+    if (e_ != cudaSuccess) return cuda_error(e_, "cudaFuncSetAttribute(construct_kernel)"); \
+  }
+}  // namespace aco

@@ -1,0 +1,75 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "tensoraco.h"
+
+namespace aco {
+
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+#define ACO_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return ::aco::cuda_error(_e, #expr); \
+  } while (0)
+
+#define ACO_CHECK_LAUNCH(what)                              \
+  do {                                                      \
+    cudaError_t _e = cudaGetLastError();                    \
+    if (_e != cudaSuccess) return ::aco::cuda_error(_e, what); \
+  } while (0)
+
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Construct-kernel launch shapes compiled in, per element size (4 or 2 bytes).
+struct ConstructShape {
+  int warps;   // warps per ant
+  int chunks;  // 16-byte chunks per lane
+};
+int construct_shapes(int elem_bytes, const ConstructShape** list);
+// Default shape for (n, m, elem_bytes): the narrowest warp count whose chunk
+// count is compiled in, unless an autotuned choice is registered.
+ConstructShape default_construct_shape(int n, int m, int elem_bytes);
+void register_tuned_shape(int n, int m, int elem_bytes, ConstructShape s);
+
+// Kernel launchers (return ACO_OK or an error code; asynchronous).
+int launch_construct_f32(const float* P, int n, int ld, int m, uint2 key, uint32_t it,
+                         const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
+                         int chunks, cudaStream_t st);
+int launch_construct_bf16(const void* P, int n, int ld, int m, uint2 key, uint32_t it,
+                          const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
+                          int chunks, cudaStream_t st);
+int launch_construct_f16(const void* P, int n, int ld, int m, uint2 key, uint32_t it,
+                         const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
+                         int chunks, cudaStream_t st);
+
+int prepare_construct_f32();
+int prepare_construct_bf16();
+int prepare_construct_f16();
+int prepare_deposit();
+int prepare_kernels();  // once per process: shared-memory opt-ins (not during capture)
+
+int launch_heuristic(const float* xy, int n, int beta, double* D, float* H, int ld,
+                     cudaStream_t st);
+int launch_fill(float* a, int n, int ld, float v, cudaStream_t st);
+int launch_build_P(const float* tau, const float* H, int n, int ld, int alpha, float inv_gamma,
+                   const float* inv_gamma_dev, const uint32_t* it_dev, int n_sched, int prec,
+                   void* P, cudaStream_t st);
+int launch_tour_length(const double* D, int n, const int32_t* tours, int m, float Q,
+                       double* L, double* c, int32_t* nbr, cudaStream_t st);
+int launch_best(const double* L, const int32_t* tours, int n, int m, int32_t* best_tour,
+                double* best_len, uint32_t* it_dev, cudaStream_t st);
+int launch_deposit(float* tau, int n, int ld, const int32_t* nbr, const double* c, int m,
+                   float rho, cudaStream_t st);
+int launch_deposit_atomic(float* tau, int n, int ld, const int32_t* tours, const double* c,
+                          int m, float rho, cudaStream_t st);
+int launch_philox(const uint32_t* ctr, uint2 key, uint32_t* out, int count, cudaStream_t st);
+int launch_pow_own(const float* x, float e, float* out, int count, cudaStream_t st);
+
+}  // namespace aco

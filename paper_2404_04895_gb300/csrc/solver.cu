@@ -1,0 +1,815 @@
+// Host runtime and C ABI of the TensorACO library: solver state in device
+// memory, the per-iteration launch sequence (captured once into a CUDA graph
+// and replayed), the single-instance global API and the step-level calls.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+#include "shapes.h"
+
+namespace aco {
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  return set_error(e == cudaErrorMemoryAllocation ? ACO_ERR_OOM : ACO_ERR_CUDA, "%s: %s (%s)",
+                   what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// ------------------------------------------------------------------ shapes
+static const ConstructShape kShapes4[] = {
+#define X(W, KC) {W, KC},
+    ACO_SHAPES_4B(X)
+#undef X
+};
+static const ConstructShape kShapes2[] = {
+#define X(W, KC) {W, KC},
+    ACO_SHAPES_2B(X)
+#undef X
+};
+
+int construct_shapes(int elem_bytes, const ConstructShape** list) {
+  if (elem_bytes == 4) {
+    *list = kShapes4;
+    return (int)(sizeof(kShapes4) / sizeof(kShapes4[0]));
+  }
+  *list = kShapes2;
+  return (int)(sizeof(kShapes2) / sizeof(kShapes2[0]));
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, ConstructShape> g_tuned;
+
+void register_tuned_shape(int n, int m, int elem_bytes, ConstructShape s) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[std::make_tuple(n, m, elem_bytes)] = s;
+}
+
+static int shape_columns(ConstructShape s, int elem_bytes) {
+  return 32 * s.warps * s.chunks * (16 / elem_bytes);
+}
+
+ConstructShape default_construct_shape(int n, int m, int elem_bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(std::make_tuple(n, m, elem_bytes));
+    if (it != g_tuned.end()) return it->second;
+  }
+  const ConstructShape* list;
+  const int cnt = construct_shapes(elem_bytes, &list);
+  ConstructShape best = {0, 0};
+  for (int q = 0; q < cnt; ++q) {
+    if (shape_columns(list[q], elem_bytes) < n) continue;
+    if (best.warps == 0 || list[q].warps < best.warps ||
+        (list[q].warps == best.warps && list[q].chunks < best.chunks))
+      best = list[q];
+  }
+  return best;
+}
+
+int prepare_kernels() {
+  static std::once_flag once;
+  static int rc = ACO_OK;
+  std::call_once(once, [] {
+    rc = prepare_construct_f32();
+    if (!rc) rc = prepare_construct_bf16();
+    if (!rc) rc = prepare_construct_f16();
+    if (!rc) rc = prepare_deposit();
+  });
+  return rc == ACO_OK ? ACO_OK : set_error(rc, "kernel preparation failed");
+}
+
+static int launch_construct(const void* P, int prec, int n, int ld, int m, uint2 key, uint32_t it,
+                            const uint32_t* it_dev, int32_t* tours, int32_t* err,
+                            ConstructShape s, cudaStream_t st) {
+  const int eb = prec == ACO_FP32 ? 4 : 2;
+  if (s.warps == 0) s = default_construct_shape(n, m, eb);
+  if (s.warps == 0 || shape_columns(s, eb) < n)
+    return set_error(ACO_ERR_UNSUPPORTED, "no construct shape covers n=%d", n);
+  switch (prec) {
+    case ACO_FP32:
+      return launch_construct_f32(static_cast<const float*>(P), n, ld, m, key, it, it_dev, tours, err,
+                                  s.warps, s.chunks, st);
+    case ACO_BF16:
+      return launch_construct_bf16(P, n, ld, m, key, it, it_dev, tours, err, s.warps, s.chunks, st);
+    case ACO_FP16:
+      return launch_construct_f16(P, n, ld, m, key, it, it_dev, tours, err, s.warps, s.chunks, st);
+  }
+  return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+}
+
+// ------------------------------------------------------------------ gamma
+static float gamma_at(int it, int T, float gmax, float gmin) {
+  if (T <= 0 || it >= T) return gmin;
+  const double hi = (double)gmax, lo = (double)gmin;
+  const double ang = 3.14159265358979323846 * (double)it / (double)T;
+  const double g = lo + 0.5 * (hi - lo) * (1.0 + std::cos(ang));
+  return (float)g;
+}
+static float inv_gamma_of(float g) { return (float)(1.0 / (double)g); }
+
+// ------------------------------------------------------------------ validation
+static bool is_small_int(float v) { return std::isfinite(v) && v >= 0.0f && v <= 8.0f && v == std::floor(v); }
+
+static int validate(const aco_params* p) {
+  if (!p) return set_error(ACO_ERR_ARG, "params is NULL");
+  if (p->n < 3 || p->n > ACO_MAX_N) return set_error(ACO_ERR_ARG, "n=%d outside [3, %d]", p->n, ACO_MAX_N);
+  if (p->m < 1 || p->m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "m=%d outside [1, %d]", p->m, ACO_MAX_M);
+  if (p->alpha < 0 || p->alpha > 8 || p->beta < 0 || p->beta > 8)
+    return set_error(ACO_ERR_UNSUPPORTED, "alpha/beta must be integers in [0, 8]");
+  if (!(p->rho >= 0.0f && p->rho <= 1.0f)) return set_error(ACO_ERR_ARG, "rho outside [0, 1]");
+  if (!(p->Q >= 0.0f) || !std::isfinite(p->Q)) return set_error(ACO_ERR_ARG, "Q must be finite and >= 0");
+  if (!(p->tau0 > 0.0f) || !std::isfinite(p->tau0)) return set_error(ACO_ERR_ARG, "tau0 must be finite and > 0");
+  if (p->prec < ACO_FP32 || p->prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", p->prec);
+  if (p->roulette != ACO_IR && p->roulette != ACO_ADAIR) return set_error(ACO_ERR_ARG, "unknown roulette %d", p->roulette);
+  if (p->deposit != ACO_DEPOSIT_DET && p->deposit != ACO_DEPOSIT_ATOMIC)
+    return set_error(ACO_ERR_ARG, "unknown deposit mode %d", p->deposit);
+  if (p->roulette == ACO_ADAIR) {
+    if (!(p->gamma_max > 0.0f && p->gamma_max <= 16.0f && p->gamma_min > 0.0f && p->gamma_min <= 16.0f))
+      return set_error(ACO_ERR_ARG, "gamma outside (0, 16]");
+    if (p->gamma_T < 1) return set_error(ACO_ERR_ARG, "gamma_T must be >= 1");
+  }
+  return ACO_OK;
+}
+
+// ------------------------------------------------------------------ workspace
+constexpr int kSchedCap = 1 << 16;  // AdaIR schedule entries (iterations 0..T, clamped)
+
+struct Layout {
+  size_t coords, D, H, tau, P, tours, L, c, nbr, best_tour, best_len, it, err, sched, total;
+};
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+static int ld_of(int n) { return (n + 7) & ~7; }
+
+static Layout layout_of(int n, int m) {
+  const size_t ld = (size_t)ld_of(n);
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += al(bytes);
+    return at;
+  };
+  L.coords = take((size_t)n * 2 * 4);
+  L.D = take((size_t)n * n * 8);
+  L.H = take((size_t)n * ld * 4);
+  L.tau = take((size_t)n * ld * 4);
+  L.P = take((size_t)n * ld * 4);
+  L.tours = take((size_t)m * n * 4);
+  L.L = take((size_t)m * 8);
+  L.c = take((size_t)m * 8);
+  L.nbr = take((size_t)n * m * 2 * 4);
+  L.best_tour = take((size_t)n * 4);
+  L.best_len = take(8);
+  L.it = take(4);
+  L.err = take(4);
+  L.sched = take((size_t)kSchedCap * 4);
+  L.total = o;
+  return L;
+}
+
+}  // namespace aco
+
+using namespace aco;
+
+struct aco_solver {
+  aco_params p;
+  int ld;
+  cudaStream_t stream;
+  bool own_ws;
+  unsigned char* ws;
+  Layout lay;
+  float *coords, *H, *tau, *P_f, *sched;
+  double *D, *L, *c, *best_len;
+  int32_t *tours, *nbr, *best_tour, *err;
+  uint32_t* it_dev;
+  uint32_t it;                 // iterations completed (host mirror)
+  ConstructShape shape;        // {0,0}: default for (n, m, prec)
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  bool graph_ok;
+  bool use_graph;
+  bool profiling;
+  cudaEvent_t ev[6];           // probes around the iteration's kernels
+
+  template <class T>
+  T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
+};
+
+namespace aco {
+
+static int upload_schedule(aco_solver* s) {
+  const aco_params& p = s->p;
+  if (p.roulette != ACO_ADAIR) return ACO_OK;
+  const int cnt = std::min(p.gamma_T + 1, kSchedCap);
+  std::vector<float> h((size_t)cnt);
+  for (int q = 0; q < cnt; ++q) h[q] = inv_gamma_of(gamma_at(q, p.gamma_T, p.gamma_max, p.gamma_min));
+  ACO_CUDA_TRY(cudaMemcpyAsync(s->sched, h.data(), sizeof(float) * cnt, cudaMemcpyHostToDevice, s->stream));
+  // pageable copy: make it complete before the host buffer goes away
+  ACO_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return ACO_OK;
+}
+
+static void drop_graph(aco_solver* s) {
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  s->exec = nullptr;
+  s->graph = nullptr;
+  s->graph_ok = false;
+}
+
+// The launches of one iteration (a)-(d); the iteration number and AdaIR's
+// exponent are read from device memory so the sequence can be replayed.
+static int enqueue_iteration(aco_solver* s) {
+  const aco_params& p = s->p;
+  const int n = p.n, m = p.m;
+  cudaStream_t st = s->stream;
+  const int n_sched = std::min(p.gamma_T + 1, kSchedCap);
+  auto probe = [&](int q) {
+    if (s->profiling) cudaEventRecord(s->ev[q], st);
+  };
+  probe(0);
+  int rc = launch_build_P(s->tau, s->H, n, s->ld, p.alpha, 1.0f,
+                          p.roulette == ACO_ADAIR ? s->sched : nullptr, s->it_dev, n_sched, p.prec,
+                          s->P_f, st);
+  if (rc) return rc;
+  probe(1);
+  rc = launch_construct(s->P_f, p.prec, n, s->ld, m, make_uint2((uint32_t)p.seed, (uint32_t)(p.seed >> 32)),
+                        0u, s->it_dev, s->tours, s->err, s->shape, st);
+  if (rc) return rc;
+  probe(2);
+  const bool det = p.deposit == ACO_DEPOSIT_DET;
+  rc = launch_tour_length(s->D, n, s->tours, m, p.Q, s->L, s->c, det ? s->nbr : nullptr, st);
+  if (rc) return rc;
+  probe(3);
+  rc = launch_best(s->L, s->tours, n, m, s->best_tour, s->best_len, s->it_dev, st);
+  if (rc) return rc;
+  probe(4);
+  if (det)
+    rc = launch_deposit(s->tau, n, s->ld, s->nbr, s->c, m, p.rho, st);
+  else
+    rc = launch_deposit_atomic(s->tau, n, s->ld, s->tours, s->c, m, p.rho, st);
+  if (rc) return rc;
+  probe(5);
+  return ACO_OK;
+}
+
+static int build_graph(aco_solver* s) {
+  drop_graph(s);
+  ACO_CUDA_TRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_iteration(s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&s->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_error(e, "cudaGraphInstantiate");
+  }
+  s->graph = g;
+  s->graph_ok = true;
+  return ACO_OK;
+}
+
+static int solver_sync_check(aco_solver* s) {
+  ACO_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  int32_t err = 0;
+  ACO_CUDA_TRY(cudaMemcpy(&err, s->err, 4, cudaMemcpyDeviceToHost));
+  if (err) return set_error(ACO_ERR_CUDA, "a kernel-side check failed (code %d)", err);
+  return ACO_OK;
+}
+
+}  // namespace aco
+
+static int check_mat(const void* p, int n, int ld, const char* name) {
+  if (!p) return set_error(ACO_ERR_ARG, "%s is NULL", name);
+  if (n < 3 || n > ACO_MAX_N) return set_error(ACO_ERR_ARG, "n=%d outside [3, %d]", n, ACO_MAX_N);
+  if (ld < n || (ld & 7)) return set_error(ACO_ERR_ARG, "ld=%d must be >= n and a multiple of 8", ld);
+  if (!aligned16(p)) return set_error(ACO_ERR_ARG, "%s must be 16-byte aligned", name);
+  return ACO_OK;
+}
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* aco_last_error(void) { return g_err; }
+
+int aco_params_default(aco_params* p) {
+  if (!p) return set_error(ACO_ERR_ARG, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->alpha = 1;
+  p->beta = 2;
+  p->rho = 0.5f;
+  p->Q = 1.0f;
+  p->tau0 = 1.0f;
+  p->prec = ACO_FP32;
+  p->roulette = ACO_IR;
+  p->deposit = ACO_DEPOSIT_DET;
+  p->gamma_max = 1.5f;
+  p->gamma_min = 0.5f;
+  p->gamma_T = 100;
+  return ACO_OK;
+}
+
+int aco_workspace_bytes(int n, int m, int prec, size_t* bytes) {
+  if (!bytes) return set_error(ACO_ERR_ARG, "bytes is NULL");
+  if (n < 3 || n > ACO_MAX_N || m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "n or m out of range");
+  if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  *bytes = layout_of(n, m).total;
+  return ACO_OK;
+}
+
+int aco_create(aco_solver** out, const float* coords_host, const aco_params* p, void* dev_workspace,
+               size_t ws_bytes, void* stream) {
+  if (!out || !coords_host) return set_error(ACO_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  int rc = validate(p);
+  if (rc) return rc;
+  for (int q = 0; q < 2 * p->n; ++q)
+    if (!std::isfinite(coords_host[q])) return set_error(ACO_ERR_ARG, "coordinate %d is not finite", q);
+  rc = prepare_kernels();
+  if (rc) return rc;
+  aco_solver* s = new aco_solver();
+  s->p = *p;
+  s->ld = ld_of(p->n);
+  s->stream = static_cast<cudaStream_t>(stream);
+  s->lay = layout_of(p->n, p->m);
+  if (dev_workspace) {
+    if (ws_bytes < s->lay.total) {
+      delete s;
+      return set_error(ACO_ERR_OOM, "workspace of %zu bytes < %zu needed", ws_bytes, s->lay.total);
+    }
+    if (((uintptr_t)dev_workspace & 255u) != 0) {
+      delete s;
+      return set_error(ACO_ERR_ARG, "workspace must be 256-byte aligned");
+    }
+    s->ws = static_cast<unsigned char*>(dev_workspace);
+    s->own_ws = false;
+  } else {
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, s->lay.total);
+    if (e != cudaSuccess) {
+      delete s;
+      return cuda_error(e, "cudaMalloc(workspace)");
+    }
+    s->ws = static_cast<unsigned char*>(mem);
+    s->own_ws = true;
+  }
+  const Layout& L = s->lay;
+  s->coords = s->at<float>(L.coords);
+  s->D = s->at<double>(L.D);
+  s->H = s->at<float>(L.H);
+  s->tau = s->at<float>(L.tau);
+  s->P_f = s->at<float>(L.P);
+  s->tours = s->at<int32_t>(L.tours);
+  s->L = s->at<double>(L.L);
+  s->c = s->at<double>(L.c);
+  s->nbr = s->at<int32_t>(L.nbr);
+  s->best_tour = s->at<int32_t>(L.best_tour);
+  s->best_len = s->at<double>(L.best_len);
+  s->it_dev = s->at<uint32_t>(L.it);
+  s->err = s->at<int32_t>(L.err);
+  s->sched = s->at<float>(L.sched);
+  // Replay through a CUDA graph on a created stream; the legacy default stream
+  // cannot be captured, so there the iteration's kernels are launched directly.
+  s->use_graph = s->stream != nullptr;
+
+  auto fail = [&](int code) {
+    if (s->own_ws) cudaFree(s->ws);
+    delete s;
+    return code;
+  };
+  const int n = p->n;
+  cudaStream_t st = s->stream;
+  if (cudaMemcpyAsync(s->coords, coords_host, sizeof(float) * 2 * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return fail(cuda_error(cudaGetLastError(), "copy coords"));
+  rc = launch_heuristic(s->coords, n, p->beta, s->D, s->H, s->ld, st);
+  if (!rc) rc = launch_fill(s->tau, n, s->ld, p->tau0, st);
+  if (rc) return fail(rc);
+  const double inf = INFINITY;
+  const uint32_t zero = 0;
+  if (cudaMemcpyAsync(s->best_len, &inf, 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(s->it_dev, &zero, 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(s->err, 0, 4, st) != cudaSuccess ||
+      cudaMemsetAsync(s->best_tour, 0, sizeof(int32_t) * n, st) != cudaSuccess)
+    return fail(cuda_error(cudaGetLastError(), "initialise state"));
+  rc = upload_schedule(s);
+  if (rc) return fail(rc);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "init sync"));
+  *out = s;
+  return ACO_OK;
+}
+
+int aco_destroy(aco_solver* s) {
+  if (!s) return ACO_OK;
+  cudaStreamSynchronize(s->stream);
+  drop_graph(s);
+  if (s->profiling)
+    for (int q = 0; q < 6; ++q) cudaEventDestroy(s->ev[q]);
+  if (s->own_ws) cudaFree(s->ws);
+  delete s;
+  return ACO_OK;
+}
+
+int aco_solver_iterate(aco_solver* s, int k) {
+  if (!s) return set_error(ACO_ERR_ARG, "solver is NULL");
+  if (k < 0) return set_error(ACO_ERR_ARG, "k must be >= 0");
+  for (int q = 0; q < k; ++q) {
+    if (s->use_graph) {
+      if (!s->graph_ok) {
+        int rc = build_graph(s);
+        if (rc) return rc;
+      }
+      ACO_CUDA_TRY(cudaGraphLaunch(s->exec, s->stream));
+    } else {
+      int rc = enqueue_iteration(s);
+      if (rc) return rc;
+    }
+    s->it += 1;
+  }
+  return ACO_OK;
+}
+
+int aco_solver_best(aco_solver* s, int32_t* tour_host, double* len_host) {
+  if (!s || !tour_host || !len_host) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (s->it == 0) return set_error(ACO_ERR_STATE, "no iteration has run yet");
+  int rc = solver_sync_check(s);
+  if (rc) return rc;
+  ACO_CUDA_TRY(cudaMemcpy(len_host, s->best_len, 8, cudaMemcpyDeviceToHost));
+  ACO_CUDA_TRY(cudaMemcpy(tour_host, s->best_tour, sizeof(int32_t) * s->p.n, cudaMemcpyDeviceToHost));
+  return ACO_OK;
+}
+
+int aco_solver_get_tau(aco_solver* s, float* tau_host) {
+  if (!s || !tau_host) return set_error(ACO_ERR_ARG, "NULL argument");
+  int rc = solver_sync_check(s);
+  if (rc) return rc;
+  ACO_CUDA_TRY(cudaMemcpy2D(tau_host, sizeof(float) * s->p.n, s->tau, sizeof(float) * s->ld,
+                            sizeof(float) * s->p.n, s->p.n, cudaMemcpyDeviceToHost));
+  return ACO_OK;
+}
+
+int aco_solver_get_tours(aco_solver* s, int32_t* tours_host) {
+  if (!s || !tours_host) return set_error(ACO_ERR_ARG, "NULL argument");
+  int rc = solver_sync_check(s);
+  if (rc) return rc;
+  ACO_CUDA_TRY(cudaMemcpy(tours_host, s->tours, sizeof(int32_t) * s->p.m * s->p.n, cudaMemcpyDeviceToHost));
+  return ACO_OK;
+}
+
+int aco_solver_get_lengths(aco_solver* s, double* lengths_host) {
+  if (!s || !lengths_host) return set_error(ACO_ERR_ARG, "NULL argument");
+  int rc = solver_sync_check(s);
+  if (rc) return rc;
+  ACO_CUDA_TRY(cudaMemcpy(lengths_host, s->L, sizeof(double) * s->p.m, cudaMemcpyDeviceToHost));
+  return ACO_OK;
+}
+
+int aco_solver_device_state(aco_solver* s, float** tau, int* ld, int32_t** tours, double** lengths,
+                            int32_t** best_tour, double** best_len) {
+  if (!s) return set_error(ACO_ERR_ARG, "solver is NULL");
+  if (tau) *tau = s->tau;
+  if (ld) *ld = s->ld;
+  if (tours) *tours = s->tours;
+  if (lengths) *lengths = s->L;
+  if (best_tour) *best_tour = s->best_tour;
+  if (best_len) *best_len = s->best_len;
+  return ACO_OK;
+}
+
+int aco_solver_iteration(aco_solver* s, uint32_t* it) {
+  if (!s || !it) return set_error(ACO_ERR_ARG, "NULL argument");
+  *it = s->it;
+  return ACO_OK;
+}
+
+int aco_solver_set_profiling(aco_solver* s, int on) {
+  if (!s) return set_error(ACO_ERR_ARG, "solver is NULL");
+  if ((bool)on == s->profiling) return ACO_OK;
+  ACO_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  drop_graph(s);
+  if (on) {
+    for (int q = 0; q < 6; ++q) ACO_CUDA_TRY(cudaEventCreate(&s->ev[q]));
+  } else {
+    for (int q = 0; q < 6; ++q) cudaEventDestroy(s->ev[q]);
+  }
+  s->profiling = on != 0;
+  return ACO_OK;
+}
+
+int aco_solver_kernel_ms(aco_solver* s, float* ms5) {
+  if (!s || !ms5) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (!s->profiling) return set_error(ACO_ERR_STATE, "profiling is off");
+  if (s->it == 0) return set_error(ACO_ERR_STATE, "no iteration has run yet");
+  ACO_CUDA_TRY(cudaEventSynchronize(s->ev[5]));
+  for (int q = 0; q < 5; ++q) ACO_CUDA_TRY(cudaEventElapsedTime(&ms5[q], s->ev[q], s->ev[q + 1]));
+  return ACO_OK;
+}
+
+int aco_solver_set_shape(aco_solver* s, int warps, int chunks) {
+  if (!s) return set_error(ACO_ERR_ARG, "solver is NULL");
+  if (warps || chunks) {
+    const int eb = s->p.prec == ACO_FP32 ? 4 : 2;
+    const ConstructShape* list;
+    const int cnt = construct_shapes(eb, &list);
+    bool found = false;
+    for (int q = 0; q < cnt; ++q) found |= list[q].warps == warps && list[q].chunks == chunks;
+    if (!found) return set_error(ACO_ERR_UNSUPPORTED, "shape (%d, %d) not compiled", warps, chunks);
+    if (shape_columns({warps, chunks}, eb) < s->p.n)
+      return set_error(ACO_ERR_ARG, "shape (%d, %d) does not cover n=%d", warps, chunks, s->p.n);
+  }
+  s->shape = {warps, chunks};
+  drop_graph(s);
+  return ACO_OK;
+}
+
+int aco_autotune_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed,
+                           int32_t* tours_scratch_dev, int reps, int* warps_out, int* chunks_out,
+                           float* ms_out, void* stream) {
+  int rc = check_mat(P_dev, n, ld, "P");
+  if (rc) return rc;
+  if (!tours_scratch_dev || m < 1 || m > ACO_MAX_M || reps < 1) return set_error(ACO_ERR_ARG, "invalid argument");
+  if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  rc = prepare_kernels();
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int eb = prec == ACO_FP32 ? 4 : 2;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  const ConstructShape* list;
+  const int cnt = construct_shapes(eb, &list);
+  cudaEvent_t e0, e1;
+  ACO_CUDA_TRY(cudaEventCreate(&e0));
+  ACO_CUDA_TRY(cudaEventCreate(&e1));
+  ConstructShape best = {0, 0};
+  float best_ms = 0.0f;
+  for (int q = 0; q < cnt && rc == ACO_OK; ++q) {
+    if (shape_columns(list[q], eb) < n) continue;
+    rc = launch_construct(P_dev, prec, n, ld, m, key, 0u, nullptr, tours_scratch_dev, nullptr, list[q], st);
+    if (rc) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && rc == ACO_OK; ++r)
+      rc = launch_construct(P_dev, prec, n, ld, m, key, (uint32_t)(r + 1), nullptr, tours_scratch_dev,
+                            nullptr, list[q], st);
+    cudaEventRecord(e1, st);
+    if (rc) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = cuda_error(cudaGetLastError(), "autotune sync");
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)reps;
+    if (best.warps == 0 || ms < best_ms) {
+      best = list[q];
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (best.warps == 0) return set_error(ACO_ERR_UNSUPPORTED, "no construct shape covers n=%d", n);
+  register_tuned_shape(n, m, eb, best);
+  if (warps_out) *warps_out = best.warps;
+  if (chunks_out) *chunks_out = best.chunks;
+  if (ms_out) *ms_out = best_ms;
+  return ACO_OK;
+}
+
+// ---------------------------------------------------------------- global API
+static aco_solver* g_solver = nullptr;
+static void* g_ws = nullptr;
+static size_t g_ws_bytes = 0;
+static void* g_stream = nullptr;
+static aco_params g_pending = [] {
+  aco_params p;
+  aco_params_default(&p);
+  return p;
+}();
+
+int aco_bind(void* dev_workspace, size_t bytes, void* stream) {
+  g_ws = dev_workspace;
+  g_ws_bytes = dev_workspace ? bytes : 0;
+  g_stream = stream;
+  return ACO_OK;
+}
+
+int aco_init(const float* coords_host, int n, int m, float alpha, float beta, float rho, float Q,
+             uint64_t seed) {
+  if (!is_small_int(alpha) || !is_small_int(beta))
+    return set_error(ACO_ERR_UNSUPPORTED, "alpha and beta must be integers in [0, 8]");
+  aco_params p = g_pending;
+  p.n = n;
+  p.m = m;
+  p.alpha = (int)alpha;
+  p.beta = (int)beta;
+  p.rho = rho;
+  p.Q = Q;
+  p.seed = seed;
+  if (g_solver) {
+    aco_destroy(g_solver);
+    g_solver = nullptr;
+  }
+  return aco_create(&g_solver, coords_host, &p, g_ws, g_ws_bytes, g_stream);
+}
+
+int aco_set_variant(int roulette, float gamma_max, float gamma_min, int T) {
+  aco_params p = g_solver ? g_solver->p : g_pending;
+  p.roulette = roulette;
+  p.gamma_max = gamma_max;
+  p.gamma_min = gamma_min;
+  p.gamma_T = T;
+  if (p.n == 0) {  // no solver yet: validate the variant fields only
+    if (roulette != ACO_IR && roulette != ACO_ADAIR) return set_error(ACO_ERR_ARG, "unknown roulette %d", roulette);
+    if (roulette == ACO_ADAIR && (!(gamma_max > 0 && gamma_max <= 16 && gamma_min > 0 && gamma_min <= 16) || T < 1))
+      return set_error(ACO_ERR_ARG, "invalid gamma schedule");
+  } else {
+    int rc = validate(&p);
+    if (rc) return rc;
+  }
+  g_pending.roulette = roulette;
+  g_pending.gamma_max = gamma_max;
+  g_pending.gamma_min = gamma_min;
+  g_pending.gamma_T = T;
+  if (g_solver) {
+    g_solver->p = p;
+    drop_graph(g_solver);
+    return upload_schedule(g_solver);
+  }
+  return ACO_OK;
+}
+
+int aco_set_precision(int prec) {
+  if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  g_pending.prec = prec;
+  if (g_solver) {
+    g_solver->p.prec = prec;
+    drop_graph(g_solver);
+  }
+  return ACO_OK;
+}
+
+int aco_set_deposit(int mode) {
+  if (mode != ACO_DEPOSIT_DET && mode != ACO_DEPOSIT_ATOMIC) return set_error(ACO_ERR_ARG, "unknown deposit mode %d", mode);
+  g_pending.deposit = mode;
+  if (g_solver) {
+    g_solver->p.deposit = mode;
+    drop_graph(g_solver);
+  }
+  return ACO_OK;
+}
+
+#define ACO_NEED_SOLVER() \
+  if (!g_solver) return set_error(ACO_ERR_STATE, "aco_init has not been called")
+
+int aco_iterate(int k) {
+  ACO_NEED_SOLVER();
+  return aco_solver_iterate(g_solver, k);
+}
+int aco_best(int32_t* tour, double* len) {
+  ACO_NEED_SOLVER();
+  return aco_solver_best(g_solver, tour, len);
+}
+int aco_get_tau(float* tau) {
+  ACO_NEED_SOLVER();
+  return aco_solver_get_tau(g_solver, tau);
+}
+int aco_get_tours(int32_t* tours) {
+  ACO_NEED_SOLVER();
+  return aco_solver_get_tours(g_solver, tours);
+}
+int aco_get_lengths(double* L) {
+  ACO_NEED_SOLVER();
+  return aco_solver_get_lengths(g_solver, L);
+}
+int aco_free(void) {
+  int rc = aco_destroy(g_solver);
+  g_solver = nullptr;
+  return rc;
+}
+
+// ---------------------------------------------------------------- step-level API
+
+int aco_op_heuristic(const float* coords_dev, int n, int beta, double* D_dev, float* H_dev, int ld,
+                     void* stream) {
+  int rc = check_mat(H_dev, n, ld, "H");
+  if (rc) return rc;
+  if (!coords_dev) return set_error(ACO_ERR_ARG, "coords is NULL");
+  if (beta < 0 || beta > 8) return set_error(ACO_ERR_UNSUPPORTED, "beta must be an integer in [0, 8]");
+  return launch_heuristic(coords_dev, n, beta, D_dev, H_dev, ld, static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_fill(float* dev, int n, int ld, float value, void* stream) {
+  int rc = check_mat(dev, n, ld, "matrix");
+  if (rc) return rc;
+  return launch_fill(dev, n, ld, value, static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_build_P(const float* tau_dev, const float* H_dev, int n, int ld, int alpha, float inv_gamma,
+                   int prec, void* P_dev, void* stream) {
+  int rc = check_mat(tau_dev, n, ld, "tau");
+  if (!rc) rc = check_mat(H_dev, n, ld, "H");
+  if (!rc) rc = check_mat(P_dev, n, ld, "P");
+  if (rc) return rc;
+  if (alpha < 0 || alpha > 8) return set_error(ACO_ERR_UNSUPPORTED, "alpha must be an integer in [0, 8]");
+  if (!(inv_gamma > 0.0f) || !std::isfinite(inv_gamma)) return set_error(ACO_ERR_ARG, "inv_gamma must be > 0");
+  return launch_build_P(tau_dev, H_dev, n, ld, alpha, inv_gamma, nullptr, nullptr, 1, prec, P_dev,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,
+                           int32_t* tours_dev, int32_t* err_dev, int warps, int chunks, void* stream) {
+  int rc = check_mat(P_dev, n, ld, "P");
+  if (rc) return rc;
+  if (m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "m=%d outside [1, %d]", m, ACO_MAX_M);
+  if (!tours_dev) return set_error(ACO_ERR_ARG, "tours is NULL");
+  if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  rc = prepare_kernels();
+  if (rc) return rc;
+  ConstructShape s = {warps, chunks};
+  return launch_construct(P_dev, prec, n, ld, m, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), it,
+                          nullptr, tours_dev, err_dev, s, static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,
+                     int32_t* tours_dev, int32_t* err_dev, void* stream) {
+  return aco_op_construct_shape(P_dev, prec, n, ld, m, seed, it, tours_dev, err_dev, 0, 0, stream);
+}
+
+int aco_op_tour_length(const double* D_dev, int n, const int32_t* tours_dev, int m, float Q, double* L_dev,
+                       double* c_dev, int32_t* nbr_dev, void* stream) {
+  if (!D_dev || !tours_dev || !L_dev) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (n < 3 || n > ACO_MAX_N || m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "n or m out of range");
+  if (nbr_dev && ((uintptr_t)nbr_dev & 7)) return set_error(ACO_ERR_ARG, "nbr must be 8-byte aligned");
+  return launch_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c_dev, nbr_dev, static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_best(const double* L_dev, const int32_t* tours_dev, int n, int m, int32_t* best_tour_dev,
+                double* best_len_dev, void* stream) {
+  if (!L_dev || !tours_dev || !best_tour_dev || !best_len_dev) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (n < 3 || n > ACO_MAX_N || m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "n or m out of range");
+  return launch_best(L_dev, tours_dev, n, m, best_tour_dev, best_len_dev, nullptr,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const double* c_dev, int m,
+                   float rho, void* stream) {
+  int rc = check_mat(tau_dev, n, ld, "tau");
+  if (rc) return rc;
+  if (!nbr_dev || !c_dev) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "m out of range");
+  if (!(rho >= 0.0f && rho <= 1.0f)) return set_error(ACO_ERR_ARG, "rho outside [0, 1]");
+  rc = prepare_kernels();
+  if (rc) return rc;
+  return launch_deposit(tau_dev, n, ld, nbr_dev, c_dev, m, rho, static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_deposit_atomic(float* tau_dev, int n, int ld, const int32_t* tours_dev, const double* c_dev,
+                          int m, float rho, void* stream) {
+  int rc = check_mat(tau_dev, n, ld, "tau");
+  if (rc) return rc;
+  if (!tours_dev || !c_dev) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "m out of range");
+  if (!(rho >= 0.0f && rho <= 1.0f)) return set_error(ACO_ERR_ARG, "rho outside [0, 1]");
+  return launch_deposit_atomic(tau_dev, n, ld, tours_dev, c_dev, m, rho, static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_philox(const uint32_t* ctr_dev, uint64_t seed, uint32_t* out_dev, int count, void* stream) {
+  if (!ctr_dev || !out_dev || count < 0) return set_error(ACO_ERR_ARG, "invalid argument");
+  if (!aligned16(ctr_dev) || !aligned16(out_dev)) return set_error(ACO_ERR_ARG, "buffers must be 16-byte aligned");
+  if (count == 0) return ACO_OK;
+  return launch_philox(ctr_dev, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), out_dev, count,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_pow_own(const float* x_dev, float e, float* out_dev, int count, void* stream) {
+  if (!x_dev || !out_dev || count < 0) return set_error(ACO_ERR_ARG, "invalid argument");
+  if (count == 0) return ACO_OK;
+  return launch_pow_own(x_dev, e, out_dev, count, static_cast<cudaStream_t>(stream));
+}
+
+float aco_gamma(int it, int T, float gamma_max, float gamma_min) { return gamma_at(it, T, gamma_max, gamma_min); }
+float aco_inv_gamma(float gamma) { return inv_gamma_of(gamma); }
+
+}  // extern "C"

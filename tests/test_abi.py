@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads without a GPU, and exports every function
+declared in include/tensoraco.h (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "tensoraco.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(aco_[A-Za-z0-9_]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_04895_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_path():
+    names = declared_functions()
+    for required in ["aco_init", "aco_iterate", "aco_best", "aco_free", "aco_op_build_P",
+                     "aco_op_construct", "aco_op_tour_length", "aco_op_deposit",
+                     "aco_op_deposit_atomic", "aco_create", "aco_solver_iterate"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_2404_04895_gb300 import binding
+    assert set(declared_functions()) <= set(binding.exported_symbols())
+
+
+def test_error_text_without_gpu(lib):
+    lib.aco_last_error.restype = ctypes.c_char_p
+    lib.aco_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_size_t)]
+    out = ctypes.c_size_t(0)
+    assert lib.aco_workspace_bytes(2, 10, 0, ctypes.byref(out)) == -1     # n < 3
+    assert b"out of range" in lib.aco_last_error()
+    assert lib.aco_workspace_bytes(5000, 1024, 0, ctypes.byref(out)) == 0
+    assert out.value > 5000 * 5000 * 8
+
+
+def test_gamma_schedule_matches_oracle(lib, orc):
+    # the host-side schedule the solvers upload is the oracle's, bit for bit
+    lib.aco_gamma.restype = ctypes.c_float
+    lib.aco_gamma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float]
+    lib.aco_inv_gamma.restype = ctypes.c_float
+    lib.aco_inv_gamma.argtypes = [ctypes.c_float]
+    for T in (1, 7, 100, 200):
+        for it in range(T + 3):
+            g = lib.aco_gamma(it, T, 1.5, 0.5)
+            assert g == orc.gamma(it, T, 1.5, 0.5)
+            assert lib.aco_inv_gamma(g) == orc.inv_gamma(g)
