@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--gap-seeds", type=int, default=5)
+    ap.add_argument("--no-autotune", action="store_true", help="default construct shape (profiling runs)")
     return ap.parse_args()
 
 
@@ -201,12 +202,13 @@ def oracle_sample(w, coords, seed, budget_s=10.0, min_ants=None):
         oracle.construct(P, seed, 0, k0, k1, threads)
         secs += time.perf_counter() - t0
         ants += k1 - k0
-        if secs >= budget_s or ants >= 4 * m:
+        if secs >= budget_s or ants >= 1000 * m:
             break
-        per_ant = secs / ants
-        batch = max(threads, int(min((budget_s - secs) / per_ant, 4 * m - ants)))
+        per_ant = max(secs / ants, 1e-7)
+        batch = max(threads, min(m, int((budget_s - secs) / per_ant)))
     return {"value": ants * (n - 1) / secs, "unit": METRIC, "cores": threads, "kind": "oracle",
-            "sample": f"{ants} ant tours (of m={m}) of iteration 0 on n={n}, {secs:.1f} s"}
+            "sample": f"{ants} ant tours (ants 0..{m - 1} cyclically, m={m}) of iteration 0 on n={n}, "
+                      f"{secs:.3f} s", "_secs": secs}
 
 
 # ---------------------------------------------------------------- native leg
@@ -250,7 +252,7 @@ def run_native(args, w, dist):
 
     tuned = {}
     for prec in ([w["prec"]] if args.no_variants else ["fp32", "bf16", "fp16"]):
-        tuned[prec] = autotune(B, torch, w, coords, prec, seed)
+        tuned[prec] = ((0, 0), None) if args.no_autotune else autotune(B, torch, w, coords, prec, seed)
     dist.barrier()
     clk = ClockSampler(dist.local)
     torch.cuda.synchronize()
@@ -335,6 +337,7 @@ def run_native(args, w, dist):
         out["e2e"] = run_e2e(args, w, coords, seed)
     if dist.rank == 0 and not args.no_cpu_baseline and dist.world == 1:
         out["cpu_baseline"] = oracle_sample(w, coords, seed)
+        out["cpu_baseline"].pop("_secs")
     return out
 
 
@@ -403,7 +406,7 @@ def run_reference(args, w, dist):
     tot_ants_steps, tot_s, samples = 0.0, 0.0, []
     for _ in range(args.steps):
         r = oracle_sample(w, coords, w["seed"], budget_s=per_step_budget)
-        secs = float(r["sample"].split(", ")[-1].split(" s")[0])
+        secs = r.pop("_secs")
         tot_s += secs
         tot_ants_steps += r["value"] * secs
         samples.append(r)

@@ -109,6 +109,12 @@ __device__ __forceinline__ void better(float s, int j, float& bs, int& bj) {
   }
 }
 
+// Order-preserving key of a candidate's score for unsigned warp reductions:
+// 0 = no candidate, else fp32 bits + 1 (scores are >= 0).
+__device__ __forceinline__ uint32_t score_key(float bs) {
+  return bs >= 0.0f ? __float_as_uint(bs) + 1u : 0u;
+}
+
 template <int PREC, int W, int KC>
 __global__ void __launch_bounds__(32 * W) construct_kernel(
     const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it_arg,
@@ -120,8 +126,10 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
   constexpr int MW = (KC * V + 31) / 32;  // visited-bit words per thread
   constexpr int TPA = 32 * W;             // threads per ant
   constexpr uint32_t CMASK = (1u << V) - 1u;
+  constexpr int NA = NG < 4 ? NG : 4;     // independent accumulators for the top-2 keys
   static_assert(NG <= 64, "survivor mask is 64 bits");
   static_assert(NG <= 255, "group index packs into 8 bits");
+  static_assert(KC <= 64, "full-chunk mask is 64 bits");
 
   const int k = blockIdx.x;
   if (k >= m) return;
@@ -132,12 +140,13 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
   const char* __restrict__ P = static_cast<const char*>(Pv);
   const size_t row_bytes = (size_t)ld * E::BYTES;
 
-  __shared__ float red_s[2][W];
+  __shared__ uint32_t red_s[2][W];
   __shared__ int red_j[2][W];
   extern __shared__ __align__(16) uint4 srow[];  // [KC * TPA] chunks of the current row
 
-  // visited bits: bit c*V + e  <->  column (c*TPA + gl)*V + e
+  // visited bits: bit c*V + e  <->  column (c*TPA + gl)*V + e; fullm bit c: chunk c done
   uint32_t vis[MW];
+  uint64_t fullm = 0ull;
 #pragma unroll
   for (int q = 0; q < MW; ++q) vis[q] = 0u;
 #pragma unroll
@@ -147,15 +156,31 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
     for (int e = 0; e < V; ++e) {
       if (j0 + e >= n) vis[(c * V + e) >> 5] |= 1u << ((c * V + e) & 31);
     }
+    if (j0 + V - 1 >= n && j0 >= n) fullm |= 1ull << c;
   }
   auto mark = [&](int v) {
     const int cg = v / V;
-    const int bit = (cg / TPA) * V + (v - cg * V);
-    if (cg % TPA == gl) {
+    const int c = cg / TPA;
+    const int bit = c * V + (v - cg * V);
+    if (cg - c * TPA == gl) {
+      uint32_t w = 0u;
 #pragma unroll
-      for (int q = 0; q < MW; ++q)
-        if (q == (bit >> 5)) vis[q] |= 1u << (bit & 31);
+      for (int q = 0; q < MW; ++q) {
+        if (q == (bit >> 5)) {
+          vis[q] |= 1u << (bit & 31);
+          w = vis[q];
+        }
+      }
+      const int sh = (c * V) & 31;
+      if (((w >> sh) & CMASK) == CMASK) fullm |= 1ull << c;
     }
+  };
+  auto nibble = [&](int bp) {  // visited bits of the 4-column group at bit bp
+    uint32_t w = 0u;
+#pragma unroll
+    for (int q = 0; q < MW; ++q)
+      if (q == (bp >> 5)) w = vis[q];
+    return (w >> (bp & 31)) & 0xFu;
   };
 
   int cur = start_city(key, it, (uint32_t)k, n);
@@ -167,39 +192,49 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
 
     // 1. stage the row: every chunk with an unvisited column, 16 bytes each
 #pragma unroll
-    for (int c = 0; c < KC; ++c) {
-      const bool full = ((vis[(c * V) >> 5] >> ((c * V) & 31)) & CMASK) == CMASK;
-      cp_async16_pred(srow + c * TPA + gl, reinterpret_cast<const uint4*>(row) + (c * TPA + gl), !full);
-    }
+    for (int c = 0; c < KC; ++c)
+      cp_async16_pred(srow + c * TPA + gl, reinterpret_cast<const uint4*>(row) + (c * TPA + gl),
+                      !((fullm >> c) & 1ull));
     cp_async_wait_all();  // this thread's copies only: it reads nothing else
 
-    // 2. per group: raw maximum packed with the group index; the thread's top group
+    // 2. per group: raw maximum packed with the group index (-1: nothing unvisited);
+    //    the thread's two largest keys, in NA independent accumulators
     int gkey[NG];
-    int top = -1;
+    int a1[NA], a2[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) a1[q] = a2[q] = -1;
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
+      const bool full = (fullm >> c) & 1ull;
+      const uint4 d = full ? make_uint4(0u, 0u, 0u, 0u) : srow[c * TPA + gl];
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int gi = c * G + g;
-        const int bp = c * V + g * 4;
-        const bool empty = ((vis[bp >> 5] >> (bp & 31)) & 0xFu) == 0xFu;
-        const uint32_t mb = E::group_max_bits(srow[c * TPA + gl], g);
+        bool empty = full;
+        if (G > 1) {
+          const int bp = c * V + g * 4;
+          empty = ((vis[bp >> 5] >> (bp & 31)) & 0xFu) == 0xFu;
+        }
+        const uint32_t mb = E::group_max_bits(d, g);
         const int kk = empty ? -1 : (int)((mb & ~0xFFu) | (uint32_t)(0xFF - gi));
         gkey[gi] = kk;
-        top = max(top, kk);
+        const int q = gi % NA;
+        a2[q] = max(a2[q], min(a1[q], kk));
+        a1[q] = max(a1[q], kk);
       }
+    }
+    int top = a1[0], second = a2[0];
+#pragma unroll
+    for (int q = 1; q < NA; ++q) {
+      second = max(max(second, a2[q]), min(top, a1[q]));
+      top = max(top, a1[q]);
     }
 
     float bs = -1.0f;
     int bj = 0x7FFFFFFF;
     auto score_group = [&](int gi) {
       const int c = gi / G, g = gi - c * G;
-      const int bp = c * V + g * 4;
-      uint32_t w = 0u;
-#pragma unroll
-      for (int q = 0; q < MW; ++q)
-        if (q == (bp >> 5)) w = vis[q];
-      const uint32_t nib = (w >> (bp & 31)) & 0xFu;
+      const uint32_t nib = nibble(c * V + g * 4);
       if (nib == 0xFu) return;
       const int j0 = (c * TPA + gl) * V + g * 4;
       const float4 p = E::group_values(srow[c * TPA + gl], g);
@@ -213,44 +248,49 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
     // 3. exact score of the top group; the warp's best exact score is the threshold
     const int top_gi = top >= 0 ? 0xFF - (top & 0xFF) : -1;
     if (top_gi >= 0) score_group(top_gi);
-    float thr = bs;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) thr = fmaxf(thr, __shfl_xor_sync(ACO_FULL_MASK, thr, off));
-    const int thr_key = thr >= 0.0f ? (int)(__float_as_uint(thr) & ~0xFFu) : 0;
+    const uint32_t thr_bits = __reduce_max_sync(ACO_FULL_MASK, bs >= 0.0f ? __float_as_uint(bs) : 0u);
+    const int thr_key = (int)(thr_bits & ~0xFFu);
 
-    // 4. groups that can still reach the threshold
-    uint64_t surv = 0ull;
+    // 4. other groups that can still reach the threshold (only if some thread's
+    //    second-largest key reaches it)
+    if (__any_sync(ACO_FULL_MASK, second >= thr_key)) {
+      uint64_t surv = 0ull;
+      if (second >= thr_key) {
 #pragma unroll
-    for (int gi = 0; gi < NG; ++gi)
-      if (gkey[gi] >= thr_key && gi != top_gi) surv |= 1ull << gi;
-    while (__any_sync(ACO_FULL_MASK, surv != 0ull)) {
-      if (surv) {
-        const int gi = __ffsll((long long)surv) - 1;
-        surv &= surv - 1ull;
-        score_group(gi);
+        for (int gi = 0; gi < NG; ++gi)
+          if (gkey[gi] >= thr_key && gi != top_gi) surv |= 1ull << gi;
+      }
+      while (__any_sync(ACO_FULL_MASK, surv != 0ull)) {
+        if (surv) {
+          const int gi = __ffsll((long long)surv) - 1;
+          surv &= surv - 1ull;
+          score_group(gi);
+        }
       }
     }
 
-    // 5. argmax across the warp, then across the ant's warps
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float os = __shfl_xor_sync(ACO_FULL_MASK, bs, off);
-      const int oj = __shfl_xor_sync(ACO_FULL_MASK, bj, off);
-      better(os, oj, bs, bj);
-    }
+    // 5. argmax across the warp (largest score, then lowest index), then across warps
+    uint32_t wkey = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
+    int next = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == wkey ? (uint32_t)bj : 0x7FFFFFFFu);
     if (W > 1) {
       if (lane == 0) {
-        red_s[t & 1][wi] = bs;
-        red_j[t & 1][wi] = bj;
+        red_s[t & 1][wi] = wkey;
+        red_j[t & 1][wi] = next;
       }
       __syncthreads();
-      bs = red_s[t & 1][0];
-      bj = red_j[t & 1][0];
+      wkey = red_s[t & 1][0];
+      next = red_j[t & 1][0];
 #pragma unroll
-      for (int w = 1; w < W; ++w) better(red_s[t & 1][w], red_j[t & 1][w], bs, bj);
+      for (int w = 1; w < W; ++w) {
+        const uint32_t ok = red_s[t & 1][w];
+        const int oj = red_j[t & 1][w];
+        if (ok > wkey || (ok == wkey && oj < next)) {
+          wkey = ok;
+          next = oj;
+        }
+      }
     }
 
-    const int next = bj;
     if (next < 0 || next >= n) {  // no unvisited city found: cannot happen for valid input
       if (gl == 0 && err) atomicExch(err, 1);
       break;

@@ -133,27 +133,35 @@ __global__ void __launch_bounds__(256) tour_length_kernel(const double* __restri
                                                           int m, float Q, double* __restrict__ L,
                                                           double* __restrict__ c,
                                                           int32_t* __restrict__ nbr) {
+  constexpr int U = 4;  // edge batches of 32 gathered before their sums
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (k >= m) return;
   const int32_t* p = tours + (size_t)k * n;
   double s = 0.0;
-  for (int base = 0; base < n; base += 32) {
-    const int t = base + lane;
-    double d = 0.0;
-    if (t < n) {
-      const int a = p[t];
-      const int b = p[t + 1 < n ? t + 1 : 0];
-      const int pr = p[t > 0 ? t - 1 : n - 1];
-      // tours come from the construction kernel; an entry out of range (only
-      // after a failed construction, which the host reports) is skipped
-      if ((unsigned)a < (unsigned)n && (unsigned)b < (unsigned)n) {
-        d = __ldg(D + (size_t)a * n + b);
-        if (nbr) reinterpret_cast<int2*>(nbr)[(size_t)a * m + k] = make_int2(pr, b);
+  for (int base = 0; base < n; base += 32 * U) {
+    double d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * 32 + lane;
+      d[u] = 0.0;
+      if (t < n) {
+        const int a = p[t];
+        const int b = p[t + 1 < n ? t + 1 : 0];
+        const int pr = p[t > 0 ? t - 1 : n - 1];
+        // tours come from the construction kernel; an entry out of range (only
+        // after a failed construction, which the host reports) is skipped
+        if ((unsigned)a < (unsigned)n && (unsigned)b < (unsigned)n) {
+          d[u] = __ldg(D + (size_t)a * n + b);
+          if (nbr) reinterpret_cast<int2*>(nbr)[(size_t)a * m + k] = make_int2(pr, b);
+        }
       }
     }
-    const int cnt = min(32, n - base);
-    for (int q = 0; q < cnt; ++q) s = __dadd_rn(s, __shfl_sync(ACO_FULL_MASK, d, q));
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int cnt = min(32, n - (base + u * 32));
+      for (int q = 0; q < cnt; ++q) s = __dadd_rn(s, __shfl_sync(ACO_FULL_MASK, d[u], q));
+    }
   }
   if (lane == 0) {
     L[k] = s;
@@ -234,7 +242,7 @@ __global__ void __launch_bounds__(32) deposit_kernel(float* __restrict__ tau, in
   extern __shared__ __align__(16) unsigned char smem[];
   double* delta = reinterpret_cast<double*>(smem);              // [tile]
   double* cs = delta + tile;                                    // [kDepAntChunk]
-  int32_t* items = reinterpret_cast<int32_t*>(cs + kDepAntChunk);  // [2 * kDepAntChunk]
+  int2* items = reinterpret_cast<int2*>(cs + kDepAntChunk);     // [kDepAntChunk]
   const int a = blockIdx.x;
   const int lane = threadIdx.x;
   float* row = tau + (size_t)a * ld;
@@ -245,15 +253,21 @@ __global__ void __launch_bounds__(32) deposit_kernel(float* __restrict__ tau, in
     for (int kb = 0; kb < m; kb += kDepAntChunk) {
       const int cnt = min(kDepAntChunk, m - kb);
       __syncwarp();
-      const int32_t* src = nbr + ((size_t)a * m + kb) * 2;
-      for (int q = lane; q < 2 * cnt; q += 32) items[q] = src[q];
-      for (int q = lane; q < cnt; q += 32) cs[q] = c[kb + q];
+      const int2* src = reinterpret_cast<const int2*>(nbr) + ((size_t)a * m + kb);
+#pragma unroll 4
+      for (int q = lane; q < cnt; q += 32) {
+        items[q] = __ldg(src + q);
+        cs[q] = __ldg(c + kb + q);
+      }
       __syncwarp();
       for (int k0 = 0; k0 < cnt; k0 += 16) {
         const int ai = lane & 15;  // ant k0 + ai
-        const int side = lane >> 4;
         const bool valid = k0 + ai < cnt;
-        int b = valid ? items[2 * (k0 + ai) + side] - col0 : -1;
+        int b = -1;
+        if (valid) {
+          const int2 it = items[k0 + ai];
+          b = (lane >> 4 ? it.y : it.x) - col0;
+        }
         const bool in_tile = valid && b >= 0 && b < cols;
         const int key = in_tile ? b : -1 - lane;  // unique keys for idle lanes
         const unsigned grp = __match_any_sync(ACO_FULL_MASK, key);
@@ -261,21 +275,34 @@ __global__ void __launch_bounds__(32) deposit_kernel(float* __restrict__ tau, in
           const unsigned ants = (grp & 0xFFFFu) | (grp >> 16);
           const int lead = __ffs(ants) - 1;
           if (lead == ai) {
-            double s = delta[b];
+            double sum = delta[b];
             unsigned rest = ants;
             while (rest) {
               const int i = __ffs(rest) - 1;
               rest &= rest - 1u;
-              s = __dadd_rn(s, cs[k0 + i]);
+              sum = __dadd_rn(sum, cs[k0 + i]);
             }
-            delta[b] = s;
+            delta[b] = sum;
           }
         }
         __syncwarp();
       }
     }
     __syncwarp();
-    for (int q = lane; q < cols; q += 32) {
+    // tau_ab <- fl32(fl64(keep * tau_ab) + Delta_ab), four columns per lane step
+    const int nv = cols >> 2;
+    float4* row4 = reinterpret_cast<float4*>(row + col0);
+#pragma unroll 4
+    for (int q = lane; q < nv; q += 32) {
+      float4 v = row4[q];
+      const double* dl = delta + 4 * q;
+      v.x = __double2float_rn(__dadd_rn(__dmul_rn(keep, (double)v.x), dl[0]));
+      v.y = __double2float_rn(__dadd_rn(__dmul_rn(keep, (double)v.y), dl[1]));
+      v.z = __double2float_rn(__dadd_rn(__dmul_rn(keep, (double)v.z), dl[2]));
+      v.w = __double2float_rn(__dadd_rn(__dmul_rn(keep, (double)v.w), dl[3]));
+      row4[q] = v;
+    }
+    for (int q = 4 * nv + lane; q < cols; q += 32) {
       const int j = col0 + q;
       row[j] = __double2float_rn(__dadd_rn(__dmul_rn(keep, (double)row[j]), delta[q]));
     }
@@ -375,7 +402,8 @@ int launch_best(const double* L, const int32_t* tours, int n, int m, int32_t* be
 
 int deposit_tile(int n) {
   // fp64 delta tile + per-chunk c and items must fit the 227 KB opt-in limit
-  const int max_tile = (200 * 1024 - kDepAntChunk * 16) / 8;
+  // (a multiple of 4 so that every tile's columns start 16-byte aligned)
+  const int max_tile = ((200 * 1024 - kDepAntChunk * 16) / 8) & ~3;
   return n < max_tile ? n : max_tile;
 }
 

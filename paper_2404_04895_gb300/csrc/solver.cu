@@ -243,8 +243,10 @@ static int enqueue_iteration(aco_solver* s) {
   const int n = p.n, m = p.m;
   cudaStream_t st = s->stream;
   const int n_sched = std::min(p.gamma_T + 1, kSchedCap);
+  // External records become event nodes of the captured graph, so the probes
+  // time every replay of it (a plain record only orders captured work).
   auto probe = [&](int q) {
-    if (s->profiling) cudaEventRecord(s->ev[q], st);
+    if (s->profiling) cudaEventRecordWithFlags(s->ev[q], st, cudaEventRecordExternal);
   };
   probe(0);
   int rc = launch_build_P(s->tau, s->H, n, s->ld, p.alpha, 1.0f,
