@@ -226,6 +226,25 @@ int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const 
 int aco_op_deposit_atomic(float* tau_dev, int n, int ld, const int32_t* tours_dev,
                           const double* c_dev, int m, float rho, void* stream);
 
+/* Allocation-free tour lengths + deterministic deposit.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory where
+ * they update the pheromone (inside CUDA stream capture, in loops that must
+ * not block on the allocator, or under a framework-owned memory pool).
+ * Same results as aco_op_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c, nbr)
+ * followed by aco_op_deposit(tau_dev, n, ld, nbr, c, m, rho), but the scratch
+ * c (m fp64) and nbr (2*n*m int32) lives in a fixed device array inside the
+ * library of ACO_NOALLOC_SCRATCH_BYTES (16 MiB; every GPU that loads the
+ * library holds it until exit), so 8*m (rounded up to 256) + 8*n*m must fit:
+ * larger n*m returns ACO_ERR_ARG.  Inputs/outputs as for the two calls above;
+ * L_dev (m fp64) receives the lengths, tau_dev is updated in place.
+ * Allocates nothing.  Its first call on a device looks up the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race. */
+#define ACO_NOALLOC_SCRATCH_BYTES (16u << 20)
+int aco_op_deposit_tours_noalloc(float* tau_dev, int n, int ld, const double* D_dev,
+                                 const int32_t* tours_dev, int m, float rho, float Q,
+                                 double* L_dev, void* stream);
+
 /* Autotuner: times every compiled construct shape that covers n on the
  * given M_p (reps launches each, after one warm-up) and registers the fastest
  * as the default for (n, m, prec) in this process.  tours_scratch_dev: m x n

@@ -75,6 +75,7 @@ _SIGS = {
     "aco_op_best": (i32, [v, v, i32, i32, v, v, v]),
     "aco_op_deposit": (i32, [v, i32, i32, v, v, i32, f32, v]),
     "aco_op_deposit_atomic": (i32, [v, i32, i32, v, v, i32, f32, v]),
+    "aco_op_deposit_tours_noalloc": (i32, [v, i32, i32, v, v, i32, f32, f32, v, v]),
     "aco_op_philox": (i32, [v, u64, v, i32, v]),
     "aco_op_pow_own": (i32, [v, f32, v, i32, v]),
     "aco_gamma": (f32, [i32, i32, f32, f32]),
@@ -168,6 +169,14 @@ def op_deposit(tau, n, ld, nbr, c, m, rho, stream=None):
 
 def op_deposit_atomic(tau, n, ld, tours, c, m, rho, stream=None):
     call("aco_op_deposit_atomic", ptr(tau), n, ld, ptr(tours), ptr(c), m, rho, stream_ptr(stream))
+
+
+def op_deposit_tours_noalloc(tau, n, ld, D, tours, m, rho, Q, L, stream=None):
+    call("aco_op_deposit_tours_noalloc", ptr(tau), n, ld, ptr(D), ptr(tours), m, rho, Q, ptr(L),
+         stream_ptr(stream))
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 def op_philox(ctr, seed, out, count, stream=None):
