@@ -252,7 +252,7 @@ def run_native(args, w, dist):
 
     tuned = {}
     for prec in ([w["prec"]] if args.no_variants else ["fp32", "bf16", "fp16"]):
-        tuned[prec] = ((0, 0), None) if args.no_autotune else autotune(B, torch, w, coords, prec, seed)
+        tuned[prec] = ((0, 0, 0), None) if args.no_autotune else autotune(B, torch, w, coords, prec, seed)
     dist.barrier()
     clk = ClockSampler(dist.local)
     torch.cuda.synchronize()
@@ -280,7 +280,8 @@ def run_native(args, w, dist):
                 "kernel": "construct_kernel", "algorithmic_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": round(construct_ms, 4), "kernel_source_hash": khash}
     roofline["construct_shape"] = {"warps_per_ant": tuned[w["prec"]][0][0],
-                                   "chunks_per_lane": tuned[w["prec"]][0][1]}
+                                   "chunks_per_lane": tuned[w["prec"]][0][1],
+                                   "mode": ["staged", "direct"][tuned[w["prec"]][0][2]]}
     kernel_ms = dict(zip(["build_P", "construct", "tour_length", "best", "deposit"],
                          [round(x / args.steps, 4) for x in kern]))
 

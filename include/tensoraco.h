@@ -163,10 +163,10 @@ int aco_solver_iteration(aco_solver* s, uint32_t* it);
 int aco_solver_set_profiling(aco_solver* s, int on);
 int aco_solver_kernel_ms(aco_solver* s, float* ms5);
 
-/* Choose the construct launch shape for this solver: warps = chunks = 0
- * restores the default (autotuned if aco_autotune_construct ran for its
- * n, m and precision). */
-int aco_solver_set_shape(aco_solver* s, int warps, int chunks);
+/* Choose the construct launch shape (warps, chunks, mode as for
+ * aco_op_construct_shape) for this solver: warps = chunks = 0 restores the
+ * default (autotuned if aco_autotune_construct ran for its n, m and precision). */
+int aco_solver_set_shape(aco_solver* s, int warps, int chunks, int mode);
 
 /* ======================================================================
  * Step-level API on caller-owned device buffers (one kernel family each),
@@ -196,12 +196,13 @@ int aco_op_build_P(const float* tau_dev, const float* H_dev, int n, int ld, int 
 int aco_op_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed,
                      uint32_t it, int32_t* tours_dev, int32_t* err_dev, void* stream);
 
-/* Same, with an explicit launch shape: warps per ant and 16-byte chunks per
- * lane (32*warps*chunks*(16/elem bytes) >= n).  ACO_ERR_UNSUPPORTED when the
- * shape is not compiled in.  Used by the autotuner. */
+/* Same, with an explicit launch shape: warps per ant, 16-byte chunks per
+ * lane (32*warps*chunks*(16/elem bytes) >= n) and mode (0: the row is staged
+ * in shared memory by cp.async, 1: direct register loads).  warps = 0 picks
+ * the default.  ACO_ERR_UNSUPPORTED when the shape is not compiled in. */
 int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed,
                            uint32_t it, int32_t* tours_dev, int32_t* err_dev, int warps,
-                           int chunks, void* stream);
+                           int chunks, int mode, void* stream);
 
 /* Eq. 3 and the index mapping of Eq. 2: L_k = sum_t D[p_t][p_{t+1 mod n}] in
  * fp64 in t order (L_dev, m), c_k = fl64(Q / L_k) (c_dev, m), and for every
@@ -251,7 +252,7 @@ int aco_op_deposit_tours_noalloc(float* tau_dev, int n, int ld, const double* D_
  * int32.  Outputs the chosen shape and its mean time in ms (nullable). */
 int aco_autotune_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed,
                            int32_t* tours_scratch_dev, int reps, int* warps_out, int* chunks_out,
-                           float* ms_out, void* stream);
+                           int* mode_out, float* ms_out, void* stream);
 
 /* Test utilities: Philox4x32-10 blocks for count counters (ctr_dev 4*count
  * u32, out_dev 4*count u32) under key (seed lo, hi); and the device pow_own

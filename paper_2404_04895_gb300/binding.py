@@ -63,14 +63,14 @@ _SIGS = {
     "aco_solver_iteration": (i32, [v, C.POINTER(u32)]),
     "aco_solver_set_profiling": (i32, [v, i32]),
     "aco_solver_kernel_ms": (i32, [v, v]),
-    "aco_solver_set_shape": (i32, [v, i32, i32]),
+    "aco_solver_set_shape": (i32, [v, i32, i32, i32]),
     "aco_autotune_construct": (i32, [v, i32, i32, i32, i32, u64, v, i32, C.POINTER(i32),
-                                     C.POINTER(i32), C.POINTER(f32), v]),
+                                     C.POINTER(i32), C.POINTER(i32), C.POINTER(f32), v]),
     "aco_op_heuristic": (i32, [v, i32, i32, v, v, i32, v]),
     "aco_op_fill": (i32, [v, i32, i32, f32, v]),
     "aco_op_build_P": (i32, [v, v, i32, i32, i32, f32, i32, v, v]),
     "aco_op_construct": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, v]),
-    "aco_op_construct_shape": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, i32, i32, v]),
+    "aco_op_construct_shape": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, i32, i32, i32, v]),
     "aco_op_tour_length": (i32, [v, i32, v, i32, f32, v, v, v, v]),
     "aco_op_best": (i32, [v, v, i32, i32, v, v, v]),
     "aco_op_deposit": (i32, [v, i32, i32, v, v, i32, f32, v]),
@@ -152,7 +152,7 @@ def op_construct(P, prec, n, ld, m, seed, it, tours, err=None, shape=None, strea
         call("aco_op_construct", ptr(P), prec, n, ld, m, seed, it, ptr(tours), ptr(err), stream_ptr(stream))
     else:
         call("aco_op_construct_shape", ptr(P), prec, n, ld, m, seed, it, ptr(tours), ptr(err),
-             shape[0], shape[1], stream_ptr(stream))
+             shape[0], shape[1], shape[2], stream_ptr(stream))
 
 
 def op_tour_length(D, n, tours, m, Q, L, c=None, nbr=None, stream=None):
@@ -188,10 +188,10 @@ def op_pow_own(x, e, out, count, stream=None):
 
 
 def autotune_construct(P, prec, n, ld, m, seed, tours_scratch, reps=3, stream=None):
-    w, c, ms = i32(0), i32(0), f32(0)
+    w, c, md, ms = i32(0), i32(0), i32(0), f32(0)
     call("aco_autotune_construct", ptr(P), prec, n, ld, m, seed, ptr(tours_scratch), reps,
-         C.byref(w), C.byref(c), C.byref(ms), stream_ptr(stream))
-    return (w.value, c.value), ms.value
+         C.byref(w), C.byref(c), C.byref(md), C.byref(ms), stream_ptr(stream))
+    return (w.value, c.value, md.value), ms.value
 
 
 def gamma(it, T, gmax, gmin):
@@ -296,8 +296,8 @@ class Solver:
         call("aco_solver_kernel_ms", self._h, out.ctypes.data)
         return out
 
-    def set_shape(self, warps=0, chunks=0):
-        call("aco_solver_set_shape", self._h, warps, chunks)
+    def set_shape(self, warps=0, chunks=0, mode=0):
+        call("aco_solver_set_shape", self._h, warps, chunks, mode)
         return self
 
     def close(self):

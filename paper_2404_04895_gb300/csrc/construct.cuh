@@ -39,6 +39,15 @@ __device__ __forceinline__ void cp_async16_pred(void* smem_dst, const void* gmem
       "l"(gmem_src), "r"((int)pred)
       : "memory");
 }
+// 16-byte read-only load into `v`, issued only when `pred` holds; otherwise v
+// keeps its previous contents (no zeroing instructions).
+__device__ __forceinline__ void ldg_pred_keep(uint4& v, const uint4* ptr, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %5, 0;\n\t"
+      "@p ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
+      : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
+      : "l"(ptr), "r"((int)pred));
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
@@ -53,7 +62,10 @@ struct Elem<ACO_FP32> {
   // fp32 bits of the largest element of group g (4 elements) of chunk d;
   // elements are >= 0, so unsigned order is numeric order.
   __device__ __forceinline__ static uint32_t group_max_bits(const uint4& d, int) {
-    return max(max(d.x, d.y), max(d.z, d.w));
+    return max(__vimax3_u32(d.x, d.y, d.z), d.w);
+  }
+  __device__ __forceinline__ static float4 load_group(const char* row, int j0) {
+    return __ldg(reinterpret_cast<const float4*>(row) + (j0 >> 2));
   }
   // the 4 values of group g of a 16-byte chunk
   __device__ __forceinline__ static float4 group_values(const uint4& d, int) {
@@ -82,6 +94,10 @@ struct Elem<ACO_BF16> {
     return make_float4(__uint_as_float(a << 16), __uint_as_float(a & 0xFFFF0000u),
                        __uint_as_float(b << 16), __uint_as_float(b & 0xFFFF0000u));
   }
+  __device__ __forceinline__ static float4 load_group(const char* row, int j0) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(row) + (j0 >> 2));
+    return group_values(make_uint4(v.x, v.y, 0u, 0u), 0);
+  }
 };
 
 template <>
@@ -99,6 +115,10 @@ struct Elem<ACO_FP16> {
     const uint32_t a = g == 0 ? d.x : d.z, b = g == 0 ? d.y : d.w;
     return make_float4(h2f(a), h2f(a >> 16), h2f(b), h2f(b >> 16));
   }
+  __device__ __forceinline__ static float4 load_group(const char* row, int j0) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(row) + (j0 >> 2));
+    return group_values(make_uint4(v.x, v.y, 0u, 0u), 0);
+  }
 };
 
 // Running argmax update with the lowest-index tie-break.
@@ -115,7 +135,16 @@ __device__ __forceinline__ uint32_t score_key(float bs) {
   return bs >= 0.0f ? __float_as_uint(bs) + 1u : 0u;
 }
 
-template <int PREC, int W, int KC>
+// MODE_STAGED: a step's chunks go global -> shared memory by cp.async (all in
+// flight regardless of registers; suits many chunks per thread).
+// MODE_DIRECT: a step's chunks go straight into registers by predicated 16-byte
+// loads (no shared-memory round trip; suits <= 12 chunks per thread, which
+// the compiler keeps in flight together); the exact scorer re-reads its 16 or
+// 8 bytes through L1.
+constexpr int MODE_STAGED = 0;
+constexpr int MODE_DIRECT = 1;
+
+template <int PREC, int W, int KC, int MODE>
 __global__ void __launch_bounds__(32 * W) construct_kernel(
     const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it_arg,
     const uint32_t* __restrict__ it_dev, int32_t* __restrict__ tours, int32_t* __restrict__ err) {
@@ -125,11 +154,10 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
   constexpr int NG = KC * G;              // groups per thread
   constexpr int MW = (KC * V + 31) / 32;  // visited-bit words per thread
   constexpr int TPA = 32 * W;             // threads per ant
-  constexpr uint32_t CMASK = (1u << V) - 1u;
+  constexpr uint64_t GMASK = (1ull << G) - 1ull;
   constexpr int NA = NG < 4 ? NG : 4;     // independent accumulators for the top-2 keys
-  static_assert(NG <= 64, "survivor mask is 64 bits");
+  static_assert(NG <= 64, "group masks are 64 bits");
   static_assert(NG <= 255, "group index packs into 8 bits");
-  static_assert(KC <= 64, "full-chunk mask is 64 bits");
 
   const int k = blockIdx.x;
   if (k >= m) return;
@@ -142,11 +170,12 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
 
   __shared__ uint32_t red_s[2][W];
   __shared__ int red_j[2][W];
-  extern __shared__ __align__(16) uint4 srow[];  // [KC * TPA] chunks of the current row
+  extern __shared__ __align__(16) uint4 srow[];  // MODE_STAGED: [KC * TPA] chunks of the row
 
-  // visited bits: bit c*V + e  <->  column (c*TPA + gl)*V + e; fullm bit c: chunk c done
+  // visited bits: bit c*V + e  <->  column (c*TPA + gl)*V + e;
+  // emptym bit gi: all 4 columns of group gi visited
   uint32_t vis[MW];
-  uint64_t fullm = 0ull;
+  uint64_t emptym = 0ull;
 #pragma unroll
   for (int q = 0; q < MW; ++q) vis[q] = 0u;
 #pragma unroll
@@ -156,7 +185,9 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
     for (int e = 0; e < V; ++e) {
       if (j0 + e >= n) vis[(c * V + e) >> 5] |= 1u << ((c * V + e) & 31);
     }
-    if (j0 + V - 1 >= n && j0 >= n) fullm |= 1ull << c;
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (j0 + 4 * g >= n) emptym |= 1ull << (c * G + g);
   }
   auto mark = [&](int v) {
     const int cg = v / V;
@@ -171,8 +202,7 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
           w = vis[q];
         }
       }
-      const int sh = (c * V) & 31;
-      if (((w >> sh) & CMASK) == CMASK) fullm |= 1ull << c;
+      if (((w >> (bit & 28)) & 0xFu) == 0xFu) emptym |= 1ull << (bit >> 2);
     }
   };
   auto nibble = [&](int bp) {  // visited bits of the 4-column group at bit bp
@@ -187,15 +217,28 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
   if (gl == 0) tours[(size_t)k * n] = cur;
   mark(cur);
 
+  uint4 d[KC];  // MODE_DIRECT: the thread's chunks of the current row
+#pragma unroll
+  for (int c = 0; c < KC; ++c) d[c] = make_uint4(0u, 0u, 0u, 0u);
+
   for (int t = 1; t < n; ++t) {
     const char* __restrict__ row = P + (size_t)cur * row_bytes;
+    const uint4* __restrict__ row4 = reinterpret_cast<const uint4*>(row);
 
-    // 1. stage the row: every chunk with an unvisited column, 16 bytes each
+    // 1. fetch every chunk with an unvisited column, 16 bytes each
+    if (MODE == MODE_DIRECT) {
 #pragma unroll
-    for (int c = 0; c < KC; ++c)
-      cp_async16_pred(srow + c * TPA + gl, reinterpret_cast<const uint4*>(row) + (c * TPA + gl),
-                      !((fullm >> c) & 1ull));
-    cp_async_wait_all();  // this thread's copies only: it reads nothing else
+      for (int c = 0; c < KC; ++c)
+        ldg_pred_keep(d[c], row4 + (c * TPA + gl), ((emptym >> (c * G)) & GMASK) != GMASK);
+    } else {
+#pragma unroll
+      for (int c = 0; c < KC; ++c)
+        cp_async16_pred(srow + c * TPA + gl, row4 + (c * TPA + gl),
+                        ((emptym >> (c * G)) & GMASK) != GMASK);
+      cp_async_wait_all();  // this thread's copies only: it reads nothing else
+#pragma unroll
+      for (int c = 0; c < KC; ++c) d[c] = srow[c * TPA + gl];
+    }
 
     // 2. per group: raw maximum packed with the group index (-1: nothing unvisited);
     //    the thread's two largest keys, in NA independent accumulators
@@ -205,17 +248,11 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
     for (int q = 0; q < NA; ++q) a1[q] = a2[q] = -1;
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-      const bool full = (fullm >> c) & 1ull;
-      const uint4 d = full ? make_uint4(0u, 0u, 0u, 0u) : srow[c * TPA + gl];
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int gi = c * G + g;
-        bool empty = full;
-        if (G > 1) {
-          const int bp = c * V + g * 4;
-          empty = ((vis[bp >> 5] >> (bp & 31)) & 0xFu) == 0xFu;
-        }
-        const uint32_t mb = E::group_max_bits(d, g);
+        const bool empty = (emptym >> gi) & 1ull;
+        const uint32_t mb = E::group_max_bits(d[c], g);
         const int kk = empty ? -1 : (int)((mb & ~0xFFu) | (uint32_t)(0xFF - gi));
         gkey[gi] = kk;
         const int q = gi % NA;
@@ -237,7 +274,8 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
       const uint32_t nib = nibble(c * V + g * 4);
       if (nib == 0xFu) return;
       const int j0 = (c * TPA + gl) * V + g * 4;
-      const float4 p = E::group_values(srow[c * TPA + gl], g);
+      const float4 p = MODE == MODE_DIRECT ? E::load_group(row, j0)
+                                           : E::group_values(srow[c * TPA + gl], g);
       const uint4 x = philox(make_uint4((uint32_t)(j0 >> 2), (uint32_t)t, (uint32_t)k, it), key);
       if (!(nib & 1u)) better(__fmul_rn(uniform01(x.x), p.x), j0, bs, bj);
       if (!(nib & 2u)) better(__fmul_rn(uniform01(x.y), p.y), j0 + 1, bs, bj);
@@ -303,23 +341,24 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
 
 // Host launcher body for one precision: dispatch over the compiled shapes.
 // The row buffer is KC * 32 * W * 16 bytes of dynamic shared memory.
-#define ACO_CONSTRUCT_CASE(PREC, W, KC)                                                    \
-  if (warps == W && chunks == KC) {                                                        \
-    construct_kernel<PREC, W, KC><<<m, 32 * W, (size_t)KC * 32 * W * 16, st>>>(             \
-        P, n, ld, m, key, it, it_dev, tours, err);                                         \
-    const cudaError_t e_ = cudaGetLastError();                                             \
-    return e_ == cudaSuccess ? ACO_OK : cuda_error(e_, "construct_kernel launch");         \
+#define ACO_CONSTRUCT_CASE(PREC, W, KC, MODE)                                              \
+  if (warps == W && chunks == KC && mode == MODE) {                                         \
+    const size_t smem_ = MODE == MODE_STAGED ? (size_t)KC * 32 * W * 16 : 0;                 \
+    construct_kernel<PREC, W, KC, MODE><<<m, 32 * W, smem_, st>>>(P, n, ld, m, key, it, it_dev, \
+                                                                  tours, err);              \
+    const cudaError_t e_ = cudaGetLastError();                                              \
+    return e_ == cudaSuccess ? ACO_OK : cuda_error(e_, "construct_kernel launch");          \
   }
 
 }  // namespace aco
 
 namespace aco {
 // Opt every compiled shape in to its dynamic shared-memory size (once).
-#define ACO_CONSTRUCT_PREPARE(PREC, W, KC)                                                  \
-  {                                                                                        \
-    const cudaError_t e_ = cudaFuncSetAttribute(construct_kernel<PREC, W, KC>,             \
+#define ACO_CONSTRUCT_PREPARE(PREC, W, KC, MODE)                                           \
+  if (MODE == MODE_STAGED) {                                                                 \
+    const cudaError_t e_ = cudaFuncSetAttribute(construct_kernel<PREC, W, KC, MODE>,         \
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                KC * 32 * W * 16);                          \
-    if (e_ != cudaSuccess) return cuda_error(e_, "cudaFuncSetAttribute(construct_kernel)"); \
+                                                KC * 32 * W * 16);                           \
+    if (e_ != cudaSuccess) return cuda_error(e_, "cudaFuncSetAttribute(construct_kernel)");  \
   }
 }  // namespace aco

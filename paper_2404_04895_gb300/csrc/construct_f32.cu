@@ -7,16 +7,16 @@ namespace aco {
 
 int launch_construct_f32(const float* P, int n, int ld, int m, uint2 key, uint32_t it,
                          const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
-                         int chunks, cudaStream_t st) {
-#define X(W, KC) ACO_CONSTRUCT_CASE(ACO_FP32, W, KC)
+                         int chunks, int mode, cudaStream_t st) {
+#define X(W, KC, MODE) ACO_CONSTRUCT_CASE(ACO_FP32, W, KC, MODE)
   ACO_SHAPES_4B(X)
 #undef X
-  return set_error(ACO_ERR_UNSUPPORTED, "construct shape (%d warps, %d chunks) not compiled for fp32",
-                   warps, chunks);
+  return set_error(ACO_ERR_UNSUPPORTED, "construct shape (%d warps, %d chunks, mode %d) not compiled for fp32",
+                   warps, chunks, mode);
 }
 
 int prepare_construct_f32() {
-#define X(W, KC) ACO_CONSTRUCT_PREPARE(ACO_FP32, W, KC)
+#define X(W, KC, MODE) ACO_CONSTRUCT_PREPARE(ACO_FP32, W, KC, MODE)
   ACO_SHAPES_4B(X)
 #undef X
   return ACO_OK;

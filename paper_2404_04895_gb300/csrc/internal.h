@@ -31,23 +31,25 @@ inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 struct ConstructShape {
   int warps;   // warps per ant
   int chunks;  // 16-byte chunks per lane
+  int mode;    // 0: row staged in shared memory by cp.async, 1: direct register loads
 };
 int construct_shapes(int elem_bytes, const ConstructShape** list);
-// Default shape for (n, m, elem_bytes): the narrowest warp count whose chunk
-// count is compiled in, unless an autotuned choice is registered.
+// Default shape for (n, m, elem_bytes) unless an autotuned choice is registered:
+// a direct-load shape with the fewest warps, then fewest chunks, that covers n;
+// a staged shape only when no direct shape covers n.
 ConstructShape default_construct_shape(int n, int m, int elem_bytes);
 void register_tuned_shape(int n, int m, int elem_bytes, ConstructShape s);
 
 // Kernel launchers (return ACO_OK or an error code; asynchronous).
 int launch_construct_f32(const float* P, int n, int ld, int m, uint2 key, uint32_t it,
                          const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
-                         int chunks, cudaStream_t st);
+                         int chunks, int mode, cudaStream_t st);
 int launch_construct_bf16(const void* P, int n, int ld, int m, uint2 key, uint32_t it,
                           const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
-                          int chunks, cudaStream_t st);
+                          int chunks, int mode, cudaStream_t st);
 int launch_construct_f16(const void* P, int n, int ld, int m, uint2 key, uint32_t it,
                          const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
-                         int chunks, cudaStream_t st);
+                         int chunks, int mode, cudaStream_t st);
 
 int prepare_construct_f32();
 int prepare_construct_bf16();

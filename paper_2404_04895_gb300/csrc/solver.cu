@@ -35,12 +35,12 @@ int cuda_error(cudaError_t e, const char* what) {
 
 // ------------------------------------------------------------------ shapes
 static const ConstructShape kShapes4[] = {
-#define X(W, KC) {W, KC},
+#define X(W, KC, MODE) {W, KC, MODE},
     ACO_SHAPES_4B(X)
 #undef X
 };
 static const ConstructShape kShapes2[] = {
-#define X(W, KC) {W, KC},
+#define X(W, KC, MODE) {W, KC, MODE},
     ACO_SHAPES_2B(X)
 #undef X
 };
@@ -74,12 +74,14 @@ ConstructShape default_construct_shape(int n, int m, int elem_bytes) {
   }
   const ConstructShape* list;
   const int cnt = construct_shapes(elem_bytes, &list);
-  ConstructShape best = {0, 0};
+  ConstructShape best = {0, 0, 0};
   for (int q = 0; q < cnt; ++q) {
-    if (shape_columns(list[q], elem_bytes) < n) continue;
-    if (best.warps == 0 || list[q].warps < best.warps ||
-        (list[q].warps == best.warps && list[q].chunks < best.chunks))
-      best = list[q];
+    const ConstructShape s = list[q];
+    if (shape_columns(s, elem_bytes) < n) continue;
+    const bool better = best.warps == 0 || s.mode > best.mode ||
+                        (s.mode == best.mode && (s.warps < best.warps ||
+                                                 (s.warps == best.warps && s.chunks < best.chunks)));
+    if (better) best = s;
   }
   return best;
 }
@@ -106,11 +108,11 @@ static int launch_construct(const void* P, int prec, int n, int ld, int m, uint2
   switch (prec) {
     case ACO_FP32:
       return launch_construct_f32(static_cast<const float*>(P), n, ld, m, key, it, it_dev, tours, err,
-                                  s.warps, s.chunks, st);
+                                  s.warps, s.chunks, s.mode, st);
     case ACO_BF16:
-      return launch_construct_bf16(P, n, ld, m, key, it, it_dev, tours, err, s.warps, s.chunks, st);
+      return launch_construct_bf16(P, n, ld, m, key, it, it_dev, tours, err, s.warps, s.chunks, s.mode, st);
     case ACO_FP16:
-      return launch_construct_f16(P, n, ld, m, key, it, it_dev, tours, err, s.warps, s.chunks, st);
+      return launch_construct_f16(P, n, ld, m, key, it, it_dev, tours, err, s.warps, s.chunks, s.mode, st);
   }
   return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
 }
@@ -530,26 +532,27 @@ int aco_solver_kernel_ms(aco_solver* s, float* ms5) {
   return ACO_OK;
 }
 
-int aco_solver_set_shape(aco_solver* s, int warps, int chunks) {
+int aco_solver_set_shape(aco_solver* s, int warps, int chunks, int mode) {
   if (!s) return set_error(ACO_ERR_ARG, "solver is NULL");
   if (warps || chunks) {
     const int eb = s->p.prec == ACO_FP32 ? 4 : 2;
     const ConstructShape* list;
     const int cnt = construct_shapes(eb, &list);
     bool found = false;
-    for (int q = 0; q < cnt; ++q) found |= list[q].warps == warps && list[q].chunks == chunks;
-    if (!found) return set_error(ACO_ERR_UNSUPPORTED, "shape (%d, %d) not compiled", warps, chunks);
-    if (shape_columns({warps, chunks}, eb) < s->p.n)
+    for (int q = 0; q < cnt; ++q)
+      found |= list[q].warps == warps && list[q].chunks == chunks && list[q].mode == mode;
+    if (!found) return set_error(ACO_ERR_UNSUPPORTED, "shape (%d, %d, %d) not compiled", warps, chunks, mode);
+    if (shape_columns({warps, chunks, mode}, eb) < s->p.n)
       return set_error(ACO_ERR_ARG, "shape (%d, %d) does not cover n=%d", warps, chunks, s->p.n);
   }
-  s->shape = {warps, chunks};
+  s->shape = {warps, chunks, mode};
   drop_graph(s);
   return ACO_OK;
 }
 
 int aco_autotune_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed,
                            int32_t* tours_scratch_dev, int reps, int* warps_out, int* chunks_out,
-                           float* ms_out, void* stream) {
+                           int* mode_out, float* ms_out, void* stream) {
   int rc = check_mat(P_dev, n, ld, "P");
   if (rc) return rc;
   if (!tours_scratch_dev || m < 1 || m > ACO_MAX_M || reps < 1) return set_error(ACO_ERR_ARG, "invalid argument");
@@ -564,7 +567,7 @@ int aco_autotune_construct(const void* P_dev, int prec, int n, int ld, int m, ui
   cudaEvent_t e0, e1;
   ACO_CUDA_TRY(cudaEventCreate(&e0));
   ACO_CUDA_TRY(cudaEventCreate(&e1));
-  ConstructShape best = {0, 0};
+  ConstructShape best = {0, 0, 0};
   float best_ms = 0.0f;
   for (int q = 0; q < cnt && rc == ACO_OK; ++q) {
     if (shape_columns(list[q], eb) < n) continue;
@@ -595,6 +598,7 @@ int aco_autotune_construct(const void* P_dev, int prec, int n, int ld, int m, ui
   register_tuned_shape(n, m, eb, best);
   if (warps_out) *warps_out = best.warps;
   if (chunks_out) *chunks_out = best.chunks;
+  if (mode_out) *mode_out = best.mode;
   if (ms_out) *ms_out = best_ms;
   return ACO_OK;
 }
@@ -741,7 +745,8 @@ int aco_op_build_P(const float* tau_dev, const float* H_dev, int n, int ld, int 
 }
 
 int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,
-                           int32_t* tours_dev, int32_t* err_dev, int warps, int chunks, void* stream) {
+                           int32_t* tours_dev, int32_t* err_dev, int warps, int chunks, int mode,
+                           void* stream) {
   int rc = check_mat(P_dev, n, ld, "P");
   if (rc) return rc;
   if (m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "m=%d outside [1, %d]", m, ACO_MAX_M);
@@ -749,14 +754,14 @@ int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, ui
   if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
   rc = prepare_kernels();
   if (rc) return rc;
-  ConstructShape s = {warps, chunks};
+  ConstructShape s = {warps, chunks, mode};
   return launch_construct(P_dev, prec, n, ld, m, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), it,
                           nullptr, tours_dev, err_dev, s, static_cast<cudaStream_t>(stream));
 }
 
 int aco_op_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,
                      int32_t* tours_dev, int32_t* err_dev, void* stream) {
-  return aco_op_construct_shape(P_dev, prec, n, ld, m, seed, it, tours_dev, err_dev, 0, 0, stream);
+  return aco_op_construct_shape(P_dev, prec, n, ld, m, seed, it, tours_dev, err_dev, 0, 0, 0, stream);
 }
 
 int aco_op_tour_length(const double* D_dev, int n, const int32_t* tours_dev, int m, float Q, double* L_dev,

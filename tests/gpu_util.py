@@ -9,11 +9,11 @@ from conftest import ROOT
 
 
 def shapes(elem_bytes):
-    """(warps, chunks) construct shapes compiled into the library."""
+    """(warps, chunks, mode) construct shapes compiled into the library."""
     text = open(os.path.join(ROOT, "paper_2404_04895_gb300", "csrc", "shapes.h")).read()
     name = "ACO_SHAPES_4B" if elem_bytes == 4 else "ACO_SHAPES_2B"
     body = text.split(f"#define {name}(X)")[1].split("\n\n")[0]
-    return [(int(a), int(b)) for a, b in re.findall(r"X\((\d+),\s*(\d+)\)", body)]
+    return [(int(a), int(b), int(c)) for a, b, c in re.findall(r"X\((\d+),\s*(\d+),\s*(\d+)\)", body)]
 
 
 def covers(shape, n, elem_bytes):
