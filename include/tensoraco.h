@@ -169,6 +169,50 @@ int aco_solver_kernel_ms(aco_solver* s, float* ms5);
 int aco_solver_set_shape(aco_solver* s, int warps, int chunks, int mode);
 
 /* ======================================================================
+ * Batches: many independent instances advanced together.  One iteration of
+ * a batch is five multi-instance launches over all active instances -- one
+ * CTA per (instance, row) for M_p and the deposit, one persistent launch for
+ * the construction of every ant of every instance (work items handed out
+ * by a global counter, largest n first), one warp per (instance, ant) for
+ * the lengths, one CTA per instance for the best -- replayed as a CUDA graph
+ * while the active set is unchanged.  Each instance keeps its whole state
+ * (tau, M_p, tours, best) resident in a workspace carved from the batch's
+ * device arena by a first-fit allocator; results are bit-identical to those
+ * of a single solver with the same parameters.
+ * ==================================================================== */
+typedef struct aco_batch aco_batch;
+
+/* max_instances: slot table size.  arena_bytes: device memory for instance
+ * workspaces; dev_arena (256-byte aligned, caller-owned, nullable) provides
+ * it, else the library allocates it.  All instances share `prec`.  stream:
+ * the batch's stream (NULL: legacy default stream, no graph replay). */
+int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int prec,
+                     void* dev_arena, void* stream);
+int aco_batch_destroy(aco_batch* b);
+
+/* Admit an instance: coords_host n x 2 fp32, p as for aco_create (p->prec
+ * must equal the batch's).  It runs iters_budget iterations (0: until
+ * removed), then stops advancing and keeps its results.  *slot receives its
+ * slot id.  ACO_ERR_OOM (nothing changed) when no slot is free or its
+ * workspace (aco_batch_instance_bytes) does not fit in the arena now. */
+int aco_batch_add(aco_batch* b, const float* coords_host, const aco_params* p, int iters_budget,
+                  int* slot);
+/* Release a slot and its workspace. */
+int aco_batch_remove(aco_batch* b, int slot);
+/* Run k iterations of every active (unfinished) instance. */
+int aco_batch_step(aco_batch* b, int k);
+int aco_batch_best(aco_batch* b, int slot, int32_t* tour_host, double* len_host);
+int aco_batch_get_tau(aco_batch* b, int slot, float* tau_host);
+int aco_batch_status(aco_batch* b, int slot, uint32_t* iterations_done, int* finished);
+/* Active instances, free arena bytes and largest free block. */
+int aco_batch_info(aco_batch* b, int* active, size_t* free_bytes, size_t* largest_block);
+/* Construct launch shape for the batch (0, 0, 0: the default covering the
+ * largest active n). */
+int aco_batch_set_shape(aco_batch* b, int warps, int chunks, int mode);
+/* Arena bytes one instance of (n, m) takes. */
+int aco_batch_instance_bytes(int n, int m, size_t* bytes);
+
+/* ======================================================================
  * Step-level API on caller-owned device buffers (one kernel family each),
  * asynchronous on `stream`.  The solvers above are built from these.
  * ==================================================================== */

@@ -66,6 +66,17 @@ _SIGS = {
     "aco_solver_set_shape": (i32, [v, i32, i32, i32]),
     "aco_autotune_construct": (i32, [v, i32, i32, i32, i32, u64, v, i32, C.POINTER(i32),
                                      C.POINTER(i32), C.POINTER(i32), C.POINTER(f32), v]),
+    "aco_batch_create": (i32, [C.POINTER(v), i32, sz, i32, v, v]),
+    "aco_batch_destroy": (i32, [v]),
+    "aco_batch_add": (i32, [v, v, C.POINTER(Params), i32, C.POINTER(i32)]),
+    "aco_batch_remove": (i32, [v, i32]),
+    "aco_batch_step": (i32, [v, i32]),
+    "aco_batch_best": (i32, [v, i32, v, v]),
+    "aco_batch_get_tau": (i32, [v, i32, v]),
+    "aco_batch_status": (i32, [v, i32, C.POINTER(u32), C.POINTER(i32)]),
+    "aco_batch_info": (i32, [v, C.POINTER(i32), C.POINTER(sz), C.POINTER(sz)]),
+    "aco_batch_set_shape": (i32, [v, i32, i32, i32]),
+    "aco_batch_instance_bytes": (i32, [i32, i32, C.POINTER(sz)]),
     "aco_op_heuristic": (i32, [v, i32, i32, v, v, i32, v]),
     "aco_op_fill": (i32, [v, i32, i32, f32, v]),
     "aco_op_build_P": (i32, [v, v, i32, i32, i32, f32, i32, v, v]),
@@ -305,6 +316,103 @@ class Solver:
             lib().aco_destroy(self._h)
             self._h = None
         self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_params(n, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec="fp32", roulette="ir",
+                deposit="det", gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0):
+    p = Params()
+    call("aco_params_default", C.byref(p))
+    p.n, p.m, p.alpha, p.beta = n, m, alpha, beta
+    p.rho, p.Q, p.tau0, p.seed = rho, Q, tau0, seed
+    p.prec = PREC[prec] if isinstance(prec, str) else prec
+    p.roulette = ROULETTE[roulette] if isinstance(roulette, str) else roulette
+    p.deposit = DEPOSIT[deposit] if isinstance(deposit, str) else deposit
+    p.gamma_max, p.gamma_min, p.gamma_T = gamma_max, gamma_min, gamma_T
+    return p
+
+
+def instance_bytes(n, m):
+    out = sz(0)
+    call("aco_batch_instance_bytes", n, m, C.byref(out))
+    return out.value
+
+
+class Batch:
+    """Many independent instances advanced together (the C batch API)."""
+
+    def __init__(self, max_instances, arena_bytes, prec="fp32", stream=None, arena="torch"):
+        import torch
+        self.prec = PREC[prec] if isinstance(prec, str) else prec
+        self._arena = None
+        arena_ptr = None
+        if arena == "torch":
+            self._arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
+            arena_ptr = self._arena.data_ptr()
+        self.stream = stream
+        h = v()
+        call("aco_batch_create", C.byref(h), max_instances, arena_bytes, self.prec, arena_ptr,
+             stream_ptr(stream))
+        self._h = h
+        self.n_of = {}
+
+    def add(self, coords, m, iters=0, **kw):
+        """Admit an instance; returns its slot, or None if it does not fit now."""
+        xy = _host(coords, np.float32)
+        n = xy.shape[0]
+        p = make_params(n, m, prec=self.prec, **kw)
+        slot = i32(-1)
+        rc = lib().aco_batch_add(self._h, xy.ctypes.data, C.byref(p), iters, C.byref(slot))
+        if rc == ERR_OOM:
+            return None
+        check(rc)
+        self.n_of[slot.value] = n
+        return slot.value
+
+    def remove(self, slot):
+        call("aco_batch_remove", self._h, slot)
+        self.n_of.pop(slot, None)
+
+    def step(self, k=1):
+        call("aco_batch_step", self._h, k)
+        return self
+
+    def best(self, slot):
+        n = self.n_of[slot]
+        tour = np.empty(n, dtype=np.int32)
+        L = np.zeros(1, dtype=np.float64)
+        call("aco_batch_best", self._h, slot, tour.ctypes.data, L.ctypes.data)
+        return tour, float(L[0])
+
+    def tau(self, slot):
+        n = self.n_of[slot]
+        out = np.empty((n, n), dtype=np.float32)
+        call("aco_batch_get_tau", self._h, slot, out.ctypes.data)
+        return out
+
+    def status(self, slot):
+        it, fin = u32(0), i32(0)
+        call("aco_batch_status", self._h, slot, C.byref(it), C.byref(fin))
+        return it.value, bool(fin.value)
+
+    def info(self):
+        a, f, l = i32(0), sz(0), sz(0)
+        call("aco_batch_info", self._h, C.byref(a), C.byref(f), C.byref(l))
+        return dict(active=a.value, free_bytes=f.value, largest_block=l.value)
+
+    def set_shape(self, warps=0, chunks=0, mode=0):
+        call("aco_batch_set_shape", self._h, warps, chunks, mode)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().aco_batch_destroy(self._h)
+            self._h = None
+        self._arena = None
 
     def __del__(self):
         try:

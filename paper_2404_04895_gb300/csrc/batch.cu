@@ -1,0 +1,508 @@
+// Batches: many independent TSP instances advanced together.
+//
+// Every step of an iteration is one launch over all active instances:
+//   build_P      one CTA per (instance, row)
+//   construct    one persistent launch; CTAs pull (instance, ant) items from a
+//                global counter, biggest instances first
+//   tour_length  one warp per (instance, ant)
+//   best         one CTA per instance
+//   deposit      one warp per (instance, row)
+// The launches of one iteration are captured into a CUDA graph and replayed
+// while the set of active instances does not change.  Instance workspaces
+// (same layout as a single solver) are carved from one device arena by a
+// first-fit allocator; an instance is admitted only if its workspace fits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <vector>
+
+#include "batch.cuh"
+#include "common.cuh"
+#include "internal.h"
+#include "steps.cuh"
+
+namespace aco {
+
+// ------------------------------------------------------------------ kernels
+template <int PREC>
+__global__ void __launch_bounds__(256) batch_build_P_kernel(const InstDev* __restrict__ insts,
+                                                            const int* __restrict__ row_off,
+                                                            int count) {
+  __shared__ float red[32];
+  const int r = blockIdx.x;
+  const int i = find_instance(row_off, count, r);
+  const InstDev& I = insts[i];
+  const int row = r - __ldg(row_off + i);
+  float inv_gamma = 1.0f;
+  if (I.adair) {
+    const uint32_t it = *I.it;
+    inv_gamma = I.sched[it < (uint32_t)I.n_sched ? it : (uint32_t)(I.n_sched - 1)];
+  }
+  const size_t eb = PREC == ACO_FP32 ? 4 : 2;
+  build_P_row<PREC>(I.tau + (size_t)row * I.ld, I.H + (size_t)row * I.ld, I.n, I.ld, row, I.alpha,
+                    inv_gamma, static_cast<char*>(I.P) + (size_t)row * I.ld * eb, red);
+}
+
+__global__ void __launch_bounds__(256) batch_tour_length_kernel(const InstDev* __restrict__ insts,
+                                                                const int* __restrict__ ant_off,
+                                                                int count, int total) {
+  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= total) return;
+  const int i = find_instance(ant_off, count, item);
+  const InstDev& I = insts[i];
+  const int k = item - __ldg(ant_off + i);
+  tour_length_ant(I.D, I.n, I.tours + (size_t)k * I.n, I.m, k, I.Q, I.L, I.c, I.nbr);
+}
+
+__global__ void __launch_bounds__(256) batch_best_kernel(const InstDev* __restrict__ insts) {
+  __shared__ double sl[32];
+  __shared__ int sk[33];
+  const InstDev& I = insts[blockIdx.x];
+  best_block(I.L, I.tours, I.n, I.m, I.best_tour, I.best_len, I.it, sl, sk);
+}
+
+__global__ void __launch_bounds__(32) batch_deposit_kernel(const InstDev* __restrict__ insts,
+                                                           const int* __restrict__ row_off,
+                                                           int count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int r = blockIdx.x;
+  const int i = find_instance(row_off, count, r);
+  const InstDev& I = insts[i];
+  const int a = r - __ldg(row_off + i);
+  const double keep = 1.0 - (double)I.rho;
+  deposit_row(I.tau + (size_t)a * I.ld, I.n, I.nbr + (size_t)a * I.m * 2, I.c, I.m, keep,
+              deposit_tile(I.n), smem);
+}
+
+// ------------------------------------------------------------------ arena
+// First-fit allocator over [0, size) with coalescing of free neighbours.
+class Arena {
+ public:
+  void reset(size_t size) {
+    free_.clear();
+    used_.clear();
+    if (size) free_[0] = size;
+    size_ = size;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t at = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        used_[*off] = bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off) {
+    auto u = used_.find(off);
+    if (u == used_.end()) return;
+    size_t at = off, bytes = u->second;
+    used_.erase(u);
+    auto next = free_.lower_bound(at);
+    if (next != free_.end() && at + bytes == next->first) {
+      bytes += next->second;
+      free_.erase(next);
+    }
+    auto it = free_.lower_bound(at);
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second == at) {
+        at = prev->first;
+        bytes += prev->second;
+        free_.erase(prev);
+      }
+    }
+    free_[at] = bytes;
+  }
+  size_t free_bytes() const {
+    size_t s = 0;
+    for (auto& f : free_) s += f.second;
+    return s;
+  }
+  size_t largest() const {
+    size_t s = 0;
+    for (auto& f : free_) s = std::max(s, f.second);
+    return s;
+  }
+
+ private:
+  std::map<size_t, size_t> free_, used_;
+  size_t size_ = 0;
+};
+
+struct Slot {
+  bool used = false;
+  aco_params p{};
+  size_t off = 0;
+  InstDev dev{};
+  uint32_t done = 0;      // iterations completed
+  int budget = 0;         // iterations to run (0: unlimited)
+  bool finished() const { return budget > 0 && (int)done >= budget; }
+};
+
+// Per-instance helpers from solver.cu (workspace layout, schedule values).
+size_t instance_workspace_bytes(int n, int m);
+int instance_bind(const aco_params& p, unsigned char* ws, InstDev* d, cudaStream_t st,
+                  const float* coords_host);
+
+}  // namespace aco
+
+using namespace aco;
+
+struct aco_batch {
+  int prec = ACO_FP32;
+  cudaStream_t stream = nullptr;
+  unsigned char* arena_mem = nullptr;
+  bool own_arena = false;
+  size_t arena_bytes = 0;
+  Arena arena;
+  std::vector<Slot> slots;
+  int num_sms = 0;
+  // device tables of the active set
+  InstDev* d_insts = nullptr;
+  int* d_row_off = nullptr;
+  int* d_ant_off = nullptr;
+  int* d_counter = nullptr;
+  int32_t* d_err = nullptr;
+  std::vector<int> active;      // slot ids, n descending
+  int total_rows = 0, total_ants = 0, max_n = 0, max_tile = 0;
+  ConstructShape shape{0, 0, 0};
+  bool tables_ok = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace aco {
+
+static void batch_drop_graph(aco_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+static int batch_shape_columns(ConstructShape s, int eb) { return 32 * s.warps * s.chunks * (16 / eb); }
+
+static ConstructShape batch_default_shape(int max_n, int eb) {
+  const ConstructShape* list;
+  const int cnt = batch_construct_shapes(eb, &list);
+  ConstructShape best = {0, 0, 0};
+  for (int q = 0; q < cnt; ++q) {
+    const ConstructShape s = list[q];
+    if (batch_shape_columns(s, eb) < max_n) continue;
+    const bool better = best.warps == 0 || s.mode > best.mode ||
+                        (s.mode == best.mode && (s.warps < best.warps ||
+                                                 (s.warps == best.warps && s.chunks < best.chunks)));
+    if (better) best = s;
+  }
+  return best;
+}
+
+// Rebuild the active set (unfinished instances, n descending) and its tables.
+static int batch_refresh(aco_batch* b) {
+  b->active.clear();
+  for (int q = 0; q < (int)b->slots.size(); ++q)
+    if (b->slots[q].used && !b->slots[q].finished()) b->active.push_back(q);
+  std::stable_sort(b->active.begin(), b->active.end(),
+                   [&](int x, int y) { return b->slots[x].p.n > b->slots[y].p.n; });
+  const int cnt = (int)b->active.size();
+  std::vector<InstDev> insts(cnt);
+  std::vector<int> row_off(cnt + 1, 0), ant_off(cnt + 1, 0);
+  b->max_n = 0;
+  for (int q = 0; q < cnt; ++q) {
+    const Slot& s = b->slots[b->active[q]];
+    insts[q] = s.dev;
+    row_off[q + 1] = row_off[q] + s.p.n;
+    ant_off[q + 1] = ant_off[q] + s.p.m;
+    b->max_n = std::max(b->max_n, s.p.n);
+  }
+  b->total_rows = row_off[cnt];
+  b->total_ants = ant_off[cnt];
+  b->max_tile = deposit_tile(std::max(b->max_n, 1));
+  if (cnt) {
+    ACO_CUDA_TRY(cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(InstDev) * cnt, cudaMemcpyHostToDevice, b->stream));
+    ACO_CUDA_TRY(cudaMemcpyAsync(b->d_row_off, row_off.data(), sizeof(int) * (cnt + 1), cudaMemcpyHostToDevice, b->stream));
+    ACO_CUDA_TRY(cudaMemcpyAsync(b->d_ant_off, ant_off.data(), sizeof(int) * (cnt + 1), cudaMemcpyHostToDevice, b->stream));
+    ACO_CUDA_TRY(cudaStreamSynchronize(b->stream));  // pageable sources
+  }
+  const int eb = b->prec == ACO_FP32 ? 4 : 2;
+  ConstructShape s = b->shape;
+  if (s.warps == 0 || batch_shape_columns(s, eb) < b->max_n) s = batch_default_shape(b->max_n, eb);
+  if (cnt && s.warps == 0) return set_error(ACO_ERR_UNSUPPORTED, "no batch construct shape covers n=%d", b->max_n);
+  b->shape = s;
+  batch_drop_graph(b);
+  b->tables_ok = true;
+  return ACO_OK;
+}
+
+static int batch_enqueue(aco_batch* b) {
+  const int cnt = (int)b->active.size();
+  if (!cnt) return ACO_OK;
+  cudaStream_t st = b->stream;
+  switch (b->prec) {
+    case ACO_FP32:
+      batch_build_P_kernel<ACO_FP32><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
+      break;
+    case ACO_BF16:
+      batch_build_P_kernel<ACO_BF16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
+      break;
+    default:
+      batch_build_P_kernel<ACO_FP16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
+  }
+  ACO_CHECK_LAUNCH("batch_build_P_kernel");
+  ACO_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
+  int rc;
+  const ConstructShape s = b->shape;
+  if (b->prec == ACO_FP32)
+    rc = launch_batch_construct_f32(b->d_insts, b->d_ant_off, cnt, b->total_ants, b->d_counter, b->d_err,
+                                    s.warps, s.chunks, s.mode, b->num_sms, st);
+  else if (b->prec == ACO_BF16)
+    rc = launch_batch_construct_bf16(b->d_insts, b->d_ant_off, cnt, b->total_ants, b->d_counter, b->d_err,
+                                     s.warps, s.chunks, s.mode, b->num_sms, st);
+  else
+    rc = launch_batch_construct_f16(b->d_insts, b->d_ant_off, cnt, b->total_ants, b->d_counter, b->d_err,
+                                    s.warps, s.chunks, s.mode, b->num_sms, st);
+  if (rc) return rc;
+  batch_tour_length_kernel<<<(b->total_ants + 7) / 8, 256, 0, st>>>(b->d_insts, b->d_ant_off, cnt,
+                                                                    b->total_ants);
+  ACO_CHECK_LAUNCH("batch_tour_length_kernel");
+  batch_best_kernel<<<cnt, 256, 0, st>>>(b->d_insts);
+  ACO_CHECK_LAUNCH("batch_best_kernel");
+  batch_deposit_kernel<<<b->total_rows, 32, deposit_smem_bytes(b->max_tile), st>>>(b->d_insts,
+                                                                                  b->d_row_off, cnt);
+  ACO_CHECK_LAUNCH("batch_deposit_kernel");
+  return ACO_OK;
+}
+
+static int batch_capture(aco_batch* b) {
+  batch_drop_graph(b);
+  ACO_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = batch_enqueue(b);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture(batch)");
+  const cudaError_t e2 = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e2 != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_error(e2, "cudaGraphInstantiate(batch)");
+  }
+  b->graph = g;
+  return ACO_OK;
+}
+
+}  // namespace aco
+
+extern "C" {
+
+int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int prec,
+                     void* dev_arena, void* stream) {
+  if (!out) return set_error(ACO_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (max_instances < 1 || max_instances > (1 << 20)) return set_error(ACO_ERR_ARG, "max_instances out of range");
+  if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  if (arena_bytes < 256) return set_error(ACO_ERR_ARG, "arena too small");
+  if (dev_arena && ((uintptr_t)dev_arena & 255u)) return set_error(ACO_ERR_ARG, "arena must be 256-byte aligned");
+  int rc = prepare_kernels();
+  if (rc) return rc;
+  aco_batch* b = new aco_batch();
+  b->prec = prec;
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->slots.resize(max_instances);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  auto fail = [&](int code) {
+    if (b->own_arena && b->arena_mem) cudaFree(b->arena_mem);
+    cudaFree(b->d_insts);
+    cudaFree(b->d_row_off);
+    cudaFree(b->d_ant_off);
+    cudaFree(b->d_counter);
+    cudaFree(b->d_err);
+    delete b;
+    return code;
+  };
+  if (dev_arena) {
+    b->arena_mem = static_cast<unsigned char*>(dev_arena);
+  } else {
+    const cudaError_t e = cudaMalloc(&b->arena_mem, arena_bytes);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cudaMalloc(batch arena)"));
+    b->own_arena = true;
+  }
+  b->arena_bytes = arena_bytes;
+  b->arena.reset(arena_bytes);
+  if (cudaMalloc(&b->d_insts, sizeof(InstDev) * max_instances) != cudaSuccess ||
+      cudaMalloc(&b->d_row_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
+      cudaMalloc(&b->d_ant_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
+      cudaMalloc(&b->d_counter, sizeof(int)) != cudaSuccess || cudaMalloc(&b->d_err, sizeof(int32_t)) != cudaSuccess)
+    return fail(cuda_error(cudaGetLastError(), "cudaMalloc(batch tables)"));
+  if (cudaMemset(b->d_err, 0, sizeof(int32_t)) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "memset"));
+  *out = b;
+  return ACO_OK;
+}
+
+int aco_batch_destroy(aco_batch* b) {
+  if (!b) return ACO_OK;
+  cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  if (b->own_arena) cudaFree(b->arena_mem);
+  cudaFree(b->d_insts);
+  cudaFree(b->d_row_off);
+  cudaFree(b->d_ant_off);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_err);
+  delete b;
+  return ACO_OK;
+}
+
+int aco_batch_add(aco_batch* b, const float* coords_host, const aco_params* p, int iters_budget,
+                  int* slot) {
+  if (!b || !coords_host || !p || !slot) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (p->prec != b->prec) return set_error(ACO_ERR_ARG, "instance precision %d differs from the batch's %d", p->prec, b->prec);
+  if (iters_budget < 0) return set_error(ACO_ERR_ARG, "iters_budget must be >= 0");
+  int q = 0;
+  while (q < (int)b->slots.size() && b->slots[q].used) ++q;
+  if (q == (int)b->slots.size()) return set_error(ACO_ERR_OOM, "all %d batch slots are in use", q);
+  const size_t need = instance_workspace_bytes(p->n, p->m);
+  size_t off = 0;
+  if (p->n < 3 || p->n > ACO_MAX_N || p->m < 1) return set_error(ACO_ERR_ARG, "n or m out of range");
+  if (!b->arena.alloc(need, &off))
+    return set_error(ACO_ERR_OOM, "instance needs %zu bytes; arena has %zu free (largest block %zu)", need,
+                     b->arena.free_bytes(), b->arena.largest());
+  Slot& s = b->slots[q];
+  const int rc = instance_bind(*p, b->arena_mem + off, &s.dev, b->stream, coords_host);
+  if (rc) {
+    b->arena.release(off);
+    return rc;
+  }
+  s.used = true;
+  s.p = *p;
+  s.off = off;
+  s.done = 0;
+  s.budget = iters_budget;
+  b->tables_ok = false;
+  *slot = q;
+  return ACO_OK;
+}
+
+int aco_batch_remove(aco_batch* b, int slot) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used)
+    return set_error(ACO_ERR_ARG, "invalid slot %d", slot);
+  ACO_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  b->arena.release(b->slots[slot].off);
+  b->slots[slot] = Slot();
+  b->tables_ok = false;
+  return ACO_OK;
+}
+
+int aco_batch_step(aco_batch* b, int k) {
+  if (!b) return set_error(ACO_ERR_ARG, "batch is NULL");
+  if (k < 0) return set_error(ACO_ERR_ARG, "k must be >= 0");
+  for (int q = 0; q < k; ++q) {
+    if (!b->tables_ok) {
+      int rc = batch_refresh(b);
+      if (rc) return rc;
+      if (b->active.empty()) return ACO_OK;
+      rc = batch_enqueue(b);  // first iteration of a new set: direct launches
+      if (rc) return rc;
+    } else {
+      if (b->active.empty()) return ACO_OK;
+      if (!b->exec && b->stream) {
+        int rc = batch_capture(b);
+        if (rc) return rc;
+      }
+      if (b->exec) {
+        ACO_CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+      } else {
+        int rc = batch_enqueue(b);
+        if (rc) return rc;
+      }
+    }
+    bool change = false;
+    for (int id : b->active) {
+      Slot& s = b->slots[id];
+      s.done += 1;
+      change |= s.finished();
+    }
+    if (change) b->tables_ok = false;
+  }
+  return ACO_OK;
+}
+
+int aco_batch_best(aco_batch* b, int slot, int32_t* tour_host, double* len_host) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used)
+    return set_error(ACO_ERR_ARG, "invalid slot %d", slot);
+  if (!tour_host || !len_host) return set_error(ACO_ERR_ARG, "NULL argument");
+  const Slot& s = b->slots[slot];
+  if (s.done == 0) return set_error(ACO_ERR_STATE, "slot %d has not run an iteration", slot);
+  ACO_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  int32_t err = 0;
+  ACO_CUDA_TRY(cudaMemcpy(&err, b->d_err, 4, cudaMemcpyDeviceToHost));
+  if (err) return set_error(ACO_ERR_CUDA, "a kernel-side check failed (code %d)", err);
+  ACO_CUDA_TRY(cudaMemcpy(len_host, s.dev.best_len, 8, cudaMemcpyDeviceToHost));
+  ACO_CUDA_TRY(cudaMemcpy(tour_host, s.dev.best_tour, sizeof(int32_t) * s.p.n, cudaMemcpyDeviceToHost));
+  return ACO_OK;
+}
+
+int aco_batch_get_tau(aco_batch* b, int slot, float* tau_host) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used || !tau_host)
+    return set_error(ACO_ERR_ARG, "invalid argument");
+  const Slot& s = b->slots[slot];
+  ACO_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  ACO_CUDA_TRY(cudaMemcpy2D(tau_host, sizeof(float) * s.p.n, s.dev.tau, sizeof(float) * s.dev.ld,
+                            sizeof(float) * s.p.n, s.p.n, cudaMemcpyDeviceToHost));
+  return ACO_OK;
+}
+
+int aco_batch_status(aco_batch* b, int slot, uint32_t* iterations_done, int* finished) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].used)
+    return set_error(ACO_ERR_ARG, "invalid slot %d", slot);
+  if (iterations_done) *iterations_done = b->slots[slot].done;
+  if (finished) *finished = b->slots[slot].finished() ? 1 : 0;
+  return ACO_OK;
+}
+
+int aco_batch_info(aco_batch* b, int* active, size_t* free_bytes, size_t* largest_block) {
+  if (!b) return set_error(ACO_ERR_ARG, "batch is NULL");
+  int cnt = 0;
+  for (auto& s : b->slots) cnt += s.used && !s.finished();
+  if (active) *active = cnt;
+  if (free_bytes) *free_bytes = b->arena.free_bytes();
+  if (largest_block) *largest_block = b->arena.largest();
+  return ACO_OK;
+}
+
+int aco_batch_set_shape(aco_batch* b, int warps, int chunks, int mode) {
+  if (!b) return set_error(ACO_ERR_ARG, "batch is NULL");
+  if (warps || chunks) {
+    const int eb = b->prec == ACO_FP32 ? 4 : 2;
+    const ConstructShape* list;
+    const int cnt = batch_construct_shapes(eb, &list);
+    bool found = false;
+    for (int q = 0; q < cnt; ++q)
+      found |= list[q].warps == warps && list[q].chunks == chunks && list[q].mode == mode;
+    if (!found) return set_error(ACO_ERR_UNSUPPORTED, "batch shape (%d, %d, %d) not compiled", warps, chunks, mode);
+  }
+  b->shape = {warps, chunks, mode};
+  b->tables_ok = false;
+  return ACO_OK;
+}
+
+int aco_batch_instance_bytes(int n, int m, size_t* bytes) {
+  if (!bytes || n < 3 || n > ACO_MAX_N || m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "invalid argument");
+  *bytes = (instance_workspace_bytes(n, m) + 255) & ~(size_t)255;
+  return ACO_OK;
+}
+
+}  // extern "C"

@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "batch.cuh"
 #include "common.cuh"
 
 namespace aco {
@@ -144,10 +145,14 @@ __device__ __forceinline__ uint32_t score_key(float bs) {
 constexpr int MODE_STAGED = 0;
 constexpr int MODE_DIRECT = 1;
 
+// The walk of ant k (all threads of the CTA call it together): start city, then
+// n-1 steps over M_p (P, n x ld), tour written to tour[0..n-1].  red_s/red_j:
+// [2][W] shared scratch; srow: [KC * 32 * W] shared chunks (MODE_STAGED only).
 template <int PREC, int W, int KC, int MODE>
-__global__ void __launch_bounds__(32 * W) construct_kernel(
-    const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it_arg,
-    const uint32_t* __restrict__ it_dev, int32_t* __restrict__ tours, int32_t* __restrict__ err) {
+__device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n, int ld, uint2 key,
+                                              uint32_t it, int k, int32_t* __restrict__ tour,
+                                              int32_t* __restrict__ err, uint32_t (*red_s)[W],
+                                              int (*red_j)[W], uint4* __restrict__ srow) {
   using E = Elem<PREC>;
   constexpr int V = E::V;
   constexpr int G = V / 4;                // 4-column groups per chunk (one Philox block each)
@@ -159,18 +164,11 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
   static_assert(NG <= 64, "group masks are 64 bits");
   static_assert(NG <= 255, "group index packs into 8 bits");
 
-  const int k = blockIdx.x;
-  if (k >= m) return;
   const int gl = threadIdx.x;
   const int lane = gl & 31;
   const int wi = gl >> 5;
-  const uint32_t it = it_dev ? *it_dev : it_arg;
   const char* __restrict__ P = static_cast<const char*>(Pv);
   const size_t row_bytes = (size_t)ld * E::BYTES;
-
-  __shared__ uint32_t red_s[2][W];
-  __shared__ int red_j[2][W];
-  extern __shared__ __align__(16) uint4 srow[];  // MODE_STAGED: [KC * TPA] chunks of the row
 
   // visited bits: bit c*V + e  <->  column (c*TPA + gl)*V + e;
   // emptym bit gi: all 4 columns of group gi visited
@@ -214,7 +212,7 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
   };
 
   int cur = start_city(key, it, (uint32_t)k, n);
-  if (gl == 0) tours[(size_t)k * n] = cur;
+  if (gl == 0) tour[0] = cur;
   mark(cur);
 
   uint4 d[KC];  // MODE_DIRECT: the thread's chunks of the current row
@@ -333,9 +331,49 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
       if (gl == 0 && err) atomicExch(err, 1);
       break;
     }
-    if (gl == 0) tours[(size_t)k * n + t] = next;
+    if (gl == 0) tour[t] = next;
     mark(next);
     cur = next;
+  }
+}
+
+template <int PREC, int W, int KC, int MODE>
+__global__ void __launch_bounds__(32 * W) construct_kernel(
+    const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it_arg,
+    const uint32_t* __restrict__ it_dev, int32_t* __restrict__ tours, int32_t* __restrict__ err) {
+  __shared__ uint32_t red_s[2][W];
+  __shared__ int red_j[2][W];
+  extern __shared__ __align__(16) uint4 srow[];  // MODE_STAGED: [KC * 32 * W] chunks of the row
+  const int k = blockIdx.x;
+  if (k >= m) return;
+  const uint32_t it = it_dev ? *it_dev : it_arg;
+  construct_ant<PREC, W, KC, MODE>(Pv, n, ld, key, it, k, tours + (size_t)k * n, err, red_s, red_j,
+                                   srow);
+}
+
+// Multi-instance construction: a persistent grid pulls work items (instance,
+// ant) from a global counter; items are ordered by instance, instances by
+// decreasing n, so the longest walks start first.  One launch covers every
+// ant of every active instance of a batch.
+template <int PREC, int W, int KC, int MODE>
+__global__ void __launch_bounds__(32 * W) batch_construct_kernel(
+    const InstDev* __restrict__ insts, const int* __restrict__ ant_off, int count, int total,
+    int* __restrict__ counter, int32_t* __restrict__ err) {
+  __shared__ uint32_t red_s[2][W];
+  __shared__ int red_j[2][W];
+  __shared__ int item_s;
+  extern __shared__ __align__(16) uint4 srow[];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    const int i = find_instance(ant_off, count, item);
+    const InstDev& I = insts[i];
+    const int k = item - __ldg(ant_off + i);
+    construct_ant<PREC, W, KC, MODE>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err,
+                                     red_s, red_j, srow);
   }
 }
 
@@ -353,6 +391,25 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
 }  // namespace aco
 
 namespace aco {
+#define ACO_BATCH_CONSTRUCT_CASE(PREC, W, KC, MODE)                                          \
+  if (warps == W && chunks == KC && mode == MODE) {                                         \
+    auto kern = batch_construct_kernel<PREC, W, KC, MODE>;                                  \
+    const size_t smem_ = MODE == MODE_STAGED ? (size_t)KC * 32 * W * 16 : 0;                 \
+    static int blocks_per_sm = 0;                                                           \
+    if (!blocks_per_sm) {                                                                   \
+      if (MODE == MODE_STAGED)                                                              \
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_); \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 32 * W, smem_);  \
+      if (blocks_per_sm < 1) blocks_per_sm = 1;                                             \
+    }                                                                                       \
+    int grid_ = blocks_per_sm * num_sms;                                                    \
+    if (grid_ > total) grid_ = total;                                                       \
+    if (grid_ < 1) grid_ = 1;                                                               \
+    kern<<<grid_, 32 * W, smem_, st>>>(insts, ant_off, count, total, counter, err);         \
+    const cudaError_t e_ = cudaGetLastError();                                              \
+    return e_ == cudaSuccess ? ACO_OK : cuda_error(e_, "batch_construct_kernel launch");    \
+  }
+
 // Opt every compiled shape in to its dynamic shared-memory size (once).
 #define ACO_CONSTRUCT_PREPARE(PREC, W, KC, MODE)                                           \
   if (MODE == MODE_STAGED) {                                                                 \

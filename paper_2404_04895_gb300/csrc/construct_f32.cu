@@ -22,4 +22,14 @@ int prepare_construct_f32() {
   return ACO_OK;
 }
 
+int launch_batch_construct_f32(const InstDev* insts, const int* ant_off, int count, int total,
+                                int* counter, int32_t* err, int warps, int chunks, int mode,
+                                int num_sms, cudaStream_t st) {
+#define X(W, KC, MODE) ACO_BATCH_CONSTRUCT_CASE(ACO_FP32, W, KC, MODE)
+  ACO_BATCH_SHAPES_4B(X)
+#undef X
+  return set_error(ACO_ERR_UNSUPPORTED, "batch construct shape (%d, %d, %d) not compiled", warps, chunks,
+                   mode);
+}
+
 }  // namespace aco

@@ -51,6 +51,18 @@ int launch_construct_f16(const void* P, int n, int ld, int m, uint2 key, uint32_
                          const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
                          int chunks, int mode, cudaStream_t st);
 
+struct InstDev;
+int launch_batch_construct_f32(const InstDev* insts, const int* ant_off, int count, int total,
+                               int* counter, int32_t* err, int warps, int chunks, int mode,
+                               int num_sms, cudaStream_t st);
+int launch_batch_construct_bf16(const InstDev* insts, const int* ant_off, int count, int total,
+                                int* counter, int32_t* err, int warps, int chunks, int mode,
+                                int num_sms, cudaStream_t st);
+int launch_batch_construct_f16(const InstDev* insts, const int* ant_off, int count, int total,
+                               int* counter, int32_t* err, int warps, int chunks, int mode,
+                               int num_sms, cudaStream_t st);
+int batch_construct_shapes(int elem_bytes, const ConstructShape** list);
+
 int prepare_construct_f32();
 int prepare_construct_bf16();
 int prepare_construct_f16();

@@ -12,6 +12,7 @@
 #include <tuple>
 #include <vector>
 
+#include "batch.cuh"
 #include "internal.h"
 #include "shapes.h"
 
@@ -44,6 +45,26 @@ static const ConstructShape kShapes2[] = {
     ACO_SHAPES_2B(X)
 #undef X
 };
+
+static const ConstructShape kBatchShapes4[] = {
+#define X(W, KC, MODE) {W, KC, MODE},
+    ACO_BATCH_SHAPES_4B(X)
+#undef X
+};
+static const ConstructShape kBatchShapes2[] = {
+#define X(W, KC, MODE) {W, KC, MODE},
+    ACO_BATCH_SHAPES_2B(X)
+#undef X
+};
+
+int batch_construct_shapes(int elem_bytes, const ConstructShape** list) {
+  if (elem_bytes == 4) {
+    *list = kBatchShapes4;
+    return (int)(sizeof(kBatchShapes4) / sizeof(kBatchShapes4[0]));
+  }
+  *list = kBatchShapes2;
+  return (int)(sizeof(kBatchShapes2) / sizeof(kBatchShapes2[0]));
+}
 
 int construct_shapes(int elem_bytes, const ConstructShape** list) {
   if (elem_bytes == 4) {
@@ -186,6 +207,61 @@ static Layout layout_of(int n, int m) {
   L.sched = take((size_t)kSchedCap * 4);
   L.total = o;
   return L;
+}
+
+size_t instance_workspace_bytes(int n, int m) { return layout_of(n, m).total; }
+
+// Validate p, lay out an instance's state in ws (instance_workspace_bytes
+// bytes, 256-byte aligned), initialise it on st (coordinates in, distances,
+// eta^beta, tau = tau0, no best yet, iteration 0, AdaIR schedule) and fill d.
+int instance_bind(const aco_params& p, unsigned char* ws, InstDev* d, cudaStream_t st,
+                  const float* coords_host) {
+  int rc = validate(&p);
+  if (rc) return rc;
+  for (int q = 0; q < 2 * p.n; ++q)
+    if (!std::isfinite(coords_host[q])) return set_error(ACO_ERR_ARG, "coordinate %d is not finite", q);
+  const Layout L = layout_of(p.n, p.m);
+  const int ld = ld_of(p.n);
+  InstDev x{};
+  x.n = p.n;
+  x.m = p.m;
+  x.ld = ld;
+  x.alpha = p.alpha;
+  x.adair = p.roulette == ACO_ADAIR;
+  x.n_sched = x.adair ? std::min(p.gamma_T + 1, kSchedCap) : 1;
+  x.rho = p.rho;
+  x.Q = p.Q;
+  x.key = make_uint2((uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+  float* coords = reinterpret_cast<float*>(ws + L.coords);
+  x.D = reinterpret_cast<double*>(ws + L.D);
+  x.H = reinterpret_cast<float*>(ws + L.H);
+  x.tau = reinterpret_cast<float*>(ws + L.tau);
+  x.P = ws + L.P;
+  x.tours = reinterpret_cast<int32_t*>(ws + L.tours);
+  x.L = reinterpret_cast<double*>(ws + L.L);
+  x.c = reinterpret_cast<double*>(ws + L.c);
+  x.nbr = reinterpret_cast<int32_t*>(ws + L.nbr);
+  x.best_tour = reinterpret_cast<int32_t*>(ws + L.best_tour);
+  x.best_len = reinterpret_cast<double*>(ws + L.best_len);
+  x.it = reinterpret_cast<uint32_t*>(ws + L.it);
+  x.sched = reinterpret_cast<float*>(ws + L.sched);
+  ACO_CUDA_TRY(cudaMemcpyAsync(coords, coords_host, sizeof(float) * 2 * p.n, cudaMemcpyHostToDevice, st));
+  rc = launch_heuristic(coords, p.n, p.beta, const_cast<double*>(x.D), const_cast<float*>(x.H), ld, st);
+  if (!rc) rc = launch_fill(x.tau, p.n, ld, p.tau0, st);
+  if (rc) return rc;
+  const double inf = INFINITY;
+  const uint32_t zero = 0;
+  ACO_CUDA_TRY(cudaMemcpyAsync(x.best_len, &inf, 8, cudaMemcpyHostToDevice, st));
+  ACO_CUDA_TRY(cudaMemcpyAsync(x.it, &zero, 4, cudaMemcpyHostToDevice, st));
+  ACO_CUDA_TRY(cudaMemsetAsync(x.best_tour, 0, sizeof(int32_t) * p.n, st));
+  std::vector<float> h((size_t)x.n_sched, 1.0f);
+  if (x.adair)
+    for (int q = 0; q < x.n_sched; ++q) h[q] = inv_gamma_of(gamma_at(q, p.gamma_T, p.gamma_max, p.gamma_min));
+  ACO_CUDA_TRY(cudaMemcpyAsync(const_cast<float*>(x.sched), h.data(), sizeof(float) * x.n_sched,
+                               cudaMemcpyHostToDevice, st));
+  ACO_CUDA_TRY(cudaStreamSynchronize(st));  // pageable sources above
+  *d = x;
+  return ACO_OK;
 }
 
 }  // namespace aco
