@@ -174,13 +174,20 @@ struct aco_batch {
   int32_t* d_err = nullptr;
   std::vector<int> active;      // slot ids, n descending
   int total_rows = 0, total_ants = 0, max_n = 0, max_tile = 0;
-  ConstructShape shape{0, 0, 0};
+  ConstructShape shape{0, 0, 0};  // forced shape for every class ({0,0,0}: per class)
+  struct Class {
+    int first, count, total;
+    ConstructShape s;
+  };
+  std::vector<Class> classes;     // contiguous ranges of `active` sharing a shape
   bool tables_ok = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
 
 namespace aco {
+
+constexpr int kMaxClasses = 32;
 
 static void batch_drop_graph(aco_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -233,11 +240,29 @@ static int batch_refresh(aco_batch* b) {
     ACO_CUDA_TRY(cudaMemcpyAsync(b->d_ant_off, ant_off.data(), sizeof(int) * (cnt + 1), cudaMemcpyHostToDevice, b->stream));
     ACO_CUDA_TRY(cudaStreamSynchronize(b->stream));  // pageable sources
   }
+  // size classes: consecutive instances (n descending) sharing a shape
   const int eb = b->prec == ACO_FP32 ? 4 : 2;
-  ConstructShape s = b->shape;
-  if (s.warps == 0 || batch_shape_columns(s, eb) < b->max_n) s = batch_default_shape(b->max_n, eb);
-  if (cnt && s.warps == 0) return set_error(ACO_ERR_UNSUPPORTED, "no batch construct shape covers n=%d", b->max_n);
-  b->shape = s;
+  b->classes.clear();
+  for (int q = 0; q < cnt; ++q) {
+    const Slot& sl = b->slots[b->active[q]];
+    ConstructShape s = b->shape;
+    if (s.warps == 0 || batch_shape_columns(s, eb) < sl.p.n) s = batch_default_shape(sl.p.n, eb);
+    if (s.warps == 0) return set_error(ACO_ERR_UNSUPPORTED, "no batch construct shape covers n=%d", sl.p.n);
+    if (!b->classes.empty()) {
+      auto& c = b->classes.back();
+      if (c.s.warps == s.warps && c.s.chunks == s.chunks && c.s.mode == s.mode) {
+        c.count += 1;
+        c.total += sl.p.m;
+        continue;
+      }
+    }
+    if ((int)b->classes.size() == kMaxClasses) {  // merge into the last class (its shape covers smaller n)
+      b->classes.back().count += 1;
+      b->classes.back().total += sl.p.m;
+      continue;
+    }
+    b->classes.push_back({q, 1, sl.p.m, s});
+  }
   batch_drop_graph(b);
   b->tables_ok = true;
   return ACO_OK;
@@ -258,19 +283,25 @@ static int batch_enqueue(aco_batch* b) {
       batch_build_P_kernel<ACO_FP16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
   }
   ACO_CHECK_LAUNCH("batch_build_P_kernel");
-  ACO_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
-  int rc;
-  const ConstructShape s = b->shape;
-  if (b->prec == ACO_FP32)
-    rc = launch_batch_construct_f32(b->d_insts, b->d_ant_off, cnt, b->total_ants, b->d_counter, b->d_err,
-                                    s.warps, s.chunks, s.mode, b->num_sms, st);
-  else if (b->prec == ACO_BF16)
-    rc = launch_batch_construct_bf16(b->d_insts, b->d_ant_off, cnt, b->total_ants, b->d_counter, b->d_err,
-                                     s.warps, s.chunks, s.mode, b->num_sms, st);
-  else
-    rc = launch_batch_construct_f16(b->d_insts, b->d_ant_off, cnt, b->total_ants, b->d_counter, b->d_err,
-                                    s.warps, s.chunks, s.mode, b->num_sms, st);
-  if (rc) return rc;
+  ACO_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int) * b->classes.size(), st));
+  for (size_t ci = 0; ci < b->classes.size(); ++ci) {
+    const auto& c = b->classes[ci];
+    const ConstructShape s = c.s;
+    const InstDev* ins = b->d_insts + c.first;
+    const int* off = b->d_ant_off + c.first;
+    int* ctr = b->d_counter + ci;
+    int rc;
+    if (b->prec == ACO_FP32)
+      rc = launch_batch_construct_f32(ins, off, c.count, c.total, ctr, b->d_err, s.warps, s.chunks, s.mode,
+                                      b->num_sms, st);
+    else if (b->prec == ACO_BF16)
+      rc = launch_batch_construct_bf16(ins, off, c.count, c.total, ctr, b->d_err, s.warps, s.chunks, s.mode,
+                                       b->num_sms, st);
+    else
+      rc = launch_batch_construct_f16(ins, off, c.count, c.total, ctr, b->d_err, s.warps, s.chunks, s.mode,
+                                      b->num_sms, st);
+    if (rc) return rc;
+  }
   batch_tour_length_kernel<<<(b->total_ants + 7) / 8, 256, 0, st>>>(b->d_insts, b->d_ant_off, cnt,
                                                                     b->total_ants);
   ACO_CHECK_LAUNCH("batch_tour_length_kernel");
@@ -316,6 +347,9 @@ int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int
   if (dev_arena && ((uintptr_t)dev_arena & 255u)) return set_error(ACO_ERR_ARG, "arena must be 256-byte aligned");
   int rc = prepare_kernels();
   if (rc) return rc;
+  // the deposit's fp64 row tile may exceed the default 48 KB of dynamic shared memory
+  ACO_CUDA_TRY(cudaFuncSetAttribute(batch_deposit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)deposit_smem_bytes(deposit_tile(ACO_MAX_N))));
   aco_batch* b = new aco_batch();
   b->prec = prec;
   b->stream = static_cast<cudaStream_t>(stream);
@@ -345,7 +379,8 @@ int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int
   if (cudaMalloc(&b->d_insts, sizeof(InstDev) * max_instances) != cudaSuccess ||
       cudaMalloc(&b->d_row_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
       cudaMalloc(&b->d_ant_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
-      cudaMalloc(&b->d_counter, sizeof(int)) != cudaSuccess || cudaMalloc(&b->d_err, sizeof(int32_t)) != cudaSuccess)
+      cudaMalloc(&b->d_counter, sizeof(int) * kMaxClasses) != cudaSuccess ||
+      cudaMalloc(&b->d_err, sizeof(int32_t)) != cudaSuccess)
     return fail(cuda_error(cudaGetLastError(), "cudaMalloc(batch tables)"));
   if (cudaMemset(b->d_err, 0, sizeof(int32_t)) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "memset"));
   *out = b;

@@ -355,10 +355,13 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
 // ant) from a global counter; items are ordered by instance, instances by
 // decreasing n, so the longest walks start first.  One launch covers every
 // ant of every active instance of a batch.
+// insts/ant_off point at the first instance of a size class of `count`
+// instances; its items are ant_off[0] .. ant_off[0] + total - 1.
 template <int PREC, int W, int KC, int MODE>
 __global__ void __launch_bounds__(32 * W) batch_construct_kernel(
     const InstDev* __restrict__ insts, const int* __restrict__ ant_off, int count, int total,
     int* __restrict__ counter, int32_t* __restrict__ err) {
+  const int base = __ldg(ant_off);
   __shared__ uint32_t red_s[2][W];
   __shared__ int red_j[2][W];
   __shared__ int item_s;
@@ -369,9 +372,9 @@ __global__ void __launch_bounds__(32 * W) batch_construct_kernel(
     const int item = item_s;
     __syncthreads();
     if (item >= total) break;
-    const int i = find_instance(ant_off, count, item);
+    const int i = find_instance(ant_off, count, base + item);
     const InstDev& I = insts[i];
-    const int k = item - __ldg(ant_off + i);
+    const int k = base + item - __ldg(ant_off + i);
     construct_ant<PREC, W, KC, MODE>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err,
                                      red_s, red_j, srow);
   }

@@ -17,9 +17,12 @@
   X(2, 12, 1) X(4, 10, 1) X(4, 12, 1) X(8, 12, 1)                                              \
   X(1, 16, 0) X(1, 20, 0) X(1, 32, 0) X(2, 16, 0) X(2, 20, 0) X(4, 16, 0) X(8, 32, 0)
 
-// Shapes of the multi-instance (persistent) construction kernel.
-#define ACO_BATCH_SHAPES_4B(X) \
-  X(1, 1, 1) X(1, 2, 1) X(1, 4, 1) X(1, 8, 1) X(1, 12, 1) X(2, 8, 1) X(2, 12, 1) X(4, 10, 1) X(1, 40, 0)
+// Shapes of the multi-instance (persistent) construction kernel; a batch
+// groups its instances into size classes, one shape (and launch) per class.
+#define ACO_BATCH_SHAPES_4B(X)                                                                 \
+  X(1, 1, 1) X(1, 2, 1) X(1, 4, 1) X(1, 8, 1) X(1, 12, 1) X(2, 8, 1) X(2, 12, 1) X(4, 10, 1)   \
+  X(4, 12, 1) X(4, 20, 0) X(8, 32, 0)
 
-#define ACO_BATCH_SHAPES_2B(X) \
-  X(1, 1, 1) X(1, 2, 1) X(1, 4, 1) X(1, 8, 1) X(1, 12, 1) X(2, 10, 1) X(1, 20, 0) X(2, 16, 0)
+#define ACO_BATCH_SHAPES_2B(X)                                                                 \
+  X(1, 1, 1) X(1, 2, 1) X(1, 4, 1) X(1, 8, 1) X(1, 12, 1) X(2, 8, 1) X(2, 10, 1) X(4, 10, 1)   \
+  X(4, 12, 1) X(4, 16, 0) X(8, 32, 0)

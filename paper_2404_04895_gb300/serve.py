@@ -1,0 +1,196 @@
+"""Continuous-batching solve server over the batch C API.
+
+Requests (TSP instances with an iteration budget) arrive over time.  The loop
+admits arrived requests in arrival order as soon as a batch slot and arena
+memory for their workspace are free (memory-gated admission; the head of the
+queue waits rather than being overtaken), advances every admitted instance by
+one iteration per batched step -- requests that arrived while others were on
+the GPU join the next step, so their work overlaps on the device -- and
+retires finished requests between steps, reading their best tour and freeing
+their slot and memory.  Each instance's state (tau, M_p, tours, best) stays
+resident on the device from admission to retirement.
+
+  python -m paper_2404_04895_gb300.serve --requests 200 --rate 50
+
+prints one JSON line: p50/p99 latency, throughput, offered and served load.
+"""
+import argparse
+import dataclasses
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import instances
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds from the start of the trace
+    coords: np.ndarray      # n x 2 fp32
+    m: int
+    seed: int
+    iters: int
+    params: dict = dataclasses.field(default_factory=dict)
+    admitted: float = None
+    finished: float = None
+    best_len: float = None
+    tour: np.ndarray = None
+
+    @property
+    def n(self):
+        return self.coords.shape[0]
+
+    @property
+    def ant_steps(self):
+        return self.iters * self.m * (self.n - 1)
+
+    @property
+    def latency(self):
+        return None if self.finished is None else self.finished - self.arrival
+
+
+def poisson_requests(count, rate, nmin, nmax, iters, mmax=1024, seed=11, **params):
+    """Arrivals of a Poisson process at `rate` per second, sizes log-uniform."""
+    t, sizes = instances.poisson_trace(count, rate, nmin, nmax, seed=seed)
+    reqs = []
+    for i, (ti, n) in enumerate(zip(t, sizes)):
+        n = int(n)
+        reqs.append(Request(rid=i, arrival=float(ti), coords=instances.uniform(n, 10_000 + i),
+                            m=min(n, mmax), seed=i, iters=iters, params=dict(params)))
+    return reqs
+
+
+class Server:
+    """Admission, batched stepping and retirement around one batch.
+
+    batch: an object with add(coords, m, iters, **kw) -> slot or None,
+    step(k), status(slot) -> (iterations, finished), best(slot), remove(slot),
+    sync() -- paper_2404_04895_gb300.binding.Batch plus a stream sync.
+    """
+
+    def __init__(self, batch, clock=time.perf_counter, sleep=time.sleep):
+        self.batch = batch
+        self.clock = clock
+        self.sleep = sleep
+
+    def run(self, requests, realtime=True):
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        active = {}
+        done = []
+        t0 = self.clock()
+        steps = 0
+        while pending or active:
+            now = self.clock() - t0
+            # admit arrived requests in order while they fit
+            while pending and (pending[0].arrival <= now or not realtime):
+                r = pending[0]
+                slot = self.batch.add(r.coords, r.m, iters=r.iters, seed=r.seed, **r.params)
+                if slot is None:
+                    break
+                pending.pop(0)
+                r.admitted = self.clock() - t0
+                active[slot] = r
+            if not active:
+                if pending:
+                    if not realtime:
+                        raise RuntimeError(f"request {pending[0].rid} (n={pending[0].n}) does not fit an empty batch")
+                    self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
+                continue
+            self.batch.step(1)
+            steps += 1
+            finished = [s for s in active if self.batch.status(s)[1]]
+            if finished:
+                self.batch.sync()
+                t = self.clock() - t0
+                for s in finished:
+                    r = active.pop(s)
+                    r.tour, r.best_len = self.batch.best(s)
+                    r.finished = t
+                    self.batch.remove(s)
+                    done.append(r)
+        wall = self.clock() - t0
+        return done, wall, steps
+
+
+def summarize(done, wall):
+    lat = np.array([r.latency for r in done])
+    ant_steps = float(sum(r.ant_steps for r in done))
+    span = max(r.arrival for r in done) - min(r.arrival for r in done) if len(done) > 1 else 0.0
+    offered_rate = (len(done) - 1) / span if span > 0 else float("nan")
+    return {
+        "requests": len(done),
+        "latency_p50_s": float(np.percentile(lat, 50)),
+        "latency_p99_s": float(np.percentile(lat, 99)),
+        "latency_mean_s": float(lat.mean()),
+        "throughput_req_per_s": len(done) / wall,
+        "ant_steps_per_s": ant_steps / wall,
+        "offered_req_per_s": offered_rate,
+        "offered_ant_steps_per_s": ant_steps / span if span > 0 else float("nan"),
+        "offered_over_served": (ant_steps / span) / (ant_steps / wall) if span > 0 else float("nan"),
+        "wall_s": wall,
+    }
+
+
+class GpuBatch:
+    """binding.Batch on its own stream, with the sync the server needs."""
+
+    def __init__(self, arena_bytes, max_slots, prec):
+        import torch
+
+        from . import binding
+        binding.lib()
+        self.torch = torch
+        self.stream = torch.cuda.Stream()
+        self.b = binding.Batch(max_slots, arena_bytes, prec=prec, stream=self.stream)
+
+    def add(self, coords, m, iters, **kw):
+        return self.b.add(coords, m, iters=iters, **kw)
+
+    def step(self, k):
+        self.b.step(k)
+
+    def status(self, slot):
+        return self.b.status(slot)
+
+    def best(self, slot):
+        return self.b.best(slot)
+
+    def remove(self, slot):
+        self.b.remove(slot)
+
+    def sync(self):
+        self.stream.synchronize()
+
+    def close(self):
+        self.b.close()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--nmin", type=int, default=50)
+    ap.add_argument("--nmax", type=int, default=10000)
+    ap.add_argument("--iters", type=int, default=100)
+    ap.add_argument("--prec", default="bf16")
+    ap.add_argument("--arena-gb", type=float, default=80.0)
+    ap.add_argument("--slots", type=int, default=1024)
+    ap.add_argument("--rho", type=float, default=0.1)
+    args = ap.parse_args(argv)
+    reqs = poisson_requests(args.requests, args.rate, args.nmin, args.nmax, args.iters, rho=args.rho)
+    gb = GpuBatch(int(args.arena_gb * (1 << 30)), args.slots, args.prec)
+    done, wall, steps = Server(gb).run(reqs, realtime=True)
+    gb.close()
+    out = summarize(done, wall)
+    out.update({"config": {"requests": args.requests, "rate": args.rate, "n": [args.nmin, args.nmax],
+                           "m": "min(n, 1024)", "iters": args.iters, "P_dtype": args.prec,
+                           "arena_gb": args.arena_gb}, "batched_steps": steps})
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,35 @@
+"""Continuous batching on the GPU: requests that arrive while others run are
+admitted as memory frees up and share batched steps, and every request's
+result equals the result of solving it alone, bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2404_04895_gb300 import binding as B
+from paper_2404_04895_gb300 import serve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    B.lib()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_served_results_equal_solo_results(prec):
+    reqs = serve.poisson_requests(14, 400.0, 20, 400, 15, mmax=48, seed=5, rho=0.2)
+    arena = 3 * B.instance_bytes(400, 48) + (1 << 20)   # a few requests at a time
+    gb = serve.GpuBatch(arena, 16, prec)
+    done, wall, steps = serve.Server(gb).run(reqs, realtime=True)
+    gb.close()
+    assert sorted(r.rid for r in done) == list(range(14))
+    assert steps < sum(r.iters for r in done)            # requests shared steps
+    for r in done:
+        s = B.Solver(r.coords, m=r.m, prec=prec, seed=r.seed, rho=0.2, stream=torch.cuda.Stream())
+        tour, L = s.iterate(r.iters).best()
+        s.close()
+        assert r.best_len == L and np.array_equal(r.tour, tour), r.rid
+    stats = serve.summarize(done, wall)
+    assert stats["latency_p99_s"] >= stats["latency_p50_s"] > 0

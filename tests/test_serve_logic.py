@@ -1,0 +1,98 @@
+"""Host logic of the continuous-batching server, on a fake batch (no GPU):
+arrival-ordered, memory-gated admission, joins between steps, retirement
+frees memory, latency accounting."""
+import numpy as np
+
+from paper_2404_04895_gb300 import serve
+
+
+class FakeBatch:
+    def __init__(self, capacity):
+        self.capacity, self.used, self.slots, self.next = capacity, 0, {}, 0
+        self.log = []
+
+    def add(self, coords, m, iters, **kw):
+        need = coords.shape[0]
+        if self.used + need > self.capacity:
+            return None
+        s = self.next
+        self.next += 1
+        self.slots[s] = [need, iters, 0]
+        self.used += need
+        self.log.append(("add", s))
+        return s
+
+    def step(self, k):
+        for v in self.slots.values():
+            if v[2] < v[1]:
+                v[2] += k
+        self.log.append(("step", sorted(s for s, v in self.slots.items() if v[2] <= v[1])))
+
+    def status(self, s):
+        v = self.slots[s]
+        return v[2], v[2] >= v[1]
+
+    def best(self, s):
+        return np.zeros(self.slots[s][0], np.int32), float(s)
+
+    def remove(self, s):
+        self.used -= self.slots.pop(s)[0]
+
+    def sync(self):
+        pass
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, d):
+        self.t += max(d, 1e-6)
+
+
+def _req(i, arrival, n, iters):
+    return serve.Request(rid=i, arrival=arrival, coords=np.zeros((n, 2), np.float32), m=4, seed=i, iters=iters)
+
+
+def test_fifo_memory_gated_admission_and_joins():
+    clock = FakeClock()
+    fb = FakeBatch(capacity=100)
+    srv = serve.Server(fb, clock=clock, sleep=clock.sleep)
+    reqs = [_req(0, 0.0, 60, 3), _req(1, 0.0, 60, 2), _req(2, 0.0, 30, 2), _req(3, 5.0, 10, 1)]
+    done, wall, steps = srv.run(reqs, realtime=True)
+    assert sorted(r.rid for r in done) == [0, 1, 2, 3]
+    adds = [e[1] for e in fb.log if e[0] == "add"]
+    # request 1 (60) does not fit beside request 0 (60): it waits, and request 2
+    # behind it is not admitted ahead of it (arrival order)
+    first_step = fb.log.index(("step", [0]))
+    assert fb.log[:first_step] == [("add", 0)]
+    assert adds == [0, 1, 2, 3]
+    by = {r.rid: r for r in done}
+    assert by[1].admitted >= by[0].admitted and by[2].admitted >= by[1].admitted
+    assert all(r.latency >= 0 and r.finished >= r.admitted >= r.arrival for r in done)
+    assert fb.used == 0
+
+
+def test_summary_reports_percentiles_and_load():
+    rs = []
+    for i in range(10):
+        r = _req(i, float(i), 10, 5)
+        r.admitted, r.finished = float(i), float(i) + 1 + i % 3
+        rs.append(r)
+    s = serve.summarize(rs, wall=12.0)
+    assert s["requests"] == 10
+    assert 1.0 <= s["latency_p50_s"] <= 3.0 and s["latency_p99_s"] <= 3.0
+    assert abs(s["throughput_req_per_s"] - 10 / 12.0) < 1e-12
+    assert s["offered_req_per_s"] == 1.0
+
+
+def test_poisson_trace_shapes():
+    reqs = serve.poisson_requests(50, 50.0, 50, 10000, 100)
+    ns = np.array([r.n for r in reqs])
+    assert ns.min() >= 50 and ns.max() <= 10000
+    assert all(r.m == min(r.n, 1024) for r in reqs)
+    gaps = np.diff([r.arrival for r in reqs])
+    assert np.all(gaps >= 0) and 0.005 < gaps.mean() < 0.05
