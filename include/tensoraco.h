@@ -130,10 +130,12 @@ typedef struct {
   int deposit;              /* ACO_DEPOSIT_DET / ACO_DEPOSIT_ATOMIC */
   float gamma_max, gamma_min;
   int gamma_T;
+  int cand_lists;           /* 1: candidate-list fast path (exact), 0: full scan only */
 } aco_params;
 
 /* Fill *p with defaults: alpha 1, beta 2, rho 0.5, Q 1, tau0 1, seed 0, FP32,
- * IR, deterministic deposit, gamma 1.5 -> 0.5 over 100 iterations. */
+ * IR, deterministic deposit, gamma 1.5 -> 0.5 over 100 iterations, candidate
+ * lists on. */
 int aco_params_default(aco_params* p);
 
 /* Create a solver for p->n cities given coords_host (n x 2 fp32).  Workspace:
@@ -247,6 +249,23 @@ int aco_op_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t
 int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed,
                            uint32_t it, int32_t* tours_dev, int32_t* err_dev, int warps,
                            int chunks, int mode, void* stream);
+
+/* Candidate lists of M_p, the exact fast path of the construction step: for
+ * each row i, lcnt_dev[i] <= 64 entries lists_dev[i*64 + q] = (fp32 bits of
+ * the stored value, column) -- every column whose value is above the row's
+ * 32nd largest, ties at it in column order -- and lkey_dev[i] bounds the
+ * score key (fp32 bits + 1) of every column not listed.  lists_dev: n*64
+ * pairs of u32, 8-byte aligned; lcnt_dev, lkey_dev: n entries. */
+int aco_op_build_lists(const void* P_dev, int prec, int n, int ld, void* lists_dev, int* lcnt_dev,
+                       uint32_t* lkey_dev, void* stream);
+
+/* aco_op_construct_shape with candidate lists (from aco_op_build_lists on the
+ * same M_p; lists_dev NULL: full scan only).  The tours are the same either
+ * way: a step is taken from the list only when no unlisted column can win. */
+int aco_op_construct_ex(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed,
+                        uint32_t it, int32_t* tours_dev, int32_t* err_dev, const void* lists_dev,
+                        const int* lcnt_dev, const uint32_t* lkey_dev, int warps, int chunks,
+                        int mode, void* stream);
 
 /* Eq. 3 and the index mapping of Eq. 2: L_k = sum_t D[p_t][p_{t+1 mod n}] in
  * fp64 in t order (L_dev, m), c_k = fl64(Q / L_k) (c_dev, m), and for every

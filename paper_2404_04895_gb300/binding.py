@@ -31,7 +31,7 @@ class Params(C.Structure):
                 ("rho", C.c_float), ("Q", C.c_float), ("tau0", C.c_float),
                 ("seed", C.c_uint64), ("prec", C.c_int), ("roulette", C.c_int),
                 ("deposit", C.c_int), ("gamma_max", C.c_float), ("gamma_min", C.c_float),
-                ("gamma_T", C.c_int)]
+                ("gamma_T", C.c_int), ("cand_lists", C.c_int)]
 
 
 _lib = None
@@ -82,6 +82,8 @@ _SIGS = {
     "aco_op_build_P": (i32, [v, v, i32, i32, i32, f32, i32, v, v]),
     "aco_op_construct": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, v]),
     "aco_op_construct_shape": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, i32, i32, i32, v]),
+    "aco_op_build_lists": (i32, [v, i32, i32, i32, v, v, v, v]),
+    "aco_op_construct_ex": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, v, v, v, i32, i32, i32, v]),
     "aco_op_tour_length": (i32, [v, i32, v, i32, f32, v, v, v, v]),
     "aco_op_best": (i32, [v, v, i32, i32, v, v, v]),
     "aco_op_deposit": (i32, [v, i32, i32, v, v, i32, f32, v]),
@@ -166,6 +168,16 @@ def op_construct(P, prec, n, ld, m, seed, it, tours, err=None, shape=None, strea
              shape[0], shape[1], shape[2], stream_ptr(stream))
 
 
+def op_build_lists(P, prec, n, ld, lists, lcnt, lkey, stream=None):
+    call("aco_op_build_lists", ptr(P), prec, n, ld, ptr(lists), ptr(lcnt), ptr(lkey), stream_ptr(stream))
+
+
+def op_construct_ex(P, prec, n, ld, m, seed, it, tours, lists=None, lcnt=None, lkey=None, err=None,
+                    shape=(0, 0, 0), stream=None):
+    call("aco_op_construct_ex", ptr(P), prec, n, ld, m, seed, it, ptr(tours), ptr(err), ptr(lists),
+         ptr(lcnt), ptr(lkey), shape[0], shape[1], shape[2], stream_ptr(stream))
+
+
 def op_tour_length(D, n, tours, m, Q, L, c=None, nbr=None, stream=None):
     call("aco_op_tour_length", ptr(D), n, ptr(tours), m, Q, ptr(L), ptr(c), ptr(nbr), stream_ptr(stream))
 
@@ -233,7 +245,7 @@ class Solver:
 
     def __init__(self, coords, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec="fp32",
                  roulette="ir", deposit="det", gamma_max=1.5, gamma_min=0.5, gamma_T=100,
-                 tau0=1.0, workspace="torch", stream=None):
+                 tau0=1.0, workspace="torch", stream=None, cand_lists=True):
         import torch
         xy = _host(coords, np.float32)
         n = xy.shape[0]
@@ -245,6 +257,7 @@ class Solver:
         p.roulette = ROULETTE[roulette] if isinstance(roulette, str) else roulette
         p.deposit = DEPOSIT[deposit] if isinstance(deposit, str) else deposit
         p.gamma_max, p.gamma_min, p.gamma_T = gamma_max, gamma_min, gamma_T
+        p.cand_lists = int(cand_lists)
         self.params = p
         self.n, self.m = n, m
         self.stream = stream
@@ -325,7 +338,7 @@ class Solver:
 
 
 def make_params(n, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec="fp32", roulette="ir",
-                deposit="det", gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0):
+                deposit="det", gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0, cand_lists=True):
     p = Params()
     call("aco_params_default", C.byref(p))
     p.n, p.m, p.alpha, p.beta = n, m, alpha, beta
@@ -334,6 +347,7 @@ def make_params(n, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec="fp32", roul
     p.roulette = ROULETTE[roulette] if isinstance(roulette, str) else roulette
     p.deposit = DEPOSIT[deposit] if isinstance(deposit, str) else deposit
     p.gamma_max, p.gamma_min, p.gamma_T = gamma_max, gamma_min, gamma_T
+    p.cand_lists = int(cand_lists)
     return p
 
 

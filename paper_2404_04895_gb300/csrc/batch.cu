@@ -45,6 +45,21 @@ __global__ void __launch_bounds__(256) batch_build_P_kernel(const InstDev* __res
                     inv_gamma, static_cast<char*>(I.P) + (size_t)row * I.ld * eb, red);
 }
 
+template <int PREC>
+__global__ void __launch_bounds__(256) batch_build_lists_kernel(const InstDev* __restrict__ insts,
+                                                                const int* __restrict__ row_off,
+                                                                int count) {
+  __shared__ uint32_t scratch[kListScratchWords];
+  const int r = blockIdx.x;
+  const int i = find_instance(row_off, count, r);
+  const InstDev& I = insts[i];
+  if (!I.lists) return;
+  const int row = r - __ldg(row_off + i);
+  const size_t eb = PREC == ACO_FP32 ? 4 : 2;
+  build_list_row<PREC>(static_cast<const char*>(I.P) + (size_t)row * I.ld * eb, I.n,
+                       I.lists + (size_t)row * kListMax, I.lcnt + row, I.lkey + row, scratch);
+}
+
 __global__ void __launch_bounds__(256) batch_tour_length_kernel(const InstDev* __restrict__ insts,
                                                                 const int* __restrict__ ant_off,
                                                                 int count, int total) {
@@ -180,6 +195,7 @@ struct aco_batch {
     ConstructShape s;
   };
   std::vector<Class> classes;     // contiguous ranges of `active` sharing a shape
+  bool lean = false;              // all active instances use candidate lists: lean kernel
   bool tables_ok = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -240,8 +256,11 @@ static int batch_refresh(aco_batch* b) {
     ACO_CUDA_TRY(cudaMemcpyAsync(b->d_ant_off, ant_off.data(), sizeof(int) * (cnt + 1), cudaMemcpyHostToDevice, b->stream));
     ACO_CUDA_TRY(cudaStreamSynchronize(b->stream));  // pageable sources
   }
-  // size classes: consecutive instances (n descending) sharing a shape
+  // lean kernel when every active instance has candidate lists (and no shape is forced);
+  // else size classes: consecutive instances (n descending) sharing a shape
   const int eb = b->prec == ACO_FP32 ? 4 : 2;
+  b->lean = cnt > 0 && b->shape.warps == 0 && b->max_n <= kLeanMaxN;
+  for (int q = 0; q < cnt; ++q) b->lean = b->lean && b->slots[b->active[q]].p.cand_lists;
   b->classes.clear();
   for (int q = 0; q < cnt; ++q) {
     const Slot& sl = b->slots[b->active[q]];
@@ -283,23 +302,40 @@ static int batch_enqueue(aco_batch* b) {
       batch_build_P_kernel<ACO_FP16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
   }
   ACO_CHECK_LAUNCH("batch_build_P_kernel");
-  ACO_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int) * b->classes.size(), st));
-  for (size_t ci = 0; ci < b->classes.size(); ++ci) {
+  switch (b->prec) {
+    case ACO_FP32:
+      batch_build_lists_kernel<ACO_FP32><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
+      break;
+    case ACO_BF16:
+      batch_build_lists_kernel<ACO_BF16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
+      break;
+    default:
+      batch_build_lists_kernel<ACO_FP16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
+  }
+  ACO_CHECK_LAUNCH("batch_build_lists_kernel");
+  ACO_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int) * std::max<size_t>(1, b->classes.size()), st));
+  if (b->lean) {  // one persistent lean launch over every ant of every instance
+    const int rc = launch_batch_construct_lean(b->d_insts, b->d_ant_off, cnt, b->total_ants, b->d_counter,
+                                               b->d_err, b->prec, b->max_n, b->num_sms, st);
+    if (rc) return rc;
+  }
+  for (size_t ci = 0; ci < (b->lean ? 0 : b->classes.size()); ++ci) {
     const auto& c = b->classes[ci];
     const ConstructShape s = c.s;
     const InstDev* ins = b->d_insts + c.first;
     const int* off = b->d_ant_off + c.first;
     int* ctr = b->d_counter + ci;
+    const int bitmap = ((b->slots[b->active[c.first]].p.n + 127) / 128) * 16;  // largest n of the class
     int rc;
     if (b->prec == ACO_FP32)
       rc = launch_batch_construct_f32(ins, off, c.count, c.total, ctr, b->d_err, s.warps, s.chunks, s.mode,
-                                      b->num_sms, st);
+                                      bitmap, b->num_sms, st);
     else if (b->prec == ACO_BF16)
       rc = launch_batch_construct_bf16(ins, off, c.count, c.total, ctr, b->d_err, s.warps, s.chunks, s.mode,
-                                       b->num_sms, st);
+                                       bitmap, b->num_sms, st);
     else
       rc = launch_batch_construct_f16(ins, off, c.count, c.total, ctr, b->d_err, s.warps, s.chunks, s.mode,
-                                      b->num_sms, st);
+                                      bitmap, b->num_sms, st);
     if (rc) return rc;
   }
   batch_tour_length_kernel<<<(b->total_ants + 7) / 8, 256, 0, st>>>(b->d_insts, b->d_ant_off, cnt,

@@ -23,6 +23,9 @@ struct InstDev {
   double* best_len;               // 1
   uint32_t* it;                   // iterations completed (device counter)
   const float* sched;             // AdaIR 1/gamma per iteration (n_sched entries)
+  uint2* lists;                   // candidate lists, n x kListMax (nullptr: full scan only)
+  int* lcnt;                      // n
+  uint32_t* lkey;                 // n
 };
 
 // Index of the instance whose half-open range [off[i], off[i+1]) holds x

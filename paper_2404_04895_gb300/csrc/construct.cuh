@@ -27,6 +27,7 @@
 
 #include "batch.cuh"
 #include "common.cuh"
+#include "steps.cuh"
 
 namespace aco {
 
@@ -148,11 +149,23 @@ constexpr int MODE_DIRECT = 1;
 // The walk of ant k (all threads of the CTA call it together): start city, then
 // n-1 steps over M_p (P, n x ld), tour written to tour[0..n-1].  red_s/red_j:
 // [2][W] shared scratch; srow: [KC * 32 * W] shared chunks (MODE_STAGED only).
+//
+// Candidate lists (one warp per ant only; lists == nullptr disables them):
+// each step first scores the unvisited entries of row cur's list (see
+// build_list_row); when the best listed score key exceeds the row's bound the
+// step is decided -- no unlisted column can reach or tie that score -- and the
+// full scan is skipped; otherwise the full scan runs, seeded with the list's
+// best candidate.  svis: n-bit shared visited bitmap the list phase reads.
 template <int PREC, int W, int KC, int MODE>
 __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n, int ld, uint2 key,
                                               uint32_t it, int k, int32_t* __restrict__ tour,
                                               int32_t* __restrict__ err, uint32_t (*red_s)[W],
-                                              int (*red_j)[W], uint4* __restrict__ srow) {
+                                              int (*red_j)[W], uint4* __restrict__ srow,
+                                              const uint2* __restrict__ lists,
+                                              const int* __restrict__ lcnt,
+                                              const uint32_t* __restrict__ lkey,
+                                              uint32_t* __restrict__ svis) {
+  const bool use_list = W == 1 && lists != nullptr;
   using E = Elem<PREC>;
   constexpr int V = E::V;
   constexpr int G = V / 4;                // 4-column groups per chunk (one Philox block each)
@@ -214,6 +227,12 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
   int cur = start_city(key, it, (uint32_t)k, n);
   if (gl == 0) tour[0] = cur;
   mark(cur);
+  if (use_list) {
+    for (int q = lane; q < (n + 31) / 32; q += 32) svis[q] = 0u;
+    __syncwarp();
+    if (lane == 0) svis[cur >> 5] |= 1u << (cur & 31);
+    __syncwarp();
+  }
 
   uint4 d[KC];  // MODE_DIRECT: the thread's chunks of the current row
 #pragma unroll
@@ -222,6 +241,42 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
   for (int t = 1; t < n; ++t) {
     const char* __restrict__ row = P + (size_t)cur * row_bytes;
     const uint4* __restrict__ row4 = reinterpret_cast<const uint4*>(row);
+    float bs = -1.0f;
+    int bj = 0x7FFFFFFF;
+    int next = -1;
+
+    // 0. candidate list of row cur, sorted by value: rounds of 32 entries; after
+    //    each round the next unscored entry (or the row's bound) bounds every
+    //    column not scored yet
+    if (use_list) {
+      const uint2* __restrict__ lrow = lists + (size_t)cur * kListMax;
+      uint2 e[kListMax / 32];
+#pragma unroll
+      for (int r = 0; r < kListMax / 32; ++r) e[r] = __ldg(lrow + 32 * r + lane);  // allocated rows
+      const int lc = __ldg(lcnt + cur);
+      const uint32_t lb = __ldg(lkey + cur);
+#pragma unroll
+      for (int r = 0; r < kListMax / 32; ++r) {
+        if (32 * r >= lc) break;
+        const bool valid = 32 * r + lane < lc;       // slots past the count hold stale data
+        const int j = valid ? (int)e[r].y : 0;
+        if (valid && !((svis[j >> 5] >> (j & 31)) & 1u)) {
+          const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it), key);
+          const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
+          better(__fmul_rn(uniform01(w), __uint_as_float(e[r].x)), j, bs, bj);
+        }
+        const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
+        uint32_t rest = lb;
+        if (r + 1 < kListMax / 32 && 32 * (r + 1) < lc)
+          rest = max(rest, __shfl_sync(ACO_FULL_MASK, e[r + 1 < kListMax / 32 ? r + 1 : r].x, 0) + 1u);
+        if (lk > rest) {
+          next = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == lk ? (uint32_t)bj : 0x7FFFFFFFu);
+          break;
+        }
+      }
+    }
+
+    if (next < 0) {  // full scan (seeded with the list's best candidate, if any)
 
     // 1. fetch every chunk with an unvisited column, 16 bytes each
     if (MODE == MODE_DIRECT) {
@@ -265,8 +320,6 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
       top = max(top, a1[q]);
     }
 
-    float bs = -1.0f;
-    int bj = 0x7FFFFFFF;
     auto score_group = [&](int gi) {
       const int c = gi / G, g = gi - c * G;
       const uint32_t nib = nibble(c * V + g * 4);
@@ -307,7 +360,7 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
 
     // 5. argmax across the warp (largest score, then lowest index), then across warps
     uint32_t wkey = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
-    int next = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == wkey ? (uint32_t)bj : 0x7FFFFFFFu);
+    next = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == wkey ? (uint32_t)bj : 0x7FFFFFFFu);
     if (W > 1) {
       if (lane == 0) {
         red_s[t & 1][wi] = wkey;
@@ -326,6 +379,7 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
         }
       }
     }
+    }  // full scan
 
     if (next < 0 || next >= n) {  // no unvisited city found: cannot happen for valid input
       if (gl == 0 && err) atomicExch(err, 1);
@@ -333,22 +387,35 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
     }
     if (gl == 0) tour[t] = next;
     mark(next);
+    if (use_list) {
+      if (lane == 0) svis[next >> 5] |= 1u << (next & 31);
+      __syncwarp();
+    }
     cur = next;
   }
+}
+
+// Dynamic shared memory: MODE_STAGED row chunks, then the list phase's bitmap.
+template <int W, int KC, int MODE>
+__host__ __device__ constexpr int srow_chunks() {
+  return MODE == MODE_STAGED ? KC * 32 * W : 0;
 }
 
 template <int PREC, int W, int KC, int MODE>
 __global__ void __launch_bounds__(32 * W) construct_kernel(
     const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it_arg,
-    const uint32_t* __restrict__ it_dev, int32_t* __restrict__ tours, int32_t* __restrict__ err) {
+    const uint32_t* __restrict__ it_dev, int32_t* __restrict__ tours, int32_t* __restrict__ err,
+    const uint2* __restrict__ lists, const int* __restrict__ lcnt,
+    const uint32_t* __restrict__ lkey) {
   __shared__ uint32_t red_s[2][W];
   __shared__ int red_j[2][W];
-  extern __shared__ __align__(16) uint4 srow[];  // MODE_STAGED: [KC * 32 * W] chunks of the row
+  extern __shared__ __align__(16) uint4 srow[];
+  uint32_t* svis = reinterpret_cast<uint32_t*>(srow + srow_chunks<W, KC, MODE>());
   const int k = blockIdx.x;
   if (k >= m) return;
   const uint32_t it = it_dev ? *it_dev : it_arg;
   construct_ant<PREC, W, KC, MODE>(Pv, n, ld, key, it, k, tours + (size_t)k * n, err, red_s, red_j,
-                                   srow);
+                                   srow, lists, lcnt, lkey, svis);
 }
 
 // Multi-instance construction: a persistent grid pulls work items (instance,
@@ -366,6 +433,7 @@ __global__ void __launch_bounds__(32 * W) batch_construct_kernel(
   __shared__ int red_j[2][W];
   __shared__ int item_s;
   extern __shared__ __align__(16) uint4 srow[];
+  uint32_t* svis = reinterpret_cast<uint32_t*>(srow + srow_chunks<W, KC, MODE>());
   for (;;) {
     if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
     __syncthreads();
@@ -376,7 +444,7 @@ __global__ void __launch_bounds__(32 * W) batch_construct_kernel(
     const InstDev& I = insts[i];
     const int k = base + item - __ldg(ant_off + i);
     construct_ant<PREC, W, KC, MODE>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err,
-                                     red_s, red_j, srow);
+                                     red_s, red_j, srow, I.lists, I.lcnt, I.lkey, svis);
   }
 }
 
@@ -384,9 +452,10 @@ __global__ void __launch_bounds__(32 * W) batch_construct_kernel(
 // The row buffer is KC * 32 * W * 16 bytes of dynamic shared memory.
 #define ACO_CONSTRUCT_CASE(PREC, W, KC, MODE)                                              \
   if (warps == W && chunks == KC && mode == MODE) {                                         \
-    const size_t smem_ = MODE == MODE_STAGED ? (size_t)KC * 32 * W * 16 : 0;                 \
-    construct_kernel<PREC, W, KC, MODE><<<m, 32 * W, smem_, st>>>(P, n, ld, m, key, it, it_dev, \
-                                                                  tours, err);              \
+    const size_t smem_ = (size_t)srow_chunks<W, KC, MODE>() * 16 +                           \
+                         (lists ? (size_t)((n + 127) / 128) * 16 : 0);                      \
+    construct_kernel<PREC, W, KC, MODE><<<m, 32 * W, smem_, st>>>(                          \
+        P, n, ld, m, key, it, it_dev, tours, err, W == 1 ? lists : nullptr, lcnt, lkey);     \
     const cudaError_t e_ = cudaGetLastError();                                              \
     return e_ == cudaSuccess ? ACO_OK : cuda_error(e_, "construct_kernel launch");          \
   }
@@ -397,13 +466,14 @@ namespace aco {
 #define ACO_BATCH_CONSTRUCT_CASE(PREC, W, KC, MODE)                                          \
   if (warps == W && chunks == KC && mode == MODE) {                                         \
     auto kern = batch_construct_kernel<PREC, W, KC, MODE>;                                  \
-    const size_t smem_ = MODE == MODE_STAGED ? (size_t)KC * 32 * W * 16 : 0;                 \
+    const size_t smem_ = (size_t)srow_chunks<W, KC, MODE>() * 16 + (size_t)bitmap_bytes;    \
+    static size_t occ_smem = (size_t)-1;                                                    \
     static int blocks_per_sm = 0;                                                           \
-    if (!blocks_per_sm) {                                                                   \
-      if (MODE == MODE_STAGED)                                                              \
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_); \
+    if (occ_smem != smem_) {                                                                \
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_);  \
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 32 * W, smem_);  \
       if (blocks_per_sm < 1) blocks_per_sm = 1;                                             \
+      occ_smem = smem_;                                                                     \
     }                                                                                       \
     int grid_ = blocks_per_sm * num_sms;                                                    \
     if (grid_ > total) grid_ = total;                                                       \
@@ -415,10 +485,10 @@ namespace aco {
 
 // Opt every compiled shape in to its dynamic shared-memory size (once).
 #define ACO_CONSTRUCT_PREPARE(PREC, W, KC, MODE)                                           \
-  if (MODE == MODE_STAGED) {                                                                 \
+  {                                                                                          \
     const cudaError_t e_ = cudaFuncSetAttribute(construct_kernel<PREC, W, KC, MODE>,         \
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                KC * 32 * W * 16);                           \
+                                                srow_chunks<W, KC, MODE>() * 16 + 8192);     \
     if (e_ != cudaSuccess) return cuda_error(e_, "cudaFuncSetAttribute(construct_kernel)");  \
   }
 }  // namespace aco

@@ -7,7 +7,8 @@ namespace aco {
 
 int launch_construct_f16(const void* P, int n, int ld, int m, uint2 key, uint32_t it,
                          const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
-                         int chunks, int mode, cudaStream_t st) {
+                         int chunks, int mode, const uint2* lists,
+                         const int* lcnt, const uint32_t* lkey, cudaStream_t st) {
 #define X(W, KC, MODE) ACO_CONSTRUCT_CASE(ACO_FP16, W, KC, MODE)
   ACO_SHAPES_2B(X)
 #undef X
@@ -24,7 +25,7 @@ int prepare_construct_f16() {
 
 int launch_batch_construct_f16(const InstDev* insts, const int* ant_off, int count, int total,
                                 int* counter, int32_t* err, int warps, int chunks, int mode,
-                                int num_sms, cudaStream_t st) {
+                                int bitmap_bytes, int num_sms, cudaStream_t st) {
 #define X(W, KC, MODE) ACO_BATCH_CONSTRUCT_CASE(ACO_FP16, W, KC, MODE)
   ACO_BATCH_SHAPES_2B(X)
 #undef X

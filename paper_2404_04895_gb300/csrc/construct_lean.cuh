@@ -1,0 +1,228 @@
+// Lean tour construction: one warp per ant, candidate lists first, a compact
+// full scan only when the list cannot decide a step (Sec. 2.2 + 2.4).
+//
+// State is the ant's visited bitmap in shared memory (n bits) and its current
+// city; no per-lane visited registers, so the step stays short and light.
+//   list step   the unvisited entries of row cur's sorted candidate list are
+//               scored in rounds of 32 (one Philox4x32-10 block per entry);
+//               after each round the next unscored entry -- or the row's bound
+//               -- bounds every column not yet scored, and the step is decided
+//               once the best score key exceeds that bound (see build_list_row)
+//   full scan   (list undecided) the row's chunks with an unvisited column are
+//               staged in shared memory by cp.async; each 4-column group's raw
+//               maximum is compared with the threshold -- the list's best score,
+//               else the warp's best exact score of each lane's largest group --
+//               and only groups reaching it are scored exactly.
+// Either way the chosen city is argmax over unvisited j of fl32(r_j * p_j),
+// lowest j on ties, exactly as a plain scan of every candidate chooses.
+#pragma once
+
+#include "construct.cuh"
+
+namespace aco {
+
+// Dynamic shared memory of the lean kernel for n cities at element size eb:
+// the staged row (chunks rounded to whole warps) and the visited bitmap.
+__host__ __device__ inline size_t lean_smem_bytes(int n, int eb) {
+  const int V = 16 / eb;
+  const int chunks = (n + V - 1) / V;
+  const int kc = (chunks + 31) / 32;
+  return (size_t)kc * 32 * 16 + (size_t)((n + 127) / 128) * 16;
+}
+
+// Largest n the lean kernel serves (shared memory and 2 x 64-bit group masks).
+__host__ __device__ inline int lean_max_n(int eb) { return eb == 4 ? 16384 : 16384; }
+
+template <int PREC>
+__device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, int n, int ld, uint2 key,
+                                                   uint32_t it, int k, int32_t* __restrict__ tour,
+                                                   int32_t* __restrict__ err,
+                                                   const uint2* __restrict__ lists,
+                                                   const int* __restrict__ lcnt,
+                                                   const uint32_t* __restrict__ lkey,
+                                                   uint4* __restrict__ srow, uint32_t* __restrict__ svis) {
+  using E = Elem<PREC>;
+  constexpr int V = E::V;
+  constexpr int G = V / 4;
+  constexpr uint32_t VMASK = (1u << V) - 1u;
+  const int lane = threadIdx.x & 31;
+  const char* __restrict__ P = static_cast<const char*>(Pv);
+  const size_t row_bytes = (size_t)ld * E::BYTES;
+  const int nchunks = (n + V - 1) / V;
+  const int kc = (nchunks + 31) / 32;  // chunks per lane
+  const int nwords = (n + 31) / 32;
+
+  // visited bits of the 4 columns of the group starting at j (columns >= n count as visited)
+  auto group_nibble = [&](int j) -> uint32_t {
+    uint32_t nib = (svis[j >> 5] >> (j & 31)) & 0xFu;
+    if (j + 4 > n) nib |= (0xFu << max(0, n - j)) & 0xFu;
+    return nib;
+  };
+
+  for (int q = lane; q < nwords; q += 32) svis[q] = 0u;
+  __syncwarp();
+  int cur = start_city(key, it, (uint32_t)k, n);
+  if (lane == 0) {
+    tour[0] = cur;
+    svis[cur >> 5] |= 1u << (cur & 31);
+  }
+  __syncwarp();
+
+  for (int t = 1; t < n; ++t) {
+    const char* __restrict__ row = P + (size_t)cur * row_bytes;
+    float bs = -1.0f;
+    int bj = 0x7FFFFFFF;
+    int next = -1;
+    auto score4 = [&](int j0, float4 p, uint32_t nib) {
+      const uint4 x = philox(make_uint4((uint32_t)(j0 >> 2), (uint32_t)t, (uint32_t)k, it), key);
+      if (!(nib & 1u)) better(__fmul_rn(uniform01(x.x), p.x), j0, bs, bj);
+      if (!(nib & 2u)) better(__fmul_rn(uniform01(x.y), p.y), j0 + 1, bs, bj);
+      if (!(nib & 4u)) better(__fmul_rn(uniform01(x.z), p.z), j0 + 2, bs, bj);
+      if (!(nib & 8u)) better(__fmul_rn(uniform01(x.w), p.w), j0 + 3, bs, bj);
+    };
+
+    // ---- list step
+    if (lists) {
+      const uint2* __restrict__ lrow = lists + (size_t)cur * kListMax;
+      uint2 e[kListMax / 32];
+#pragma unroll
+      for (int r = 0; r < kListMax / 32; ++r) e[r] = __ldg(lrow + 32 * r + lane);  // allocated rows
+      const int lc = __ldg(lcnt + cur);
+      const uint32_t lb = __ldg(lkey + cur);
+#pragma unroll
+      for (int r = 0; r < kListMax / 32; ++r) {
+        if (32 * r >= lc) break;
+        const bool valid = 32 * r + lane < lc;  // slots past the count hold stale data
+        const int j = valid ? (int)e[r].y : 0;
+        if (valid && !((svis[j >> 5] >> (j & 31)) & 1u)) {
+          const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it), key);
+          const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
+          better(__fmul_rn(uniform01(w), __uint_as_float(e[r].x)), j, bs, bj);
+        }
+        const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
+        uint32_t rest = lb;
+        if (r + 1 < kListMax / 32 && 32 * (r + 1) < lc)
+          rest = max(rest, __shfl_sync(ACO_FULL_MASK, e[r + 1 < kListMax / 32 ? r + 1 : r].x, 0) + 1u);
+        if (lk > rest) {
+          next = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == lk ? (uint32_t)bj : 0x7FFFFFFFu);
+          break;
+        }
+      }
+    }
+
+    // ---- compact full scan
+    if (next < 0) {
+      const uint4* __restrict__ row4 = reinterpret_cast<const uint4*>(row);
+      for (int c = 0; c < kc; ++c) {
+        const int cg = c * 32 + lane;
+        bool need = false;
+        if (cg < nchunks) {
+          const int j0 = cg * V;
+          uint32_t bits = (svis[j0 >> 5] >> (j0 & 31)) & VMASK;
+          if (j0 + V > n) bits |= (VMASK << (n - j0)) & VMASK;
+          need = bits != VMASK;
+        }
+        cp_async16_pred(srow + c * 32 + lane, row4 + cg, need);
+      }
+      cp_async_wait_all();  // this lane's copies only: it reads nothing else
+      // group keys: raw maximum packed with the group index (16 bits); -1 when empty
+      auto gkey = [&](int c, int g) -> int {
+        const int cg = c * 32 + lane;
+        if (cg >= nchunks) return -1;
+        const int j0 = cg * V + 4 * g;
+        if (j0 >= n || group_nibble(j0) == 0xFu) return -1;
+        const uint32_t mb = E::group_max_bits(srow[c * 32 + lane], g);
+        return (int)((mb & ~0xFFFFu) | (uint32_t)(0xFFFF - (c * G + g)));
+      };
+      uint32_t thr = bs >= 0.0f ? __float_as_uint(bs) : 0u;
+      thr = __reduce_max_sync(ACO_FULL_MASK, thr);  // the list's best score, warp-wide
+      if (thr == 0u) {
+        // no list candidate: score each lane's largest group for a threshold
+        int top = -1;
+        for (int c = 0; c < kc; ++c)
+#pragma unroll
+          for (int g = 0; g < G; ++g) top = max(top, gkey(c, g));
+        if (top >= 0) {
+          const int gi = 0xFFFF - (top & 0xFFFF);
+          const int c = gi / G, g = gi - c * G;
+          const int j0 = (c * 32 + lane) * V + 4 * g;
+          score4(j0, E::group_values(srow[c * 32 + lane], g), group_nibble(j0));
+        }
+        thr = __reduce_max_sync(ACO_FULL_MASK, bs >= 0.0f ? __float_as_uint(bs) : 0u);
+      }
+      const int thr_key = (int)(thr & ~0xFFFFu);
+      // every other group whose raw maximum reaches the threshold, one per lane per round
+      uint64_t surv[2] = {0ull, 0ull};
+      for (int c = 0; c < kc; ++c)
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int gi = c * G + g;
+          if (gkey(c, g) >= thr_key) surv[gi >> 6] |= 1ull << (gi & 63);
+        }
+      while (__any_sync(ACO_FULL_MASK, (surv[0] | surv[1]) != 0ull)) {
+        if (surv[0] | surv[1]) {
+          const int h = surv[0] ? 0 : 1;
+          const int gi = h * 64 + __ffsll((long long)surv[h]) - 1;
+          surv[h] &= surv[h] - 1ull;
+          const int c = gi / G, g = gi - c * G;
+          const int j0 = (c * 32 + lane) * V + 4 * g;
+          score4(j0, E::group_values(srow[c * 32 + lane], g), group_nibble(j0));
+        }
+      }
+      const uint32_t wkey = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
+      next = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == wkey ? (uint32_t)bj : 0x7FFFFFFFu);
+    }
+
+    if (next < 0 || next >= n) {  // no unvisited city found: cannot happen for valid input
+      if (lane == 0 && err) atomicExch(err, 1);
+      break;
+    }
+    if (lane == 0) {
+      tour[t] = next;
+      svis[next >> 5] |= 1u << (next & 31);
+    }
+    __syncwarp();
+    cur = next;
+  }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(32) construct_lean_kernel(
+    const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it_arg,
+    const uint32_t* __restrict__ it_dev, int32_t* __restrict__ tours, int32_t* __restrict__ err,
+    const uint2* __restrict__ lists, const int* __restrict__ lcnt, const uint32_t* __restrict__ lkey) {
+  extern __shared__ __align__(16) uint4 lsm[];
+  const int k = blockIdx.x;
+  if (k >= m) return;
+  const int eb = PREC == ACO_FP32 ? 4 : 2;
+  const int chunks = (n + 16 / eb - 1) / (16 / eb);
+  uint32_t* svis = reinterpret_cast<uint32_t*>(lsm + ((chunks + 31) / 32) * 32);
+  const uint32_t it = it_dev ? *it_dev : it_arg;
+  construct_ant_lean<PREC>(Pv, n, ld, key, it, k, tours + (size_t)k * n, err, lists, lcnt, lkey, lsm,
+                           svis);
+}
+
+// Multi-instance form: persistent warps pull (instance, ant) items.
+template <int PREC>
+__global__ void __launch_bounds__(32) batch_construct_lean_kernel(
+    const InstDev* __restrict__ insts, const int* __restrict__ ant_off, int count, int total,
+    int* __restrict__ counter, int32_t* __restrict__ err, int max_n) {
+  extern __shared__ __align__(16) uint4 lsm[];
+  const int eb = PREC == ACO_FP32 ? 4 : 2;
+  const int max_chunks = (max_n + 16 / eb - 1) / (16 / eb);
+  uint32_t* svis = reinterpret_cast<uint32_t*>(lsm + ((max_chunks + 31) / 32) * 32);
+  const int base = __ldg(ant_off);
+  for (;;) {
+    int item = 0;
+    if ((threadIdx.x & 31) == 0) item = atomicAdd(counter, 1);
+    item = __shfl_sync(ACO_FULL_MASK, item, 0);
+    if (item >= total) break;
+    const int i = find_instance(ant_off, count, base + item);
+    const InstDev& I = insts[i];
+    const int k = base + item - __ldg(ant_off + i);
+    construct_ant_lean<PREC>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err, I.lists,
+                             I.lcnt, I.lkey, lsm, svis);
+  }
+}
+
+}  // namespace aco

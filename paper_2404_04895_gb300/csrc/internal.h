@@ -41,27 +41,46 @@ ConstructShape default_construct_shape(int n, int m, int elem_bytes);
 void register_tuned_shape(int n, int m, int elem_bytes, ConstructShape s);
 
 // Kernel launchers (return ACO_OK or an error code; asynchronous).
+// lists/lcnt/lkey: the candidate lists of M_p (nullptr: full scan only)
 int launch_construct_f32(const float* P, int n, int ld, int m, uint2 key, uint32_t it,
                          const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
-                         int chunks, int mode, cudaStream_t st);
+                         int chunks, int mode, const uint2* lists, const int* lcnt,
+                         const uint32_t* lkey, cudaStream_t st);
 int launch_construct_bf16(const void* P, int n, int ld, int m, uint2 key, uint32_t it,
                           const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
-                          int chunks, int mode, cudaStream_t st);
+                          int chunks, int mode, const uint2* lists, const int* lcnt,
+                          const uint32_t* lkey, cudaStream_t st);
 int launch_construct_f16(const void* P, int n, int ld, int m, uint2 key, uint32_t it,
                          const uint32_t* it_dev, int32_t* tours, int32_t* err, int warps,
-                         int chunks, int mode, cudaStream_t st);
+                         int chunks, int mode, const uint2* lists, const int* lcnt,
+                         const uint32_t* lkey, cudaStream_t st);
+int launch_build_lists(const void* P, int prec, int n, int ld, uint2* lists, int* lcnt,
+                       uint32_t* lkey, cudaStream_t st);
 
 struct InstDev;
+// bitmap_bytes: shared bytes of the list phase's visited bitmap (0: no lists)
 int launch_batch_construct_f32(const InstDev* insts, const int* ant_off, int count, int total,
                                int* counter, int32_t* err, int warps, int chunks, int mode,
-                               int num_sms, cudaStream_t st);
+                               int bitmap_bytes, int num_sms, cudaStream_t st);
 int launch_batch_construct_bf16(const InstDev* insts, const int* ant_off, int count, int total,
                                 int* counter, int32_t* err, int warps, int chunks, int mode,
-                                int num_sms, cudaStream_t st);
+                                int bitmap_bytes, int num_sms, cudaStream_t st);
 int launch_batch_construct_f16(const InstDev* insts, const int* ant_off, int count, int total,
                                int* counter, int32_t* err, int warps, int chunks, int mode,
-                               int num_sms, cudaStream_t st);
+                               int bitmap_bytes, int num_sms, cudaStream_t st);
 int batch_construct_shapes(int elem_bytes, const ConstructShape** list);
+
+// Lean (candidate-list) construction, any n <= 16384, one warp per ant
+// (mode 2 of a ConstructShape; lists may be null: compact full scans only).
+int launch_construct_lean(const void* P, int prec, int n, int ld, int m, uint2 key, uint32_t it,
+                          const uint32_t* it_dev, int32_t* tours, int32_t* err, const uint2* lists,
+                          const int* lcnt, const uint32_t* lkey, cudaStream_t st);
+int launch_batch_construct_lean(const InstDev* insts, const int* ant_off, int count, int total,
+                                int* counter, int32_t* err, int prec, int max_n, int num_sms,
+                                cudaStream_t st);
+int prepare_construct_lean();
+constexpr int kModeLean = 2;
+constexpr int kLeanMaxN = 16384;
 
 int prepare_construct_f32();
 int prepare_construct_bf16();

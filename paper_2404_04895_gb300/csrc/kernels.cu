@@ -65,6 +65,18 @@ __global__ void __launch_bounds__(256) build_P_kernel(const float* __restrict__ 
                     static_cast<char*>(Pv) + (size_t)i * ld * eb, red);
 }
 
+template <int PREC>
+__global__ void __launch_bounds__(256) build_lists_kernel(const void* __restrict__ Pv, int n, int ld,
+                                                          uint2* __restrict__ lists,
+                                                          int* __restrict__ lcnt,
+                                                          uint32_t* __restrict__ lkey) {
+  __shared__ uint32_t scratch[kListScratchWords];
+  const int i = blockIdx.x;
+  const size_t eb = PREC == ACO_FP32 ? 4 : 2;
+  build_list_row<PREC>(static_cast<const char*>(Pv) + (size_t)i * ld * eb, n,
+                       lists + (size_t)i * kListMax, lcnt + i, lkey + i, scratch);
+}
+
 __global__ void __launch_bounds__(256) tour_length_kernel(const double* __restrict__ D, int n,
                                                           const int32_t* __restrict__ tours,
                                                           int m, float Q, double* __restrict__ L,
@@ -171,6 +183,24 @@ int launch_build_P(const float* tau, const float* H, int n, int ld, int alpha, f
       return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
   }
   return check_launch("build_P_kernel");
+}
+
+int launch_build_lists(const void* P, int prec, int n, int ld, uint2* lists, int* lcnt,
+                       uint32_t* lkey, cudaStream_t st) {
+  switch (prec) {
+    case ACO_FP32:
+      build_lists_kernel<ACO_FP32><<<n, 256, 0, st>>>(P, n, ld, lists, lcnt, lkey);
+      break;
+    case ACO_BF16:
+      build_lists_kernel<ACO_BF16><<<n, 256, 0, st>>>(P, n, ld, lists, lcnt, lkey);
+      break;
+    case ACO_FP16:
+      build_lists_kernel<ACO_FP16><<<n, 256, 0, st>>>(P, n, ld, lists, lcnt, lkey);
+      break;
+    default:
+      return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  }
+  return check_launch("build_lists_kernel");
 }
 
 int launch_tour_length(const double* D, int n, const int32_t* tours, int m, float Q, double* L,

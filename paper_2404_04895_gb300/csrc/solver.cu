@@ -14,6 +14,7 @@
 
 #include "batch.cuh"
 #include "internal.h"
+#include "steps.cuh"
 #include "shapes.h"
 
 namespace aco {
@@ -84,6 +85,7 @@ void register_tuned_shape(int n, int m, int elem_bytes, ConstructShape s) {
 }
 
 static int shape_columns(ConstructShape s, int elem_bytes) {
+  if (s.mode == kModeLean) return kLeanMaxN;
   return 32 * s.warps * s.chunks * (16 / elem_bytes);
 }
 
@@ -115,25 +117,32 @@ int prepare_kernels() {
     if (!rc) rc = prepare_construct_bf16();
     if (!rc) rc = prepare_construct_f16();
     if (!rc) rc = prepare_deposit();
+    if (!rc) rc = prepare_construct_lean();
   });
   return rc == ACO_OK ? ACO_OK : set_error(rc, "kernel preparation failed");
 }
 
 static int launch_construct(const void* P, int prec, int n, int ld, int m, uint2 key, uint32_t it,
                             const uint32_t* it_dev, int32_t* tours, int32_t* err,
-                            ConstructShape s, cudaStream_t st) {
+                            ConstructShape s, const uint2* lists, const int* lcnt,
+                            const uint32_t* lkey, cudaStream_t st) {
   const int eb = prec == ACO_FP32 ? 4 : 2;
+  if (s.warps == 0 && lists && n <= kLeanMaxN) s = {1, 0, kModeLean};  // lists: lean kernel by default
   if (s.warps == 0) s = default_construct_shape(n, m, eb);
   if (s.warps == 0 || shape_columns(s, eb) < n)
     return set_error(ACO_ERR_UNSUPPORTED, "no construct shape covers n=%d", n);
+  if (s.mode == kModeLean)
+    return launch_construct_lean(P, prec, n, ld, m, key, it, it_dev, tours, err, lists, lcnt, lkey, st);
   switch (prec) {
     case ACO_FP32:
       return launch_construct_f32(static_cast<const float*>(P), n, ld, m, key, it, it_dev, tours, err,
-                                  s.warps, s.chunks, s.mode, st);
+                                  s.warps, s.chunks, s.mode, lists, lcnt, lkey, st);
     case ACO_BF16:
-      return launch_construct_bf16(P, n, ld, m, key, it, it_dev, tours, err, s.warps, s.chunks, s.mode, st);
+      return launch_construct_bf16(P, n, ld, m, key, it, it_dev, tours, err, s.warps, s.chunks, s.mode,
+                                   lists, lcnt, lkey, st);
     case ACO_FP16:
-      return launch_construct_f16(P, n, ld, m, key, it, it_dev, tours, err, s.warps, s.chunks, s.mode, st);
+      return launch_construct_f16(P, n, ld, m, key, it, it_dev, tours, err, s.warps, s.chunks, s.mode,
+                                  lists, lcnt, lkey, st);
   }
   return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
 }
@@ -176,7 +185,8 @@ static int validate(const aco_params* p) {
 constexpr int kSchedCap = 1 << 16;  // AdaIR schedule entries (iterations 0..T, clamped)
 
 struct Layout {
-  size_t coords, D, H, tau, P, tours, L, c, nbr, best_tour, best_len, it, err, sched, total;
+  size_t coords, D, H, tau, P, tours, L, c, nbr, best_tour, best_len, it, err, sched, lists, lcnt,
+      lkey, total;
 };
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -205,6 +215,9 @@ static Layout layout_of(int n, int m) {
   L.it = take(4);
   L.err = take(4);
   L.sched = take((size_t)kSchedCap * 4);
+  L.lists = take((size_t)n * kListMax * 8);
+  L.lcnt = take((size_t)n * 4);
+  L.lkey = take((size_t)n * 4);
   L.total = o;
   return L;
 }
@@ -245,6 +258,9 @@ int instance_bind(const aco_params& p, unsigned char* ws, InstDev* d, cudaStream
   x.best_len = reinterpret_cast<double*>(ws + L.best_len);
   x.it = reinterpret_cast<uint32_t*>(ws + L.it);
   x.sched = reinterpret_cast<float*>(ws + L.sched);
+  x.lists = p.cand_lists ? reinterpret_cast<uint2*>(ws + L.lists) : nullptr;
+  x.lcnt = reinterpret_cast<int*>(ws + L.lcnt);
+  x.lkey = reinterpret_cast<uint32_t*>(ws + L.lkey);
   ACO_CUDA_TRY(cudaMemcpyAsync(coords, coords_host, sizeof(float) * 2 * p.n, cudaMemcpyHostToDevice, st));
   rc = launch_heuristic(coords, p.n, p.beta, const_cast<double*>(x.D), const_cast<float*>(x.H), ld, st);
   if (!rc) rc = launch_fill(x.tau, p.n, ld, p.tau0, st);
@@ -276,6 +292,9 @@ struct aco_solver {
   unsigned char* ws;
   Layout lay;
   float *coords, *H, *tau, *P_f, *sched;
+  uint2* lists;
+  int* lcnt;
+  uint32_t* lkey;
   double *D, *L, *c, *best_len;
   int32_t *tours, *nbr, *best_tour, *err;
   uint32_t* it_dev;
@@ -331,9 +350,13 @@ static int enqueue_iteration(aco_solver* s) {
                           p.roulette == ACO_ADAIR ? s->sched : nullptr, s->it_dev, n_sched, p.prec,
                           s->P_f, st);
   if (rc) return rc;
+  const bool lists = p.cand_lists != 0;
+  if (lists) rc = launch_build_lists(s->P_f, p.prec, n, s->ld, s->lists, s->lcnt, s->lkey, st);
+  if (rc) return rc;
   probe(1);
   rc = launch_construct(s->P_f, p.prec, n, s->ld, m, make_uint2((uint32_t)p.seed, (uint32_t)(p.seed >> 32)),
-                        0u, s->it_dev, s->tours, s->err, s->shape, st);
+                        0u, s->it_dev, s->tours, s->err, s->shape, lists ? s->lists : nullptr, s->lcnt,
+                        s->lkey, st);
   if (rc) return rc;
   probe(2);
   const bool det = p.deposit == ACO_DEPOSIT_DET;
@@ -410,6 +433,7 @@ int aco_params_default(aco_params* p) {
   p->gamma_max = 1.5f;
   p->gamma_min = 0.5f;
   p->gamma_T = 100;
+  p->cand_lists = 1;
   return ACO_OK;
 }
 
@@ -472,6 +496,9 @@ int aco_create(aco_solver** out, const float* coords_host, const aco_params* p, 
   s->it_dev = s->at<uint32_t>(L.it);
   s->err = s->at<int32_t>(L.err);
   s->sched = s->at<float>(L.sched);
+  s->lists = s->at<uint2>(L.lists);
+  s->lcnt = s->at<int>(L.lcnt);
+  s->lkey = s->at<uint32_t>(L.lkey);
   // Replay through a CUDA graph on a created stream; the legacy default stream
   // cannot be captured, so there the iteration's kernels are launched directly.
   s->use_graph = s->stream != nullptr;
@@ -614,7 +641,7 @@ int aco_solver_set_shape(aco_solver* s, int warps, int chunks, int mode) {
     const int eb = s->p.prec == ACO_FP32 ? 4 : 2;
     const ConstructShape* list;
     const int cnt = construct_shapes(eb, &list);
-    bool found = false;
+    bool found = mode == kModeLean && warps == 1;
     for (int q = 0; q < cnt; ++q)
       found |= list[q].warps == warps && list[q].chunks == chunks && list[q].mode == mode;
     if (!found) return set_error(ACO_ERR_UNSUPPORTED, "shape (%d, %d, %d) not compiled", warps, chunks, mode);
@@ -647,12 +674,13 @@ int aco_autotune_construct(const void* P_dev, int prec, int n, int ld, int m, ui
   float best_ms = 0.0f;
   for (int q = 0; q < cnt && rc == ACO_OK; ++q) {
     if (shape_columns(list[q], eb) < n) continue;
-    rc = launch_construct(P_dev, prec, n, ld, m, key, 0u, nullptr, tours_scratch_dev, nullptr, list[q], st);
+    rc = launch_construct(P_dev, prec, n, ld, m, key, 0u, nullptr, tours_scratch_dev, nullptr, list[q],
+                          nullptr, nullptr, nullptr, st);
     if (rc) break;
     cudaEventRecord(e0, st);
     for (int r = 0; r < reps && rc == ACO_OK; ++r)
       rc = launch_construct(P_dev, prec, n, ld, m, key, (uint32_t)(r + 1), nullptr, tours_scratch_dev,
-                            nullptr, list[q], st);
+                            nullptr, list[q], nullptr, nullptr, nullptr, st);
     cudaEventRecord(e1, st);
     if (rc) break;
     if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -832,7 +860,36 @@ int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, ui
   if (rc) return rc;
   ConstructShape s = {warps, chunks, mode};
   return launch_construct(P_dev, prec, n, ld, m, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), it,
-                          nullptr, tours_dev, err_dev, s, static_cast<cudaStream_t>(stream));
+                          nullptr, tours_dev, err_dev, s, nullptr, nullptr, nullptr,
+                          static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_build_lists(const void* P_dev, int prec, int n, int ld, void* lists_dev, int* lcnt_dev,
+                       uint32_t* lkey_dev, void* stream) {
+  int rc = check_mat(P_dev, n, ld, "P");
+  if (rc) return rc;
+  if (!lists_dev || !lcnt_dev || !lkey_dev) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (((uintptr_t)lists_dev & 7) != 0) return set_error(ACO_ERR_ARG, "lists must be 8-byte aligned");
+  if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  return launch_build_lists(P_dev, prec, n, ld, static_cast<uint2*>(lists_dev), lcnt_dev, lkey_dev,
+                            static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_construct_ex(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,
+                        int32_t* tours_dev, int32_t* err_dev, const void* lists_dev, const int* lcnt_dev,
+                        const uint32_t* lkey_dev, int warps, int chunks, int mode, void* stream) {
+  int rc = check_mat(P_dev, n, ld, "P");
+  if (rc) return rc;
+  if (m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "m=%d outside [1, %d]", m, ACO_MAX_M);
+  if (!tours_dev) return set_error(ACO_ERR_ARG, "tours is NULL");
+  if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  if (lists_dev && (!lcnt_dev || !lkey_dev)) return set_error(ACO_ERR_ARG, "lists need lcnt and lkey");
+  rc = prepare_kernels();
+  if (rc) return rc;
+  ConstructShape s = {warps, chunks, mode};
+  return launch_construct(P_dev, prec, n, ld, m, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), it,
+                          nullptr, tours_dev, err_dev, s, static_cast<const uint2*>(lists_dev), lcnt_dev,
+                          lkey_dev, static_cast<cudaStream_t>(stream));
 }
 
 int aco_op_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,

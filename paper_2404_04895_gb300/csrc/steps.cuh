@@ -273,3 +273,218 @@ __host__ __device__ inline int deposit_tile(int n) {
 }
 
 }  // namespace aco
+
+namespace aco {
+
+// ---------------------------------------------------------------------------
+// Candidate list of row i of M_p (exact fast path of the construction step).
+// Keys are the fp32 bit patterns of the stored values (>= 0, so key order is
+// value order).  With T the kListTarget-th largest key of the row (radix
+// select, 8 bits per pass), the list holds every column with key > T and
+// columns with key == T up to kListMax entries, sorted by key (descending,
+// ties by column); bkey bounds the score key (fp32 bits + 1, see construct)
+// of every column left out:
+//   all columns with key >= T listed  ->  outside keys < T,  bkey = T
+//   ties at T truncated               ->  outside keys <= T, bkey = T + 1
+//   row has <= kListMax columns        ->  nothing outside,   bkey = 0
+// Sorted, the first r entries bound the rest: a column after them has a
+// score key <= key(entry r) + 1.  A step is decided by the list when its best
+// score over the entries scored so far exceeds the bound of everything else:
+// no other column can then reach (or tie) that score.
+// All threads of the CTA (blockDim.x <= 256); scratch: kListScratchWords
+// shared words.
+// ---------------------------------------------------------------------------
+constexpr int kListTarget = 64;
+constexpr int kListMax = 128;
+constexpr int kListScratchWords = 256 + 8 + 2 * kListMax * 2;
+
+template <int PREC>
+__device__ __forceinline__ uint32_t p_key(const void* __restrict__ row, int j) {
+  if (PREC == ACO_FP32) return __ldg(static_cast<const uint32_t*>(row) + j);
+  const uint32_t h = __ldg(static_cast<const unsigned short*>(row) + j);
+  if (PREC == ACO_BF16) return h << 16;
+  return __float_as_uint(__half2float(__ushort_as_half((unsigned short)h)));
+}
+
+template <int PREC>
+__device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, int n,
+                                               uint2* __restrict__ list, int* __restrict__ cnt_out,
+                                               uint32_t* __restrict__ bkey_out,
+                                               uint32_t* scratch) {
+  uint32_t* hist = scratch;             // [256]
+  uint32_t* sh = scratch + 256;         // [0] prefix, [1] need, [2] gt count, [3] eq count
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (n <= kListMax) {  // every column listed, bound 0; sorted below
+    for (int j = tid; j < n; j += nt) list[j] = make_uint2(p_key<PREC>(P_row, j), (uint32_t)j);
+    if (tid == 0) {
+      *cnt_out = n;
+      *bkey_out = 0u;
+    }
+    __syncthreads();
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(scratch + 256 + 8);
+    for (int q = tid; q < kListMax; q += nt) {
+      unsigned long long v = 0ull;
+      if (q < n) {
+        const uint2 e = list[q];
+        v = ((unsigned long long)e.x << 32) | (unsigned long long)(0xFFFFFFFFu - e.y);
+      }
+      sk[q] = v;
+    }
+    __syncthreads();
+    for (int size = 2; size <= kListMax; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int q = tid; q < kListMax; q += nt) {
+          const int partner = q ^ stride;
+          if (partner > q) {
+            const bool desc = (q & size) == 0;
+            const unsigned long long a = sk[q], b = sk[partner];
+            if (desc ? (a < b) : (a > b)) {
+              sk[q] = b;
+              sk[partner] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int q = tid; q < n; q += nt) {
+      const unsigned long long v = sk[q];
+      list[q] = make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v);
+    }
+    __syncthreads();
+    return;
+  }
+  // 1. radix select of the kListTarget-th largest key T
+  if (tid == 0) {
+    sh[0] = 0u;
+    sh[1] = kListTarget;
+  }
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int b = tid; b < 256; b += nt) hist[b] = 0u;
+    __syncthreads();
+    const uint32_t prefix = sh[0];
+    const uint32_t hi_mask = shift == 24 ? 0u : (0xFFFFFFFFu << (shift + 8));
+    for (int j = tid; j < n; j += nt) {
+      const uint32_t key = p_key<PREC>(P_row, j);
+      if ((key & hi_mask) == prefix) atomicAdd(&hist[(key >> shift) & 0xFFu], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t need = sh[1], cum = 0u;
+      int digit = 0;
+      for (int b = 255; b >= 0; --b) {
+        if (cum + hist[b] >= need) {
+          digit = b;
+          break;
+        }
+        cum += hist[b];
+      }
+      sh[0] = prefix | ((uint32_t)digit << shift);
+      sh[1] = need - cum;
+    }
+    __syncthreads();
+  }
+  const uint32_t T = sh[0];
+  // 2. counts above and at T
+  if (tid == 0) {
+    sh[2] = 0u;
+    sh[3] = 0u;
+  }
+  __syncthreads();
+  uint32_t gt = 0, eq = 0;
+  for (int j = tid; j < n; j += nt) {
+    const uint32_t key = p_key<PREC>(P_row, j);
+    gt += key > T;
+    eq += key == T;
+  }
+  atomicAdd(&sh[2], gt);
+  atomicAdd(&sh[3], eq);
+  __syncthreads();
+  const uint32_t n_gt = sh[2], n_eq = sh[3];
+  const bool all_ties = n_gt + n_eq <= (uint32_t)kListMax;
+  const uint32_t eq_take = all_ties ? n_eq : (uint32_t)kListMax - n_gt;
+  // 3. compaction in column order: thread tid owns columns [tid*span, (tid+1)*span)
+  const int span = (n + nt - 1) / nt;
+  const int j0 = tid * span, j1 = min(n, j0 + span);
+  uint32_t my_gt = 0, my_eq = 0;
+  for (int j = j0; j < j1; ++j) {
+    const uint32_t key = p_key<PREC>(P_row, j);
+    my_gt += key > T;
+    my_eq += key == T;
+  }
+  // exclusive scans over threads of the two counts (warp shuffles, then warp totals)
+  const int lane = tid & 31, wid = tid >> 5;
+  uint32_t inc_gt = my_gt, inc_eq = my_eq;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t vg = __shfl_up_sync(ACO_FULL_MASK, inc_gt, off);
+    const uint32_t ve = __shfl_up_sync(ACO_FULL_MASK, inc_eq, off);
+    if (lane >= off) {
+      inc_gt += vg;
+      inc_eq += ve;
+    }
+  }
+  __syncthreads();
+  if (lane == 31) {  // warp totals (hist is free again)
+    hist[wid] = inc_gt;
+    hist[32 + wid] = inc_eq;
+  }
+  __syncthreads();
+  uint32_t before_gt = inc_gt - my_gt, before_eq = inc_eq - my_eq;
+  for (int w = 0; w < wid; ++w) {
+    before_gt += hist[w];
+    before_eq += hist[32 + w];
+  }
+  // listed: all gt; eq in column order until eq_take
+  uint32_t pos = before_gt + min(before_eq, eq_take);
+  uint32_t eq_seen = before_eq;
+  for (int j = j0; j < j1; ++j) {
+    const uint32_t key = p_key<PREC>(P_row, j);
+    if (key > T) {
+      list[pos++] = make_uint2(key, (uint32_t)j);
+    } else if (key == T) {
+      if (eq_seen < eq_take) list[pos++] = make_uint2(key, (uint32_t)j);
+      ++eq_seen;
+    }
+  }
+  const int cnt = (int)(n_gt + eq_take);
+  if (tid == 0) {
+    *cnt_out = cnt;
+    *bkey_out = all_ties ? T : T + 1u;
+  }
+  // 4. sort the list by key, descending (ties: lower column first): bitonic
+  //    sort of kListMax 64-bit composite keys in shared memory
+  __syncthreads();
+  unsigned long long* sk = reinterpret_cast<unsigned long long*>(scratch + 256 + 8);
+  for (int q = tid; q < kListMax; q += nt) {
+    unsigned long long v = 0ull;  // padding sorts last
+    if (q < cnt) {
+      const uint2 e = list[q];
+      v = ((unsigned long long)e.x << 32) | (unsigned long long)(0xFFFFFFFFu - e.y);
+    }
+    sk[q] = v;
+  }
+  __syncthreads();
+  for (int size = 2; size <= kListMax; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int q = tid; q < kListMax; q += nt) {
+        const int partner = q ^ stride;
+        if (partner > q) {
+          const bool desc = (q & size) == 0;
+          const unsigned long long a = sk[q], b = sk[partner];
+          if (desc ? (a < b) : (a > b)) {
+            sk[q] = b;
+            sk[partner] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int q = tid; q < cnt; q += nt) {
+    const unsigned long long v = sk[q];
+    list[q] = make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v);
+  }
+  __syncthreads();
+}
+
+}  // namespace aco

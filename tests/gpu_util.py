@@ -27,6 +27,7 @@ def dev(a):
 def padded_dev(mat, ld, np_dtype):
     """n x n host matrix -> n x ld device tensor, zero padding columns."""
     n = mat.shape[0]
+    assert mat.shape == (n, n) and ld >= n
     out = np.zeros((n, ld), dtype=np_dtype)
     out[:, :n] = mat
     return dev(out)
