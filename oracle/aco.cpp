@@ -7,6 +7,7 @@
 //   Eq. 3             fitness f = closed tour length
 //   Sec. 2.3 (Eq. 2/3) index matrix I, increment A, Delta M_tau = sum of A
 // plus Ant System evaporation before the deposit.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -162,18 +163,121 @@ void orc_construct(const float* P_val, int n, uint64_t seed, uint32_t it, int k_
   (void)nthreads;
 }
 
-// f(s) (Eq. 3): closed tour length, sum over t = 0..n-1 of d(p_t, p_{t+1 mod n}),
-// accumulated in fp64 in that order.
+// f(s) (Eq. 3): closed tour length, the sum over t = 0..n-1 of
+// d(p_t, p_{t+1 mod n}) in fp64, taken in blocks of 32 consecutive edges:
+// each block t = 32b .. 32b+31 summed in t order, then the block sums added
+// in block order.
 void orc_tour_lengths(const double* D, int n, const int32_t* tours, int m, double* L) {
   for (int k = 0; k < m; ++k) {
     const int32_t* p = tours + (size_t)k * n;
-    double s = 0.0;
-    for (int t = 0; t < n; ++t) {
-      int32_t a = p[t], b = p[(t + 1) % n];
-      s = s + D[(size_t)a * n + b];
+    double total = 0.0;
+    for (int b = 0; 32 * b < n; ++b) {
+      double s = 0.0;
+      for (int t = 32 * b; t < n && t < 32 * b + 32; ++t) {
+        int32_t a = p[t], c = p[(t + 1) % n];
+        s = s + D[(size_t)a * n + c];
+      }
+      total = total + s;
     }
-    L[k] = s;
+    L[k] = total;
   }
+}
+
+// Exact summation after Shewchuk, "Adaptive Precision Floating-Point
+// Arithmetic" (1997): the running sum is kept as an expansion -- a list of
+// non-overlapping doubles of increasing magnitude whose real sum is exactly
+// the sum of every input so far.  grow() adds one double with two-sum steps.
+static void grow(std::vector<double>& partials, double v) {
+  size_t used = 0;
+  for (size_t r = 0; r < partials.size(); ++r) {
+    double y = partials[r];
+    if (std::fabs(v) < std::fabs(y)) std::swap(v, y);
+    const double hi = v + y;
+    const double lo = y - (hi - v);
+    if (lo != 0.0) partials[used++] = lo;
+    v = hi;
+  }
+  partials.resize(used);
+  partials.push_back(v);
+}
+
+// The double nearest to the real value of an expansion (ties to even): add the
+// components from the largest down until a rounding error appears, then settle
+// an exact half-way case with the sign of the next component.
+static double round_expansion(const std::vector<double>& partials) {
+  if (partials.empty()) return 0.0;
+  size_t r = partials.size();
+  double hi = partials[--r];
+  double lo = 0.0;
+  while (r > 0) {
+    const double v = hi;
+    const double y = partials[--r];
+    hi = v + y;
+    const double yr = hi - v;
+    lo = y - yr;
+    if (lo != 0.0) break;
+  }
+  if (r > 0 && ((lo < 0.0 && partials[r - 1] < 0.0) || (lo > 0.0 && partials[r - 1] > 0.0))) {
+    const double y = lo * 2.0;
+    const double v = hi + y;
+    const double yr = v - hi;
+    if (y == yr) hi = v;
+  }
+  return hi;
+}
+
+static bool all_finite(const double* x, size_t count) {
+  for (size_t q = 0; q < count; ++q)
+    if (!std::isfinite(x[q])) return false;
+  return true;
+}
+
+// The exact sum of count doubles rounded once to double.  Inputs that are not
+// all finite give the plain IEEE sum (an infinity or NaN).
+static double exact_sum(const double* x, size_t count) {
+  if (!all_finite(x, count)) {
+    double s = 0.0;
+    for (size_t q = 0; q < count; ++q) s = s + x[q];
+    return s;
+  }
+  std::vector<double> partials;
+  for (size_t q = 0; q < count; ++q) grow(partials, x[q]);
+  return round_expansion(partials);
+}
+
+// fp32 value of a double with an infinity read as +-2^128 (the point where
+// the fp32 range ends), so that half-way tests work at the overflow boundary.
+static double f32_as_double(float f) {
+  if (std::isinf(f)) return std::copysign(std::ldexp(1.0, 128), (double)f);
+  return (double)f;
+}
+
+// The exact sum of count doubles rounded once to fp32 (ties to even).  With h
+// the nearest double to the exact sum x, every fp32 value and every point
+// half-way between two fp32 neighbours is a double, so rounding h to fp32
+// gives the fp32 rounding of x -- except when h is itself such a half-way
+// point and x != h; then the sign of x - h (an exact expansion again) picks
+// the neighbour.  Inputs that are not all finite give fl32 of the IEEE sum.
+static float exact_sum_f32(const double* x, size_t count) {
+  if (!all_finite(x, count)) return (float)exact_sum(x, count);
+  std::vector<double> partials;
+  for (size_t q = 0; q < count; ++q) grow(partials, x[q]);
+  const double h = round_expansion(partials);
+  float f = (float)h;
+  const double fd = f32_as_double(f);
+  if (fd != h) {
+    const float g = (fd < h) ? std::nextafter(f, INFINITY) : std::nextafter(f, -INFINITY);
+    const double gd = f32_as_double(g);
+    if (h - fd == gd - h) {  // h lies half-way between f and g
+      std::vector<double> rest = partials;
+      grow(rest, -h);  // exact x - h
+      double sign = 0.0;
+      for (double v : rest)
+        if (v != 0.0) sign = v;  // the largest component decides the sign
+      if ((sign > 0.0 && gd > fd) || (sign < 0.0 && gd < fd)) f = g;
+    }
+  }
+  return f;
 }
 
 // Eq. 2: the path and its one-step cyclic shift side by side, row t = (p_t, p_{t-1}).
@@ -185,33 +289,48 @@ void orc_index_matrix(const int32_t* tour, int n, int32_t* I) {
 }
 
 // Evaporation then deposit (Sec. 2.3, Eq. 3 with weight Q / f):
-//   A^(k)_ij = Q / L_k if (i,j) or (j,i) is a row of I^(k), else 0;
-//   Delta = sum_k A^(k) in fp64, ants in ascending order;
-//   tau_ij <- fl32( fl64((1 - rho) * tau_ij) + Delta_ij ).
+//   c_k = fl64(Q / L_k);
+//   A^(k)_ij = c_k if (i,j) or (j,i) is a row of I^(k), else 0;
+//   tau'_ij = fl32(keep * tau_ij) with keep = fl32(1 - rho)      (fp32 tensor)
+//   tau_ij <- tau'_ij + sum over paths of A^(k)_ij, the real sum rounded once
+//             to fp32 (ties to even); tau'_ij where no path has the edge.
 void orc_deposit(float* tau, int n, const int32_t* tours, const double* L, int m,
                  float rho, float Q) {
-  std::vector<double> delta((size_t)n * n, 0.0);
+  // every (entry, weight) pair, grouped by entry
+  std::vector<std::pair<size_t, double>> items;
+  items.reserve((size_t)2 * n * m);
   std::vector<int32_t> I((size_t)2 * n);
   for (int k = 0; k < m; ++k) {
     double c = (double)Q / L[k];
     orc_index_matrix(tours + (size_t)k * n, n, I.data());
     for (int t = 0; t < n; ++t) {
       int32_t a = I[2 * t], b = I[2 * t + 1];
-      delta[(size_t)a * n + b] = delta[(size_t)a * n + b] + c;
-      delta[(size_t)b * n + a] = delta[(size_t)b * n + a] + c;
+      items.emplace_back((size_t)a * n + b, c);
+      items.emplace_back((size_t)b * n + a, c);
     }
   }
-  double keep = 1.0 - (double)rho;
-  for (size_t e = 0; e < (size_t)n * n; ++e) {
-    double v = keep * (double)tau[e];
-    tau[e] = (float)(v + delta[e]);
+  std::stable_sort(items.begin(), items.end(),
+                   [](const std::pair<size_t, double>& x, const std::pair<size_t, double>& y) {
+                     return x.first < y.first;
+                   });
+  const float keep = 1.0f - rho;
+  for (size_t e = 0; e < (size_t)n * n; ++e) tau[e] = keep * tau[e];
+  std::vector<double> group;
+  for (size_t q = 0; q < items.size();) {
+    const size_t e = items[q].first;
+    group.assign(1, (double)tau[e]);
+    while (q < items.size() && items[q].first == e) group.push_back(items[q++].second);
+    tau[e] = exact_sum_f32(group.data(), group.size());
   }
 }
 
+double orc_exact_sum(const double* x, int64_t count) { return exact_sum(x, (size_t)count); }
+float orc_exact_sum_f32(const double* x, int64_t count) { return exact_sum_f32(x, (size_t)count); }
+
 void orc_deposit_fp32_order(float* tau, int n, const int32_t* tours, const double* L,
                             int m, float rho, float Q, const int64_t* perm) {
-  double keep = 1.0 - (double)rho;
-  for (size_t e = 0; e < (size_t)n * n; ++e) tau[e] = (float)(keep * (double)tau[e]);
+  const float keep = 1.0f - rho;
+  for (size_t e = 0; e < (size_t)n * n; ++e) tau[e] = keep * tau[e];
   int64_t total = (int64_t)2 * m * n;
   for (int64_t q = 0; q < total; ++q) {
     int64_t id = perm ? perm[q] : q;

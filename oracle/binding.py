@@ -54,6 +54,8 @@ def lib():
             "orc_select": (i32, [v, v, C.c_int, u64, u32, u32, u32]),
             "orc_select_literal_adair": (i32, [v, v, C.c_int, u64, u32, u32, u32, f64]),
             "orc_tour_lengths": (None, [v, C.c_int, v, C.c_int, v]),
+            "orc_exact_sum": (f64, [v, C.c_int64]),
+            "orc_exact_sum_f32": (C.c_float, [v, C.c_int64]),
             "orc_index_matrix": (None, [v, C.c_int, v]),
             "orc_deposit": (None, [v, C.c_int, v, v, C.c_int, f32, f32]),
             "orc_deposit_fp32_order": (None, [v, C.c_int, v, v, C.c_int, f32, f32, v]),
@@ -205,6 +207,16 @@ def tour_lengths(D, tours):
     L = np.empty(m, dtype=np.float64)
     lib().orc_tour_lengths(_p(D), n, _p(tours), m, _p(L))
     return L
+
+
+def exact_sum(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(lib().orc_exact_sum(_p(x), x.size))
+
+
+def exact_sum_f32(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return np.float32(lib().orc_exact_sum_f32(_p(x), x.size))
 
 
 def index_matrix(tour):

@@ -33,9 +33,14 @@
  *   - AdaIR's argmax(r^gamma * p) is computed as argmax(r * p^(1/gamma)):
  *     M_p is raised to 1/gamma once per iteration with pow_own (own log2 /
  *     exp2 polynomials, fp32).  gamma follows a cosine-annealing schedule.
- *   - Deposit: every ant deposits Q / L_k on both (i,j) and (j,i) for each
- *     edge of its closed tour; Delta is summed in fp64 in ascending ant order;
- *     tau <- fl32(fl64((1-rho) * tau) + Delta).
+ *   - Evaporation in fp32, the precision of M_tau: tau' = fl32(keep * tau)
+ *     with keep = fl32(1 - rho).
+ *   - Deposit: every ant deposits c_k = fl64(Q / L_k) on both (i,j) and (j,i)
+ *     for each edge of its closed tour; the new tau_ij is tau'_ij plus the
+ *     sum of those weights, taken exactly and rounded once to fp32 (the
+ *     paper's sum over paths fixes no order, so none is imposed).
+ *   - Tour length: fp64, edges in blocks of 32 consecutive ones, each block
+ *     summed in tour order, the block sums added in block order.
  *
  * All matrices here are dense row-major n x n (no padding).
  */
@@ -101,6 +106,9 @@ int32_t orc_select_literal_adair(const float* row, const uint8_t* visited, int n
 
 /* ---- fitness f (Eq. 3) ---- */
 void orc_tour_lengths(const double* D, int n, const int32_t* tours, int m, double* L);
+/* exact sum of count doubles rounded once to fp64 / to fp32 (ties to even) */
+double orc_exact_sum(const double* x, int64_t count);
+float orc_exact_sum_f32(const double* x, int64_t count);
 
 /* ---- Sec. 2.3: index matrix, increment matrix, evaporation + deposit ---- */
 /* I of one tour (Eq. 2): rows (p_t, p_{t-1}) with cyclic predecessor; out n x 2 */
@@ -108,7 +116,7 @@ void orc_index_matrix(const int32_t* tour, int n, int32_t* I);
 void orc_deposit(float* tau, int n, const int32_t* tours, const double* L, int m,
                  float rho, float Q);
 /* float-atomic reading, applied in a caller-given edge order (tests only):
- * tau <- fl32(fl64(1-rho)*tau) then tau[a][b] += fl32(Q/L_k) in fp32 per
+ * tau <- fl32(fl32(1-rho)*tau) then tau[a][b] += fl32(Q/L_k) in fp32 per
  * directed edge, edges visited in the order given by perm (length 2*m*n). */
 void orc_deposit_fp32_order(float* tau, int n, const int32_t* tours, const double* L,
                             int m, float rho, float Q, const int64_t* perm);

@@ -1,0 +1,159 @@
+"""Oracle pins for the order-free readings of two sums of the path:
+the deposit (Sec. 2.3, Eq. 3: the real sum of the paths' weights added to the
+evaporated pheromone, rounded once to fp32) and the fitness f (Eq. 3, fp64 in
+blocks of 32 edges).  Exact rational arithmetic (fractions.Fraction) and
+math.fsum are the independent references."""
+import math
+from fractions import Fraction
+
+import numpy as np
+
+from conftest import golden_path
+
+F32_INF_AT = Fraction(2) ** 128 - Fraction(2) ** 103  # fp32 overflow threshold (rounds to inf)
+
+
+def _rn32(x: Fraction) -> np.float32:
+    """Nearest fp32 to the rational x, ties to even, by exact comparison."""
+    if x < 0:
+        return -_rn32(-x)
+    if x >= F32_INF_AT:
+        return np.float32(np.inf)
+    g = np.float32(float(x))
+    cands = {g, np.nextafter(g, np.float32(np.inf)), np.nextafter(g, np.float32(0))}
+    cands = [c for c in cands if np.isfinite(c)]
+
+    def dist(c):
+        return abs(Fraction(float(c)) - x)
+
+    best = min(dist(c) for c in cands)
+    tied = [c for c in cands if dist(c) == best]
+    if len(tied) == 1:
+        return tied[0]
+    even = [c for c in tied if (np.array(c, np.float32).view(np.uint32) & 1) == 0]
+    assert len(even) == 1
+    return even[0]
+
+
+def _cases(rng):
+    out = []
+    for _ in range(3000):
+        k = int(rng.integers(1, 12))
+        kind = int(rng.integers(0, 5))
+        if kind == 0:
+            x = rng.uniform(1e-4, 2.0, size=k)
+        elif kind == 1:
+            x = np.exp(rng.normal(0, 30, size=k))
+        elif kind == 2:
+            x = rng.normal(0, 1, size=k) * np.exp(rng.normal(0, 10, size=k))
+        elif kind == 3:
+            # an fp32 value, half of its ulp, and a tiny push either way or none
+            a = np.float32(rng.uniform(0.5, 4.0))
+            half = math.ulp(float(a)) * 2.0 ** 29 / 2.0  # half an fp32 ulp (fp32 has 29 fewer bits)
+            tiny = [0.0, 2.0 ** -70, -(2.0 ** -70), 2.0 ** -30][int(rng.integers(0, 4))]
+            x = np.array([float(a), half, tiny])
+        else:
+            # cancellation: large values that cancel and leave small ones
+            big = rng.uniform(1e10, 1e12, size=k)
+            x = np.concatenate([big, -big, rng.uniform(-1, 1, size=2)])
+            rng.shuffle(x)
+        out.append(np.asarray(x, dtype=np.float64))
+    return out
+
+
+def test_exact_sum_matches_fsum(orc):
+    rng = np.random.default_rng(11)
+    for x in _cases(rng):
+        assert orc.exact_sum(x) == math.fsum(x)
+
+
+def test_exact_sum_f32_matches_rational(orc):
+    rng = np.random.default_rng(12)
+    for x in _cases(rng):
+        exact = sum((Fraction(float(v)) for v in x), Fraction(0))
+        got = orc.exact_sum_f32(x)
+        ref = _rn32(exact)
+        assert (np.isinf(got) and np.isinf(ref) and got == ref) or got == ref, (x.tolist(), got, ref)
+
+
+def test_exact_sum_f32_boundaries(orc):
+    big = float(np.finfo(np.float32).max)
+    half = 2.0 ** 103  # half an ulp at the top of the fp32 range
+    assert orc.exact_sum_f32(np.array([big, half])) == np.float32(np.inf)          # tie -> even -> inf
+    assert orc.exact_sum_f32(np.array([big, half, -(2.0 ** 40)])) == np.float32(big)
+    sub = float(np.float32(2.0 ** -149))
+    assert orc.exact_sum_f32(np.array([sub, sub / 2])) == np.float32(2.0 ** -148)   # tie -> even
+    assert orc.exact_sum_f32(np.array([sub / 2, 2.0 ** -200])) == np.float32(sub)
+    assert orc.exact_sum_f32(np.array([1.0, 2.0 ** -24])) == np.float32(1.0)
+    assert orc.exact_sum_f32(np.array([1.0, 2.0 ** -24, 2.0 ** -80])) == np.float32(1 + 2.0 ** -23)
+    assert np.isinf(orc.exact_sum_f32(np.array([1.0, np.inf])))
+
+
+def test_deposit_single_rounding_golden(orc):
+    ref = np.loadtxt(golden_path("deposit_single_rounding.txt"), dtype=np.float64)
+    tours = np.array([[0, 1, 2], [1, 2, 0]], dtype=np.int32)
+    L = np.array([2.0 ** 24, 2.0 ** 60])
+    tau = orc.deposit(np.ones((3, 3), np.float32), tours, L, rho=0.0, Q=1.0)
+    assert np.array_equal(tau.astype(np.float64), ref)
+
+
+def test_deposit_is_rounded_exact_sum(orc):
+    """Brute force with rationals on small colonies: every entry equals the
+    fp32 rounding of fl32(keep * tau) + the weights of the paths using it."""
+    rng = np.random.default_rng(13)
+    for trial in range(6):
+        n, m = int(rng.integers(3, 9)), int(rng.integers(1, 7))
+        tours = np.stack([rng.permutation(n) for _ in range(m)]).astype(np.int32)
+        if trial % 2:
+            tours[1:] = tours[0]  # a converged colony: every ant on one tour
+        L = rng.uniform(0.5, 3.0, size=m) * (2.0 ** rng.integers(-3, 4, size=m))
+        rho, Q = np.float32(rng.uniform(0, 1)), np.float32(rng.uniform(0.1, 5))
+        tau0 = rng.uniform(0.01, 2, size=(n, n)).astype(np.float32)
+        got = orc.deposit(tau0, tours, L, float(rho), float(Q))
+        keep = np.float32(np.float32(1) - rho)
+        w = [Fraction(float(np.float64(Q) / L[k])) for k in range(m)]
+        acc = [[Fraction(float(np.float32(keep * tau0[i, j]))) for j in range(n)] for i in range(n)]
+        touched = np.zeros((n, n), bool)
+        for k in range(m):
+            for t in range(n):
+                a, b = int(tours[k, t]), int(tours[k, t - 1])
+                acc[a][b] += w[k]
+                acc[b][a] += w[k]
+                touched[a, b] = touched[b, a] = True
+        for i in range(n):
+            for j in range(n):
+                ref = _rn32(acc[i][j]) if touched[i, j] else np.float32(keep * tau0[i, j])
+                assert got[i, j] == ref, (trial, i, j)
+
+
+def test_tour_length_integer_grid_exact(orc):
+    """On a line of integer points every edge and every partial sum is an
+    integer below 2^53, so any summation order gives the exact length."""
+    rng = np.random.default_rng(14)
+    n = 1000
+    x = rng.permutation(4 * n)[:n].astype(np.float32)
+    xy = np.stack([x, np.zeros(n, np.float32)], axis=1)
+    D = orc.distances(xy)
+    tours = np.stack([rng.permutation(n) for _ in range(3)]).astype(np.int32)
+    L = orc.tour_lengths(D, tours)
+    for k in range(3):
+        p = tours[k]
+        exact = sum(abs(int(x[p[t]]) - int(x[p[(t + 1) % n]])) for t in range(n))
+        assert L[k] == float(exact)
+
+
+def test_tour_length_blocked_error_bound(orc):
+    """fp64 in blocks of 32 edges: within (32 + n/32) roundings of the exact
+    sum (fsum), on random planar tours of ragged lengths."""
+    rng = np.random.default_rng(15)
+    u = 2.0 ** -53
+    for n in (3, 31, 32, 33, 1000, 1025):
+        xy = rng.uniform(0, 1, size=(n, 2)).astype(np.float32)
+        D = orc.distances(xy)
+        tours = np.stack([rng.permutation(n) for _ in range(4)]).astype(np.int32)
+        L = orc.tour_lengths(D, tours)
+        for k in range(4):
+            p = tours[k]
+            edges = [D[p[t], p[(t + 1) % n]] for t in range(n)]
+            exact = math.fsum(edges)
+            assert abs(L[k] - exact) <= (32 + n / 32 + 2) * u * exact

@@ -268,11 +268,13 @@ def test_evaporation_closed_form(orc):
     L = rng.uniform(1, 5, size=5)
     rho = np.float32(0.1)
     tau = np.ones((12, 12), np.float32)
+    keep = np.float32(1) - rho              # evaporation in fp32, the precision of M_tau
     for t in range(1, 61):
         tau = orc.deposit(tau, tours, L, rho=float(rho), Q=0.0)
-        exact = (1.0 - float(rho)) ** t
+        exact = float(keep) ** t
         ulp = 2.0 ** (math.frexp(exact)[1] - 24)
         assert np.all(np.abs(tau.astype(np.float64) - exact) <= t * ulp)
+        assert np.all(tau == tau[0, 0])
 
 
 def test_deposit_symmetry_sum_and_support(orc):
@@ -285,7 +287,7 @@ def test_deposit_symmetry_sum_and_support(orc):
     rho, Q = 0.25, 3.0
     tau = orc.deposit(tau0, tours, L, rho, Q)
     assert np.array_equal(tau, tau.T)
-    evap = (np.float64(1 - np.float64(np.float32(rho))) * tau0.astype(np.float64)).astype(np.float32)
+    evap = (np.float32(1) - np.float32(rho)) * tau0      # fp32 evaporation
     delta = tau.astype(np.float64) - evap.astype(np.float64)
     c = Q / L
     assert abs(delta.sum() - 2 * n * c.sum()) < 1e-5 * 2 * n * c.sum()
