@@ -65,7 +65,7 @@ const char* aco_last_error(void);
 
 /* Create the global solver on the current device: copies coords_host
  * (n x 2 fp32, (x, y) per city) to the device, builds the fp64 distance
- * matrix and eta^beta, sets tau = 1 (Sec. 2.1).  rho in [0,1], Q >= 0,
+ * matrix and eta^beta, sets tau = 1 (Sec. 2.1).  rho in [0,1], Q > 0,
  * alpha/beta integers in [0,8].  Replaces a previous global solver.
  * Uses the workspace given to aco_bind() when one is bound, else allocates. */
 int aco_init(const float* coords_host, int n, int m, float alpha, float beta, float rho,
@@ -83,8 +83,9 @@ int aco_set_variant(int roulette, float gamma_max, float gamma_min, int T);
  * Scores are always fp32, tau always fp32.  Takes effect at the next iteration. */
 int aco_set_precision(int prec);
 
-/* Deposit summation: ACO_DEPOSIT_DET sums Delta in fp64 in ascending ant
- * order (reproducible bit for bit); ACO_DEPOSIT_ATOMIC adds fl32(Q/L_k) with
+/* Deposit summation: ACO_DEPOSIT_DET gives every entry the exact sum of its
+ * paths' weights added to the evaporated value, rounded once to fp32 (no
+ * order; reproducible bit for bit); ACO_DEPOSIT_ATOMIC adds fl32(Q/L_k) with
  * fp32 atomics in hardware order (not reproducible). */
 int aco_set_deposit(int mode);
 
@@ -123,7 +124,7 @@ typedef struct aco_solver aco_solver;
 typedef struct {
   int n, m;
   int alpha, beta;          /* integers in [0, 8] */
-  float rho, Q, tau0;       /* rho in [0,1], Q >= 0, tau0 > 0 */
+  float rho, Q, tau0;       /* rho in [0,1], Q > 0, tau0 > 0 */
   uint64_t seed;
   int prec;                 /* ACO_FP32 / ACO_BF16 / ACO_FP16 */
   int roulette;             /* ACO_IR / ACO_ADAIR */
@@ -268,7 +269,9 @@ int aco_op_construct_ex(const void* P_dev, int prec, int n, int ld, int m, uint6
                         int mode, void* stream);
 
 /* Eq. 3 and the index mapping of Eq. 2: L_k = sum_t D[p_t][p_{t+1 mod n}] in
- * fp64 in t order (L_dev, m), c_k = fl64(Q / L_k) (c_dev, m), and for every
+ * fp64, in blocks of 32 consecutive edges (each summed in t order from 0, the
+ * block sums then added in block order) (L_dev, m), c_k = fl64(Q / L_k)
+ * (c_dev, m), and for every
  * city a the neighbours of a in tour k: nbr_dev[(a*m + k)*2 + {0,1}] =
  * (predecessor, successor) (nbr_dev: n*m*2 int32, nullable). */
 int aco_op_tour_length(const double* D_dev, int n, const int32_t* tours_dev, int m, float Q,
@@ -279,13 +282,20 @@ int aco_op_tour_length(const double* D_dev, int n, const int32_t* tours_dev, int
 int aco_op_best(const double* L_dev, const int32_t* tours_dev, int n, int m,
                 int32_t* best_tour_dev, double* best_len_dev, void* stream);
 
-/* Sec. 2.3, deterministic: Delta_ab = sum over ants k ascending whose tour
- * has edge {a,b} of c_k, in fp64; tau_ab <- fl32(fl64((1-rho) tau_ab) + Delta_ab).
- * Input: nbr/c from aco_op_tour_length.  tau_dev n x ld, updated in place. */
+/* Sec. 2.3, deterministic: tau'_ab = fl32(keep * tau_ab), keep = fl32(1 - rho)
+ * (fp32); an entry (a,b) on the tour of some ant becomes tau'_ab plus the
+ * c_k of every such ant, summed exactly and rounded once to fp32 (ties to
+ * even); other entries become tau'_ab.  The sum is exact, so no order of the
+ * ants is involved.  Input: nbr/c from aco_op_tour_length; every c_k must be
+ * >= 0 or +inf (+inf makes the entries of that tour +inf) and the positive
+ * finite ones must lie within a factor 2^19 of each other (true for the
+ * tour lengths of one planar instance).  Otherwise the entries are only
+ * evaporated and *err_dev (nullable, device int32) is set to 2.
+ * tau_dev n x ld, 16-byte aligned, updated in place. */
 int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const double* c_dev,
-                   int m, float rho, void* stream);
+                   int m, float rho, int32_t* err_dev, void* stream);
 
-/* Sec. 2.3, float-atomic: tau <- fl32(fl64(1-rho) tau), then for every
+/* Sec. 2.3, float-atomic: tau <- fl32(fl32(1-rho) tau), then for every
  * directed tour edge (a,b) of ant k: atomicAdd(tau_ab, fl32(c_k)). */
 int aco_op_deposit_atomic(float* tau_dev, int n, int ld, const int32_t* tours_dev,
                           const double* c_dev, int m, float rho, void* stream);
@@ -295,7 +305,7 @@ int aco_op_deposit_atomic(float* tau_dev, int n, int ld, const int32_t* tours_de
  * they update the pheromone (inside CUDA stream capture, in loops that must
  * not block on the allocator, or under a framework-owned memory pool).
  * Same results as aco_op_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c, nbr)
- * followed by aco_op_deposit(tau_dev, n, ld, nbr, c, m, rho), but the scratch
+ * followed by aco_op_deposit(tau_dev, n, ld, nbr, c, m, rho, NULL), but the scratch
  * c (m fp64) and nbr (2*n*m int32) lives in a fixed device array inside the
  * library of ACO_NOALLOC_SCRATCH_BYTES (16 MiB; every GPU that loads the
  * library holds it until exit), so 8*m (rounded up to 256) + 8*n*m must fit:

@@ -86,7 +86,7 @@ _SIGS = {
     "aco_op_construct_ex": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, v, v, v, i32, i32, i32, v]),
     "aco_op_tour_length": (i32, [v, i32, v, i32, f32, v, v, v, v]),
     "aco_op_best": (i32, [v, v, i32, i32, v, v, v]),
-    "aco_op_deposit": (i32, [v, i32, i32, v, v, i32, f32, v]),
+    "aco_op_deposit": (i32, [v, i32, i32, v, v, i32, f32, v, v]),
     "aco_op_deposit_atomic": (i32, [v, i32, i32, v, v, i32, f32, v]),
     "aco_op_deposit_tours_noalloc": (i32, [v, i32, i32, v, v, i32, f32, f32, v, v]),
     "aco_op_philox": (i32, [v, u64, v, i32, v]),
@@ -186,8 +186,9 @@ def op_best(L, tours, n, m, best_tour, best_len, stream=None):
     call("aco_op_best", ptr(L), ptr(tours), n, m, ptr(best_tour), ptr(best_len), stream_ptr(stream))
 
 
-def op_deposit(tau, n, ld, nbr, c, m, rho, stream=None):
-    call("aco_op_deposit", ptr(tau), n, ld, ptr(nbr), ptr(c), m, rho, stream_ptr(stream))
+def op_deposit(tau, n, ld, nbr, c, m, rho, err=None, stream=None):
+    call("aco_op_deposit", ptr(tau), n, ld, ptr(nbr), ptr(c), m, rho, ptr(err) if err is not None else None,
+         stream_ptr(stream))
 
 
 def op_deposit_atomic(tau, n, ld, tours, c, m, rho, stream=None):

@@ -71,24 +71,31 @@ __global__ void __launch_bounds__(256) batch_tour_length_kernel(const InstDev* _
   tour_length_ant(I.D, I.n, I.tours + (size_t)k * I.n, I.m, k, I.Q, I.L, I.c, I.nbr);
 }
 
-__global__ void __launch_bounds__(256) batch_best_kernel(const InstDev* __restrict__ insts) {
+__global__ void __launch_bounds__(256) batch_best_kernel(const InstDev* __restrict__ insts,
+                                                         int32_t* __restrict__ err) {
   __shared__ double sl[32];
   __shared__ int sk[33];
+  __shared__ int sred[100];
   const InstDev& I = insts[blockIdx.x];
   best_block(I.L, I.tours, I.n, I.m, I.best_tour, I.best_len, I.it, sl, sk);
+  const int2 d = deposit_scale_block(I.c, I.m, sred);
+  if (threadIdx.x == 0) {
+    *I.dep = d;
+    if (d.y == kDepBad && err) atomicExch(err, kErrDepositRange);
+  }
 }
 
-__global__ void __launch_bounds__(32) batch_deposit_kernel(const InstDev* __restrict__ insts,
-                                                           const int* __restrict__ row_off,
-                                                           int count) {
+__global__ void __launch_bounds__(kDepThreads) batch_deposit_kernel(const InstDev* __restrict__ insts,
+                                                                    const int* __restrict__ row_off,
+                                                                    int count) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int r = blockIdx.x;
   const int i = find_instance(row_off, count, r);
   const InstDev& I = insts[i];
   const int a = r - __ldg(row_off + i);
-  const double keep = 1.0 - (double)I.rho;
-  deposit_row(I.tau + (size_t)a * I.ld, I.n, I.nbr + (size_t)a * I.m * 2, I.c, I.m, keep,
-              deposit_tile(I.n), smem);
+  const int2 d = *I.dep;
+  deposit_row_exact(I.tau + (size_t)a * I.ld, I.n, reinterpret_cast<const int2*>(I.nbr) + (size_t)a * I.m,
+                    I.c, I.m, 1.0f - I.rho, d.x, d.y, deposit_cap(I.n, I.m), smem);
 }
 
 // ------------------------------------------------------------------ arena
@@ -188,7 +195,8 @@ struct aco_batch {
   int* d_counter = nullptr;
   int32_t* d_err = nullptr;
   std::vector<int> active;      // slot ids, n descending
-  int total_rows = 0, total_ants = 0, max_n = 0, max_tile = 0;
+  int total_rows = 0, total_ants = 0, max_n = 0;
+  size_t dep_smem = 0;          // deposit shared memory of the largest instance
   ConstructShape shape{0, 0, 0};  // forced shape for every class ({0,0,0}: per class)
   struct Class {
     int first, count, total;
@@ -240,16 +248,17 @@ static int batch_refresh(aco_batch* b) {
   std::vector<InstDev> insts(cnt);
   std::vector<int> row_off(cnt + 1, 0), ant_off(cnt + 1, 0);
   b->max_n = 0;
+  b->dep_smem = 0;
   for (int q = 0; q < cnt; ++q) {
     const Slot& s = b->slots[b->active[q]];
     insts[q] = s.dev;
     row_off[q + 1] = row_off[q] + s.p.n;
     ant_off[q + 1] = ant_off[q] + s.p.m;
     b->max_n = std::max(b->max_n, s.p.n);
+    b->dep_smem = std::max(b->dep_smem, deposit_smem_bytes(s.p.n, deposit_cap(s.p.n, s.p.m)));
   }
   b->total_rows = row_off[cnt];
   b->total_ants = ant_off[cnt];
-  b->max_tile = deposit_tile(std::max(b->max_n, 1));
   if (cnt) {
     ACO_CUDA_TRY(cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(InstDev) * cnt, cudaMemcpyHostToDevice, b->stream));
     ACO_CUDA_TRY(cudaMemcpyAsync(b->d_row_off, row_off.data(), sizeof(int) * (cnt + 1), cudaMemcpyHostToDevice, b->stream));
@@ -341,10 +350,9 @@ static int batch_enqueue(aco_batch* b) {
   batch_tour_length_kernel<<<(b->total_ants + 7) / 8, 256, 0, st>>>(b->d_insts, b->d_ant_off, cnt,
                                                                     b->total_ants);
   ACO_CHECK_LAUNCH("batch_tour_length_kernel");
-  batch_best_kernel<<<cnt, 256, 0, st>>>(b->d_insts);
+  batch_best_kernel<<<cnt, 256, 0, st>>>(b->d_insts, b->d_err);
   ACO_CHECK_LAUNCH("batch_best_kernel");
-  batch_deposit_kernel<<<b->total_rows, 32, deposit_smem_bytes(b->max_tile), st>>>(b->d_insts,
-                                                                                  b->d_row_off, cnt);
+  batch_deposit_kernel<<<b->total_rows, kDepThreads, b->dep_smem, st>>>(b->d_insts, b->d_row_off, cnt);
   ACO_CHECK_LAUNCH("batch_deposit_kernel");
   return ACO_OK;
 }
@@ -383,9 +391,9 @@ int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int
   if (dev_arena && ((uintptr_t)dev_arena & 255u)) return set_error(ACO_ERR_ARG, "arena must be 256-byte aligned");
   int rc = prepare_kernels();
   if (rc) return rc;
-  // the deposit's fp64 row tile may exceed the default 48 KB of dynamic shared memory
+  // the deposit's slot table may exceed the default 48 KB of dynamic shared memory
   ACO_CUDA_TRY(cudaFuncSetAttribute(batch_deposit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)deposit_smem_bytes(deposit_tile(ACO_MAX_N))));
+                                    (int)deposit_smem_bytes(ACO_MAX_N, kDepCap)));
   aco_batch* b = new aco_batch();
   b->prec = prec;
   b->stream = static_cast<cudaStream_t>(stream);

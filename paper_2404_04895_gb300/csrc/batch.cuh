@@ -18,6 +18,7 @@ struct InstDev {
   int32_t* tours;                 // m x n
   double* L;                      // m
   double* c;                      // m
+  int2* dep;                      // deposit weights' scaling (E0, mode), written by best
   int32_t* nbr;                   // n x m x 2
   int32_t* best_tour;             // n
   double* best_len;               // 1

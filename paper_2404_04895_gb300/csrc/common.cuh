@@ -14,6 +14,10 @@
 
 namespace aco {
 
+// kernel-side check codes written to an instance's error word
+constexpr int kErrConstruct = 1;     // an ant found no unvisited city
+constexpr int kErrDepositRange = 2;  // deposit weights negative, NaN or spanning > 2^19
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
 //   (c0,c1,c2,c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),

@@ -382,7 +382,7 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
     }  // full scan
 
     if (next < 0 || next >= n) {  // no unvisited city found: cannot happen for valid input
-      if (gl == 0 && err) atomicExch(err, 1);
+      if (gl == 0 && err) atomicExch(err, kErrConstruct);
       break;
     }
     if (gl == 0) tour[t] = next;

@@ -174,7 +174,7 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
     }
 
     if (next < 0 || next >= n) {  // no unvisited city found: cannot happen for valid input
-      if (lane == 0 && err) atomicExch(err, 1);
+      if (lane == 0 && err) atomicExch(err, kErrConstruct);
       break;
     }
     if (lane == 0) {

@@ -91,27 +91,50 @@ __global__ void __launch_bounds__(1024) best_kernel(const double* __restrict__ L
                                                     const int32_t* __restrict__ tours, int n,
                                                     int m, int32_t* __restrict__ best_tour,
                                                     double* __restrict__ best_len,
-                                                    uint32_t* __restrict__ it_dev) {
+                                                    uint32_t* __restrict__ it_dev,
+                                                    const double* __restrict__ c,
+                                                    int2* __restrict__ dep, int32_t* __restrict__ err) {
   __shared__ double sl[32];
   __shared__ int sk[33];
+  __shared__ int sred[100];
   best_block(L, tours, n, m, best_tour, best_len, it_dev, sl, sk);
+  if (dep) {
+    const int2 d = deposit_scale_block(c, m, sred);
+    if (threadIdx.x == 0) {
+      *dep = d;
+      if (d.y == kDepBad && err) atomicExch(err, kErrDepositRange);
+    }
+  }
 }
 
-__global__ void __launch_bounds__(32) deposit_kernel(float* __restrict__ tau, int n, int ld,
-                                                     const int32_t* __restrict__ nbr,
-                                                     const double* __restrict__ c, int m,
-                                                     double keep, int tile) {
+// One CTA per row.  The weights' scaling comes from dep (written by the best
+// kernel) or, when dep is null, is derived by every CTA from c itself.
+__global__ void __launch_bounds__(kDepThreads) deposit_kernel(float* __restrict__ tau, int n, int ld,
+                                                              const int32_t* __restrict__ nbr,
+                                                              const double* __restrict__ c, int m,
+                                                              float keep, const int2* __restrict__ dep,
+                                                              int cap, int32_t* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int sred[100];
+  int2 d;
+  if (dep) {
+    d = *dep;
+  } else {
+    d = deposit_scale_block(c, m, sred);
+    if (d.y == kDepBad && blockIdx.x == 0 && threadIdx.x == 0 && err) atomicExch(err, kErrDepositRange);
+  }
   const int a = blockIdx.x;
-  deposit_row(tau + (size_t)a * ld, n, nbr + (size_t)a * m * 2, c, m, keep, tile, smem);
+  deposit_row_exact(tau + (size_t)a * ld, n, reinterpret_cast<const int2*>(nbr) + (size_t)a * m, c, m,
+                    keep, d.x, d.y, cap, smem);
 }
 
-__global__ void evaporate_kernel(float* __restrict__ tau, int n, int ld, double keep) {
+// tau <- fl32(keep * tau), keep = fl32(1 - rho): evaporation in fp32
+__global__ void evaporate_kernel(float* __restrict__ tau, int n, int ld, float keep) {
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   float* p = tau + (size_t)i * ld + j;
-  *p = __double2float_rn(__dmul_rn(keep, (double)*p));
+  *p = __fmul_rn(keep, *p);
 }
 
 // Float-atomic deposit: every directed tour edge adds fl32(c_k) in hardware order.
@@ -210,29 +233,30 @@ int launch_tour_length(const double* D, int n, const int32_t* tours, int m, floa
 }
 
 int launch_best(const double* L, const int32_t* tours, int n, int m, int32_t* best_tour,
-                double* best_len, uint32_t* it_dev, cudaStream_t st) {
-  best_kernel<<<1, 1024, 0, st>>>(L, tours, n, m, best_tour, best_len, it_dev);
+                double* best_len, uint32_t* it_dev, const double* c, int2* dep, int32_t* err,
+                cudaStream_t st) {
+  best_kernel<<<1, 1024, 0, st>>>(L, tours, n, m, best_tour, best_len, it_dev, c, dep, err);
   return check_launch("best_kernel");
 }
 
 int prepare_deposit() {
   ACO_CUDA_TRY(cudaFuncSetAttribute(deposit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    200 * 1024));
+                                    (int)deposit_smem_bytes(ACO_MAX_N, kDepCap)));
   return ACO_OK;
 }
 
 int launch_deposit(float* tau, int n, int ld, const int32_t* nbr, const double* c, int m,
-                   float rho, cudaStream_t st) {
-  const int tile = deposit_tile(n);
-  const size_t smem = deposit_smem_bytes(tile);
-  const double keep = 1.0 - (double)rho;
-  deposit_kernel<<<n, 32, smem, st>>>(tau, n, ld, nbr, c, m, keep, tile);
+                   float rho, const int2* dep, int32_t* err, cudaStream_t st) {
+  const int cap = deposit_cap(n, m);
+  const size_t smem = deposit_smem_bytes(n, cap);
+  const float keep = 1.0f - rho;
+  deposit_kernel<<<n, kDepThreads, smem, st>>>(tau, n, ld, nbr, c, m, keep, dep, cap, err);
   return check_launch("deposit_kernel");
 }
 
 int launch_deposit_atomic(float* tau, int n, int ld, const int32_t* tours, const double* c, int m,
                           float rho, cudaStream_t st) {
-  const double keep = 1.0 - (double)rho;
+  const float keep = 1.0f - rho;
   dim3 g1((n + 255) / 256, n);
   evaporate_kernel<<<g1, 256, 0, st>>>(tau, n, ld, keep);
   int rc = check_launch("evaporate_kernel");

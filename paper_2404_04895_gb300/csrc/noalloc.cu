@@ -19,6 +19,7 @@
 // has to be cleared between calls.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "internal.h"
@@ -62,7 +63,7 @@ extern "C" int aco_op_deposit_tours_noalloc(float* tau_dev, int n, int ld, const
   if (ld < n || (ld & 7) || !aligned16(tau_dev))
     return set_error(ACO_ERR_ARG, "tau: ld must be >= n and a multiple of 8, base 16-byte aligned");
   if (!(rho >= 0.0f && rho <= 1.0f)) return set_error(ACO_ERR_ARG, "rho outside [0, 1]");
-  if (!(Q >= 0.0f)) return set_error(ACO_ERR_ARG, "Q must be >= 0");
+  if (!(Q > 0.0f) || !std::isfinite(Q)) return set_error(ACO_ERR_ARG, "Q must be finite and > 0");
   const size_t c_bytes = round256((size_t)m * sizeof(double));
   const size_t need = c_bytes + (size_t)n * m * 2 * sizeof(int32_t);
   if (need > ACO_NOALLOC_SCRATCH_BYTES)
@@ -79,5 +80,5 @@ extern "C" int aco_op_deposit_tours_noalloc(float* tau_dev, int n, int ld, const
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc = launch_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c, nbr, st);
   if (rc) return rc;
-  return launch_deposit(tau_dev, n, ld, nbr, c, m, rho, st);
+  return launch_deposit(tau_dev, n, ld, nbr, c, m, rho, nullptr, nullptr, st);
 }

@@ -167,7 +167,7 @@ static int validate(const aco_params* p) {
   if (p->alpha < 0 || p->alpha > 8 || p->beta < 0 || p->beta > 8)
     return set_error(ACO_ERR_UNSUPPORTED, "alpha/beta must be integers in [0, 8]");
   if (!(p->rho >= 0.0f && p->rho <= 1.0f)) return set_error(ACO_ERR_ARG, "rho outside [0, 1]");
-  if (!(p->Q >= 0.0f) || !std::isfinite(p->Q)) return set_error(ACO_ERR_ARG, "Q must be finite and >= 0");
+  if (!(p->Q > 0.0f) || !std::isfinite(p->Q)) return set_error(ACO_ERR_ARG, "Q must be finite and > 0");
   if (!(p->tau0 > 0.0f) || !std::isfinite(p->tau0)) return set_error(ACO_ERR_ARG, "tau0 must be finite and > 0");
   if (p->prec < ACO_FP32 || p->prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", p->prec);
   if (p->roulette != ACO_IR && p->roulette != ACO_ADAIR) return set_error(ACO_ERR_ARG, "unknown roulette %d", p->roulette);
@@ -185,8 +185,8 @@ static int validate(const aco_params* p) {
 constexpr int kSchedCap = 1 << 16;  // AdaIR schedule entries (iterations 0..T, clamped)
 
 struct Layout {
-  size_t coords, D, H, tau, P, tours, L, c, nbr, best_tour, best_len, it, err, sched, lists, lcnt,
-      lkey, total;
+  size_t coords, D, H, tau, P, tours, L, c, dep, nbr, best_tour, best_len, it, err, sched, lists,
+      lcnt, lkey, total;
 };
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -209,6 +209,7 @@ static Layout layout_of(int n, int m) {
   L.tours = take((size_t)m * n * 4);
   L.L = take((size_t)m * 8);
   L.c = take((size_t)m * 8);
+  L.dep = take(8);
   L.nbr = take((size_t)n * m * 2 * 4);
   L.best_tour = take((size_t)n * 4);
   L.best_len = take(8);
@@ -253,6 +254,7 @@ int instance_bind(const aco_params& p, unsigned char* ws, InstDev* d, cudaStream
   x.tours = reinterpret_cast<int32_t*>(ws + L.tours);
   x.L = reinterpret_cast<double*>(ws + L.L);
   x.c = reinterpret_cast<double*>(ws + L.c);
+  x.dep = reinterpret_cast<int2*>(ws + L.dep);
   x.nbr = reinterpret_cast<int32_t*>(ws + L.nbr);
   x.best_tour = reinterpret_cast<int32_t*>(ws + L.best_tour);
   x.best_len = reinterpret_cast<double*>(ws + L.best_len);
@@ -296,6 +298,7 @@ struct aco_solver {
   int* lcnt;
   uint32_t* lkey;
   double *D, *L, *c, *best_len;
+  int2* dep;
   int32_t *tours, *nbr, *best_tour, *err;
   uint32_t* it_dev;
   uint32_t it;                 // iterations completed (host mirror)
@@ -363,11 +366,12 @@ static int enqueue_iteration(aco_solver* s) {
   rc = launch_tour_length(s->D, n, s->tours, m, p.Q, s->L, s->c, det ? s->nbr : nullptr, st);
   if (rc) return rc;
   probe(3);
-  rc = launch_best(s->L, s->tours, n, m, s->best_tour, s->best_len, s->it_dev, st);
+  rc = launch_best(s->L, s->tours, n, m, s->best_tour, s->best_len, s->it_dev, s->c, det ? s->dep : nullptr,
+                   s->err, st);
   if (rc) return rc;
   probe(4);
   if (det)
-    rc = launch_deposit(s->tau, n, s->ld, s->nbr, s->c, m, p.rho, st);
+    rc = launch_deposit(s->tau, n, s->ld, s->nbr, s->c, m, p.rho, s->dep, s->err, st);
   else
     rc = launch_deposit_atomic(s->tau, n, s->ld, s->tours, s->c, m, p.rho, st);
   if (rc) return rc;
@@ -490,6 +494,7 @@ int aco_create(aco_solver** out, const float* coords_host, const aco_params* p, 
   s->tours = s->at<int32_t>(L.tours);
   s->L = s->at<double>(L.L);
   s->c = s->at<double>(L.c);
+  s->dep = s->at<int2>(L.dep);
   s->nbr = s->at<int32_t>(L.nbr);
   s->best_tour = s->at<int32_t>(L.best_tour);
   s->best_len = s->at<double>(L.best_len);
@@ -909,12 +914,12 @@ int aco_op_best(const double* L_dev, const int32_t* tours_dev, int n, int m, int
                 double* best_len_dev, void* stream) {
   if (!L_dev || !tours_dev || !best_tour_dev || !best_len_dev) return set_error(ACO_ERR_ARG, "NULL argument");
   if (n < 3 || n > ACO_MAX_N || m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "n or m out of range");
-  return launch_best(L_dev, tours_dev, n, m, best_tour_dev, best_len_dev, nullptr,
+  return launch_best(L_dev, tours_dev, n, m, best_tour_dev, best_len_dev, nullptr, nullptr, nullptr, nullptr,
                      static_cast<cudaStream_t>(stream));
 }
 
 int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const double* c_dev, int m,
-                   float rho, void* stream) {
+                   float rho, int32_t* err_dev, void* stream) {
   int rc = check_mat(tau_dev, n, ld, "tau");
   if (rc) return rc;
   if (!nbr_dev || !c_dev) return set_error(ACO_ERR_ARG, "NULL argument");
@@ -922,7 +927,8 @@ int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const 
   if (!(rho >= 0.0f && rho <= 1.0f)) return set_error(ACO_ERR_ARG, "rho outside [0, 1]");
   rc = prepare_kernels();
   if (rc) return rc;
-  return launch_deposit(tau_dev, n, ld, nbr_dev, c_dev, m, rho, static_cast<cudaStream_t>(stream));
+  return launch_deposit(tau_dev, n, ld, nbr_dev, c_dev, m, rho, nullptr, err_dev,
+                        static_cast<cudaStream_t>(stream));
 }
 
 int aco_op_deposit_atomic(float* tau_dev, int n, int ld, const int32_t* tours_dev, const double* c_dev,

@@ -6,7 +6,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <climits>
+
 #include "common.cuh"
+#include "exact.cuh"
 
 namespace aco {
 
@@ -82,46 +85,54 @@ __device__ __forceinline__ void build_P_row(const float* __restrict__ tau_row,
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 3 + Eq. 2 for ant k (one warp): edge lengths D[p_t][p_{t+1}] gathered
-// 32*U at a time, summed in fp64 in t order through shuffles (the order of a
-// sequential loop); for city a = p_t the index mapping nbr[a][k] =
-// (p_{t-1}, p_{t+1}); L_k and c_k = Q / L_k.
+// Eq. 3 + Eq. 2 for ant k (one warp).  f in fp64 in blocks of 32 consecutive
+// edges: in round r lane l sums block b = 32r + l (edges 32b .. 32b+31) in
+// edge order, then the round's block sums are added to the total in block
+// order -- chains of 32 + n/32 additions instead of n.  For city a = p_t the
+// index mapping nbr[a][k] = (p_{t-1}, p_{t+1}); L_k and c_k = Q / L_k.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void tour_length_ant(const double* __restrict__ D, int n,
                                                 const int32_t* __restrict__ p, int m, int k,
                                                 float Q, double* __restrict__ L,
                                                 double* __restrict__ c,
                                                 int32_t* __restrict__ nbr) {
-  constexpr int U = 4;
   const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int base = 0; base < n; base += 32 * U) {
-    double d[U];
+  const int nb = (n + 31) >> 5;
+  double total = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 32) {
+    const int b = b0 + lane;
+    double s = 0.0;
+    if (b < nb) {
+      const int t0 = b << 5;
+      const int cnt = min(32, n - t0);
+      int prev = __ldg(p + (t0 > 0 ? t0 - 1 : n - 1));
+      int cur = __ldg(p + t0);
+      double d[32];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int t = base + u * 32 + lane;
-      d[u] = 0.0;
-      if (t < n) {
-        const int a = p[t];
-        const int b = p[t + 1 < n ? t + 1 : 0];
-        const int pr = p[t > 0 ? t - 1 : n - 1];
-        // tours come from the construction kernel; an entry out of range (only
-        // after a failed construction, which the host reports) is skipped
-        if ((unsigned)a < (unsigned)n && (unsigned)b < (unsigned)n) {
-          d[u] = __ldg(D + (size_t)a * n + b);
-          if (nbr) reinterpret_cast<int2*>(nbr)[(size_t)a * m + k] = make_int2(pr, b);
+      for (int i = 0; i < 32; ++i) {
+        d[i] = 0.0;  // past the last edge: adding +0 leaves s unchanged
+        if (i < cnt) {
+          const int t = t0 + i;
+          const int nx = __ldg(p + (t + 1 < n ? t + 1 : 0));
+          // tours come from the construction kernel; an entry out of range
+          // (only after a failed construction, which the host reports) is skipped
+          if ((unsigned)cur < (unsigned)n && (unsigned)nx < (unsigned)n) {
+            d[i] = __ldg(D + (size_t)cur * n + nx);
+            if (nbr) reinterpret_cast<int2*>(nbr)[(size_t)cur * m + k] = make_int2(prev, nx);
+          }
+          prev = cur;
+          cur = nx;
         }
       }
-    }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int cnt = min(32, n - (base + u * 32));
-      for (int q = 0; q < cnt; ++q) s = __dadd_rn(s, __shfl_sync(ACO_FULL_MASK, d[u], q));
+      for (int i = 0; i < 32; ++i) s = __dadd_rn(s, d[i]);
     }
+    const int nr = min(32, nb - b0);
+    for (int q = 0; q < nr; ++q) total = __dadd_rn(total, __shfl_sync(ACO_FULL_MASK, s, q));
   }
   if (lane == 0) {
-    L[k] = s;
-    if (c) c[k] = __ddiv_rn((double)Q, s);
+    L[k] = total;
+    if (c) c[k] = __ddiv_rn((double)Q, total);
   }
 }
 
@@ -178,98 +189,240 @@ __device__ __forceinline__ void best_block(const double* __restrict__ L,
 }
 
 // ---------------------------------------------------------------------------
-// Sec. 2.3 deterministic deposit of row a (one warp).  The row's increment
-// Delta_a. is accumulated in fp64 shared memory; the row's 2m index-mapping
-// entries (two neighbours per ant) are taken 16 ants at a time: lanes 0-15
-// hold predecessors, lanes 16-31 successors.  __match_any_sync groups lanes
-// with the same target column b; the lane of the lowest ant in a group adds
-// the group's c_k to Delta_ab in ascending k, so every Delta_ab is summed in
-// ascending ant order.  Columns in tiles of `tile`, ants in chunks of 1024.
-// smem: tile doubles + kDepAntChunk * 16 bytes.
+// Scaling of the deposit weights c[0..m) for the exact fixed-point sums
+// (exact.cuh): x = E0, the smallest exponent of a positive finite weight, and
+// y = mode: kDepFixed; kDepInf if some weight is +inf (a zero tour length:
+// every city at one point); kDepBad if a weight is negative or NaN, or the
+// positive ones span more than kDepSpan binades (tour lengths of one planar
+// instance span at most log2(n) + 1).  All threads of the CTA; every thread
+// gets the result.  sred: 100 ints of shared memory.
 // ---------------------------------------------------------------------------
-constexpr int kDepAntChunk = 1024;
+__device__ __forceinline__ int2 deposit_scale_block(const double* __restrict__ c, int m, int* sred) {
+  int emin = INT_MAX, emax = INT_MIN;
+  unsigned flags = 0u;  // 1: +inf seen, 2: negative or NaN seen
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    const double v = c[k];
+    if (v > 0.0 && v < INFINITY) {
+      const int e = exponent_of(v);
+      emin = min(emin, e);
+      emax = max(emax, e);
+    } else if (v == INFINITY) {
+      flags |= 1u;
+    } else if (!(v == 0.0)) {
+      flags |= 2u;
+    }
+  }
+  emin = __reduce_min_sync(ACO_FULL_MASK, emin);
+  emax = __reduce_max_sync(ACO_FULL_MASK, emax);
+  flags = __reduce_or_sync(ACO_FULL_MASK, flags);
+  const int w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  if ((threadIdx.x & 31) == 0) {
+    sred[w] = emin;
+    sred[32 + w] = emax;
+    sred[64 + w] = (int)flags;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    const int a = __reduce_min_sync(ACO_FULL_MASK, l < nw ? sred[l] : INT_MAX);
+    const int b = __reduce_max_sync(ACO_FULL_MASK, l < nw ? sred[32 + l] : INT_MIN);
+    const unsigned f = __reduce_or_sync(ACO_FULL_MASK, l < nw ? (unsigned)sred[64 + l] : 0u);
+    if (l == 0) {
+      sred[96] = a;
+      sred[97] = b;
+      sred[98] = (int)f;
+    }
+  }
+  __syncthreads();
+  emin = sred[96];
+  emax = sred[97];
+  flags = (unsigned)sred[98];
+  __syncthreads();  // sred may be reused by the caller
+  int mode = (flags & 2u) ? kDepBad : (flags & 1u) ? kDepInf : kDepFixed;
+  if (emin != INT_MAX && emax - emin > kDepSpan) mode = kDepBad;
+  return make_int2(emin == INT_MAX ? 0 : emin, mode);
+}
 
-__device__ __forceinline__ void deposit_row(float* __restrict__ row, int n,
-                                            const int32_t* __restrict__ nbr_row,
-                                            const double* __restrict__ c, int m, double keep,
-                                            int tile, unsigned char* smem) {
-  double* delta = reinterpret_cast<double*>(smem);            // [tile]
-  double* cs = delta + tile;                                  // [kDepAntChunk]
-  int2* items = reinterpret_cast<int2*>(cs + kDepAntChunk);   // [kDepAntChunk]
-  const int lane = threadIdx.x & 31;
-  for (int col0 = 0; col0 < n; col0 += tile) {
-    const int cols = min(tile, n - col0);
-    for (int q = lane; q < cols; q += 32) delta[q] = 0.0;
-    for (int kb = 0; kb < m; kb += kDepAntChunk) {
-      const int cnt = min(kDepAntChunk, m - kb);
-      __syncwarp();
-      const int2* src = reinterpret_cast<const int2*>(nbr_row) + kb;
-#pragma unroll 4
-      for (int q = lane; q < cnt; q += 32) {
-        items[q] = __ldg(src + q);
-        cs[q] = __ldg(c + kb + q);
+// ---------------------------------------------------------------------------
+// Sec. 2.3 evaporation + deposit of one row a (all threads of the CTA), in
+// the order-free reading: tau'_ab = fl32(keep * tau_ab) with keep =
+// fl32(1 - rho); an entry that some path uses becomes tau'_ab + the sum of
+// those paths' weights, taken exactly and rounded once to fp32.
+//   1. the row's 2m index-mapping entries (two neighbours per ant) mark the
+//      touched columns in a shared bitmap
+//   2. a touched column's slot is the number of touched columns before it
+//      (exclusive scan of the bitmap's popcounts), so slots are dense
+//   3. each warp takes 32 ants at a time: lanes whose columns share a slot
+//      are grouped by __match_any_sync, their 24-bit weight chunks summed by
+//      one redux per chunk, and the group's leader adds the sums to the
+//      slot's carry-save words with shared 64-bit atomics (integer sums: any
+//      order gives the same bits)
+//   4. one coalesced pass over the row writes tau' or the rounded sum
+// At most `cap` slots are summed per pass; rows with more touched columns
+// take further passes (only their touched columns are rewritten).
+// smem: deposit_smem_bytes(n, cap).
+// ---------------------------------------------------------------------------
+constexpr int kDepThreads = 256;
+constexpr int kDepCap = 2048;
+
+__host__ __device__ inline int deposit_cap(int n, long long m) {
+  long long c = 2 * m < (long long)n ? 2 * m : (long long)n;
+  return (int)(c < kDepCap ? c : kDepCap);
+}
+
+__host__ __device__ inline size_t deposit_smem_bytes(int n, int cap) {
+  const size_t nw = (size_t)(n + 31) / 32;
+  return (size_t)cap * 32 + nw * 8 + 33 * 4;
+}
+
+__device__ __forceinline__ void deposit_row_exact(float* __restrict__ row, int n,
+                                                  const int2* __restrict__ nbr_row,
+                                                  const double* __restrict__ c, int m, float keep,
+                                                  int E0, int mode, int cap, unsigned char* smem) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthr = blockDim.x;
+  const int nw = (n + 31) >> 5;
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem);  // [cap][4]
+  uint32_t* bm = reinterpret_cast<uint32_t*>(acc + (size_t)cap * 4);      // [nw]
+  uint32_t* base = bm + nw;                                                // [nw]
+  int* sc = reinterpret_cast<int*>(base + nw);                             // [33]
+
+  // 1. touched columns
+  for (int w = tid; w < nw; w += nthr) bm[w] = 0u;
+  __syncthreads();
+  if (mode != kDepBad) {
+    for (int k = tid; k < m; k += nthr) {
+      const int2 e = __ldg(nbr_row + k);
+      if ((unsigned)e.x < (unsigned)n) atomicOr(bm + (e.x >> 5), 1u << (e.x & 31));
+      if ((unsigned)e.y < (unsigned)n) atomicOr(bm + (e.y >> 5), 1u << (e.y & 31));
+    }
+  }
+  __syncthreads();
+
+  // 2. dense slots: exclusive scan of the popcounts, each thread a run of words
+  const int per = (nw + nthr - 1) / nthr;
+  const int wb = tid * per;
+  int loc = 0;
+  for (int q = 0; q < per; ++q)
+    if (wb + q < nw) loc += __popc(bm[wb + q]);
+  int incl = loc;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int v = __shfl_up_sync(ACO_FULL_MASK, incl, off);
+    if (lane >= off) incl += v;
+  }
+  if (lane == 31) sc[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int v = lane < (nthr >> 5) ? sc[lane] : 0;
+    int inc = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int u = __shfl_up_sync(ACO_FULL_MASK, inc, off);
+      if (lane >= off) inc += u;
+    }
+    sc[lane] = inc - v;
+    if (lane == 31) sc[32] = inc;
+  }
+  __syncthreads();
+  {
+    int run = sc[warp] + incl - loc;
+    for (int q = 0; q < per; ++q)
+      if (wb + q < nw) {
+        base[wb + q] = (uint32_t)run;
+        run += __popc(bm[wb + q]);
       }
-      __syncwarp();
-      for (int k0 = 0; k0 < cnt; k0 += 16) {
-        const int ai = lane & 15;  // ant k0 + ai
-        const bool valid = k0 + ai < cnt;
-        int b = -1;
+  }
+  const int D = sc[32];
+  __syncthreads();
+  auto slot_of = [&](int j) -> int {
+    return (int)base[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
+  };
+
+  float4* row4 = reinterpret_cast<float4*>(row);
+  const int npass = D > 0 ? (D + cap - 1) / cap : 1;
+  for (int p = 0; p < npass; ++p) {
+    const int s0 = p * cap;
+    const int used = min(cap, D - s0);
+    for (int q = tid; q < used * 4; q += nthr) acc[q] = 0ull;
+    __syncthreads();
+
+    // 3. exact sums
+    if (used > 0) {
+      for (int kb = warp * 32; kb < m; kb += nthr) {
+        const int k = kb + lane;
+        const bool valid = k < m;
+        int2 e = make_int2(-1, -1);
+        uint32_t q0 = 0u, q1 = 0u, q2 = 0u, qi = 0u;
         if (valid) {
-          const int2 it = items[k0 + ai];
-          b = (lane >> 4 ? it.y : it.x) - col0;
+          e = __ldg(nbr_row + k);
+          const double v = __ldg(c + k);
+          if (v > 0.0 && v < INFINITY)
+            weight_chunks(v, E0, &q0, &q1, &q2);
+          else if (v == INFINITY)
+            qi = 1u;
         }
-        const bool in_tile = valid && b >= 0 && b < cols;
-        const int key = in_tile ? b : -1 - lane;  // unique keys for idle lanes
-        const unsigned grp = __match_any_sync(ACO_FULL_MASK, key);
-        if (in_tile) {
-          const unsigned ants = (grp & 0xFFFFu) | (grp >> 16);
-          const int lead = __ffs(ants) - 1;
-          if (lead == ai) {
-            double sum = delta[b];
-            unsigned rest = ants;
-            while (rest) {
-              const int i = __ffs(rest) - 1;
-              rest &= rest - 1u;
-              sum = __dadd_rn(sum, cs[k0 + i]);
-            }
-            delta[b] = sum;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const int col = side ? e.y : e.x;
+          const bool ok = valid && (unsigned)col < (unsigned)n;
+          const int sl = ok ? slot_of(col) - s0 : -1;
+          const bool in = ok && sl >= 0 && sl < cap;
+          const unsigned grp = __match_any_sync(ACO_FULL_MASK, in ? sl : -1 - lane);
+          const uint32_t r0 = __reduce_add_sync(grp, in ? q0 : 0u);
+          const uint32_t r1 = __reduce_add_sync(grp, in ? q1 : 0u);
+          const uint32_t r2 = __reduce_add_sync(grp, in ? q2 : 0u);
+          uint32_t ri = 0u;
+          if (mode == kDepInf) ri = __reduce_add_sync(grp, in ? qi : 0u);
+          if (in && lane == __ffs(grp) - 1) {
+            unsigned long long* a = acc + 4 * sl;
+            if (r0) atomicAdd(a + 0, (unsigned long long)r0);
+            if (r1) atomicAdd(a + 1, (unsigned long long)r1);
+            if (r2) atomicAdd(a + 2, (unsigned long long)r2);
+            if (ri) atomicAdd(a + 3, (unsigned long long)ri);
           }
         }
-        __syncwarp();
       }
     }
-    __syncwarp();
-    // tau_ab <- fl32(fl64(keep * tau_ab) + Delta_ab), four columns per lane step
-    const int nv = cols >> 2;
-    float4* row4 = reinterpret_cast<float4*>(row + col0);
-#pragma unroll 4
-    for (int q = lane; q < nv; q += 32) {
-      float4 v = row4[q];
-      const double* dl = delta + 4 * q;
-      v.x = __double2float_rn(__dadd_rn(__dmul_rn(keep, (double)v.x), dl[0]));
-      v.y = __double2float_rn(__dadd_rn(__dmul_rn(keep, (double)v.y), dl[1]));
-      v.z = __double2float_rn(__dadd_rn(__dmul_rn(keep, (double)v.z), dl[2]));
-      v.w = __double2float_rn(__dadd_rn(__dmul_rn(keep, (double)v.w), dl[3]));
-      row4[q] = v;
+    __syncthreads();
+
+    // 4. the row: tau' everywhere on the first pass, rounded sums on touched entries
+    for (int q = tid; 4 * q < n; q += nthr) {
+      const int j0 = 4 * q;
+      const uint32_t nib = (bm[j0 >> 5] >> (j0 & 31)) & 0xFu;
+      if (p > 0 && nib == 0u) continue;
+      const bool full = j0 + 4 <= n;
+      float v[4];
+      if (full) {
+        const float4 x = row4[q];
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = j0 + i < n ? row[j0 + i] : 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float tp = __fmul_rn(keep, v[i]);
+        if (!((nib >> i) & 1u)) {
+          if (p == 0) v[i] = tp;
+          continue;
+        }
+        const int sl = slot_of(j0 + i) - s0;
+        if (sl < 0 || sl >= cap) continue;  // summed in another pass
+        const unsigned long long* a = acc + 4 * sl;
+        v[i] = (mode == kDepInf && a[3]) ? INFINITY : round_sum_f32(tp, a[0], a[1], a[2], E0);
+      }
+      if (full) {
+        row4[q] = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+        for (int i = 0; i < 4 && j0 + i < n; ++i) row[j0 + i] = v[i];
+      }
     }
-    for (int q = 4 * nv + lane; q < cols; q += 32) {
-      const int j = col0 + q;
-      row[j] = __double2float_rn(__dadd_rn(__dmul_rn(keep, (double)row[j]), delta[q]));
-    }
-    __syncwarp();
+    __syncthreads();
   }
-}
-
-// fp64 shared bytes deposit_row needs for a tile of `tile` columns
-__host__ __device__ inline size_t deposit_smem_bytes(int tile) {
-  return (size_t)tile * 8 + (size_t)kDepAntChunk * 16;
-}
-
-// Column tile: the fp64 delta tile plus the per-chunk c and items fit 200 KB;
-// a multiple of 4 so that every tile's columns start 16-byte aligned.
-__host__ __device__ inline int deposit_tile(int n) {
-  const int max_tile = ((200 * 1024 - kDepAntChunk * 16) / 8) & ~3;
-  return n < max_tile ? n : max_tile;
 }
 
 }  // namespace aco

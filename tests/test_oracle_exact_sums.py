@@ -91,10 +91,14 @@ def test_exact_sum_f32_boundaries(orc):
 
 def test_deposit_single_rounding_golden(orc):
     ref = np.loadtxt(golden_path("deposit_single_rounding.txt"), dtype=np.float64)
-    tours = np.array([[0, 1, 2], [1, 2, 0]], dtype=np.int32)
-    L = np.array([2.0 ** 24, 2.0 ** 60])
-    tau = orc.deposit(np.ones((3, 3), np.float32), tours, L, rho=0.0, Q=1.0)
+    tours = np.array([[0, 1, 2]], dtype=np.int32)
+    L = np.array([float.fromhex("0x1.fffffffp-17")])
+    tau = orc.deposit(np.full((3, 3), 2.0 ** 40, np.float32), tours, L, rho=0.0, Q=1.0)
     assert np.array_equal(tau.astype(np.float64), ref)
+    # weights far apart (36 binades): 1 + 2^-24 + 2^-60 is above the tie at 1 + 2^-24
+    tau = orc.deposit(np.ones((3, 3), np.float32), np.array([[0, 1, 2], [1, 2, 0]], np.int32),
+                      np.array([2.0 ** 24, 2.0 ** 60]), rho=0.0, Q=1.0)
+    assert tau[0, 1] == np.float32(1 + 2.0 ** -23) and tau[0, 0] == np.float32(1)
 
 
 def test_deposit_is_rounded_exact_sum(orc):
