@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 from paper_2404_04895_gb300 import instances  # noqa: E402
 
 METRIC = "ant-steps/s"
+STEPS = ["build_P", "build_lists", "construct", "tour_length", "best", "deposit"]
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -48,7 +49,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--gap-seeds", type=int, default=5)
-    ap.add_argument("--no-autotune", action="store_true", help="default construct shape (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true", help="default full-scan shape (profiling runs)")
+    ap.add_argument("--no-lists", action="store_true",
+                    help="time the full-scan construction instead of the candidate-list one")
+    ap.add_argument("--no-full-scan", action="store_true",
+                    help="skip the side measurement of the full-scan construction kernel")
     return ap.parse_args()
 
 
@@ -75,21 +80,29 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def construct_source_hash():
+KERNEL_SOURCES = {
+    # the candidate-list construction kernel and what shapes its traffic (the lists)
+    "construct_lean_kernel": ("construct_lean.cuh", "construct.cuh", "common.cuh", "steps.cuh"),
+    # the full-scan construction kernel
+    "construct_kernel": ("construct.cuh", "shapes.h", "common.cuh"),
+}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
-    for f in ("construct.cuh", "shapes.h", "common.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2404_04895_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel_hash, workload_name, prec):
-    """dram bytes per construct launch from the committed ncu summary, if it
+def traffic_from_profile(kernel, kernel_hash, workload_name, prec):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "construct_dram_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(f"{workload_name}:{prec}")
+    e = d.get(f"{kernel}:{workload_name}:{prec}")
     if not e or e.get("kernel_hash") != kernel_hash:
         return None
     return e.get("dram_bytes_per_launch")
@@ -224,9 +237,9 @@ def run_native(args, w, dist):
     st = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    def timed_run(prec, steps, warmup, profile=True):
+    def timed_run(prec, steps, warmup, lists, profile=True):
         kw = solver_kwargs(dict(w, prec=prec), seed)
-        s = B.Solver(coords, stream=st, **kw)
+        s = B.Solver(coords, stream=st, cand_lists=lists, **kw)
         if profile:
             s.set_profiling(True)
         s.iterate(warmup)
@@ -234,7 +247,7 @@ def run_native(args, w, dist):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         total = 0.0
-        kern = np.zeros(5)
+        kern = np.zeros(len(STEPS))
         for q in range(steps):
             with torch.cuda.stream(st):
                 flush.fill_(q & 0xFF)          # L2 flush, outside the timed region
@@ -250,15 +263,20 @@ def run_native(args, w, dist):
         s.close()
         return total, kern, best
 
-    tuned = {}
-    for prec in ([w["prec"]] if args.no_variants else ["fp32", "bf16", "fp16"]):
-        tuned[prec] = ((0, 0, 0), None) if args.no_autotune else autotune(B, torch, w, coords, prec, seed)
+    lists = not args.no_lists
+    peak, peak_src = peaks()
+    peak_note = "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s"
+    bp = 4 if w["prec"] == "fp32" else 2
+    alg_bytes = m * n * (n - 1) / 2 * bp      # every unvisited M_p entry of every ant-step
+    tuned = None
+    if not lists or not args.no_full_scan:    # full-scan launch shape for this workload (untimed)
+        tuned = ((0, 0, 0), None) if args.no_autotune else autotune(B, torch, w, coords, w["prec"], seed)
     dist.barrier()
     clk = ClockSampler(dist.local)
     torch.cuda.synchronize()
     dist.barrier()
     clk.start()
-    total_ms, kern, best_len = timed_run(w["prec"], args.steps, args.warmup)
+    total_ms, kern, best_len = timed_run(w["prec"], args.steps, args.warmup, lists)
     torch.cuda.synchronize()
     dist.barrier()
     clocks = clk.stop()
@@ -267,23 +285,34 @@ def run_native(args, w, dist):
     ant_steps = m * (n - 1)
     value = ant_steps * dist.world / (ms_per_step / 1e3)
 
-    # roofline of the construction kernel (the dominant one)
-    bp = 4 if w["prec"] == "fp32" else 2
-    construct_ms = kern[1] / args.steps
-    alg_bytes = m * n * (n - 1) / 2 * bp
-    achieved = alg_bytes / (construct_ms / 1e3) / 1e9
-    peak, peak_src = peaks()
-    khash = construct_source_hash()
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
-                "traffic": traffic_from_profile(khash, args.workload, w["prec"]),
+    def full_scan_roofline(construct_ms, shape):
+        achieved = alg_bytes / (construct_ms / 1e3) / 1e9
+        kh = kernel_source_hash("construct_kernel")
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_note,
+                "traffic": traffic_from_profile("construct_kernel", kh, args.workload, w["prec"]),
                 "kernel": "construct_kernel", "algorithmic_bytes_per_launch": alg_bytes,
-                "avg_launch_ms": round(construct_ms, 4), "kernel_source_hash": khash}
-    roofline["construct_shape"] = {"warps_per_ant": tuned[w["prec"]][0][0],
-                                   "chunks_per_lane": tuned[w["prec"]][0][1],
-                                   "mode": ["staged", "direct"][tuned[w["prec"]][0][2]]}
-    kernel_ms = dict(zip(["build_P", "construct", "tour_length", "best", "deposit"],
-                         [round(x / args.steps, 4) for x in kern]))
+                "avg_launch_ms": round(construct_ms, 4), "kernel_source_hash": kh,
+                "construct_shape": {"warps_per_ant": shape[0], "chunks_per_lane": shape[1],
+                                    "mode": ["staged", "direct"][shape[2]] if shape[0] else "default"}}
+
+    construct_ms = kern[2] / args.steps
+    if lists:
+        # the candidate-list kernel decides most steps from a row's top entries
+        # and reads the row only when the list cannot; achieved counts the
+        # algorithmic bytes of a full scan, so frac > 1 is the pruning's effect
+        kh = kernel_source_hash("construct_lean_kernel")
+        achieved = alg_bytes / (construct_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "peak_source": peak_note,
+                    "traffic": traffic_from_profile("construct_lean_kernel", kh, args.workload, w["prec"]),
+                    "kernel": "construct_lean_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+                    "avg_launch_ms": round(construct_ms, 4), "kernel_source_hash": kh,
+                    "note": "exact pruning: achieved = full-scan algorithmic bytes (m*n*(n-1)/2 M_p "
+                            "entries) / launch time; traffic = DRAM bytes the kernel moves (ncu)"}
+    else:
+        roofline = full_scan_roofline(construct_ms, tuned[0])
+    kernel_ms = dict(zip(STEPS, [round(x / args.steps, 4) for x in kern]))
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": dist.world,
@@ -294,15 +323,20 @@ def run_native(args, w, dist):
         "config": {"workload": args.workload, "kind": w["kind"], "n": n, "m": m, "alpha": w["alpha"],
                    "beta": w["beta"], "rho": w["rho"], "Q": w["Q"],
                    "roulette": "adair" if w["adair"] else "ir", "deposit": "deterministic",
-                   "P_dtype": w["prec"], "l2": "flushed between timed steps (512 MiB write)",
+                   "P_dtype": w["prec"], "construction": "candidate lists" if lists else "full scan",
+                   "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU",
                    "iters_per_s": round(1e3 / ms_per_step, 2)},
         "roofline": roofline,
         "kernel_ms": kernel_ms,
-        "gpu_launches": args.steps * 5,
+        "gpu_launches": args.steps * (6 if lists else 5),
         "clocks": clocks,
         "best_len_after_steps": best_len,
     }
+    if lists and not args.no_full_scan and dist.rank == 0:
+        steps_f = min(args.steps, 20)
+        _, kf, _ = timed_run(w["prec"], steps_f, 3, False)
+        out["full_scan_roofline"] = full_scan_roofline(kf[2] / steps_f, tuned[0])
 
     if dist.rank == 0 and not args.no_variants:
         # BF16 / FP16 M_p against fp32 on the same GPU: throughput and best-length gap
@@ -310,19 +344,19 @@ def run_native(args, w, dist):
         gaps = {}
         for prec in ("fp32", "bf16", "fp16"):
             if prec != w["prec"]:
-                t, kv, _ = timed_run(prec, min(args.steps, 30), 3)
+                t, kv, _ = timed_run(prec, min(args.steps, 30), 3, lists)
                 steps_v = min(args.steps, 30)
-                cms = kv[1] / steps_v
+                cms = kv[2] / steps_v
                 bpv = 4 if prec == "fp32" else 2
                 ach = m * n * (n - 1) / 2 * bpv / (cms / 1e3) / 1e9
                 variants[prec] = {"ms_per_step": round(t / steps_v, 4),
                                   "value": round(ant_steps / (t / steps_v / 1e3), 1),
-                                  "construct_ms": round(cms, 4), "construct_GBps": round(ach, 1),
+                                  "construct_ms": round(cms, 4), "construct_alg_GBps": round(ach, 1),
                                   "frac_of_hbm": round(ach / peak, 4)}
             # best length after the workload's full iteration budget, mean over seeds
             lens = []
             for sd in range(args.gap_seeds):
-                s = B.Solver(coords, stream=st, **solver_kwargs(dict(w, prec=prec), sd))
+                s = B.Solver(coords, stream=st, cand_lists=lists, **solver_kwargs(dict(w, prec=prec), sd))
                 s.iterate(w["iters"])
                 lens.append(s.best()[1])
                 s.close()

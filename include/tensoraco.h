@@ -161,10 +161,11 @@ int aco_solver_iteration(aco_solver* s, uint32_t* it);
 /* Kernel timing probes.  When on, the solver records CUDA events around each
  * kernel of every iteration (inside its CUDA graph as well).  After an
  * iteration has been issued, aco_solver_kernel_ms() waits for it and writes
- * the durations in milliseconds of its kernels, in order: build_P, construct,
- * tour_length, best, deposit (evaporation + deposit for the atomic mode). */
+ * the durations in milliseconds of its six steps, in order: build_P,
+ * build_lists (0 without candidate lists), construct, tour_length, best,
+ * deposit (evaporation + deposit for the atomic mode). */
 int aco_solver_set_profiling(aco_solver* s, int on);
-int aco_solver_kernel_ms(aco_solver* s, float* ms5);
+int aco_solver_kernel_ms(aco_solver* s, float* ms6);
 
 /* Choose the construct launch shape (warps, chunks, mode as for
  * aco_op_construct_shape) for this solver: warps = chunks = 0 restores the
@@ -252,11 +253,17 @@ int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, ui
                            int chunks, int mode, void* stream);
 
 /* Candidate lists of M_p, the exact fast path of the construction step: for
- * each row i, lcnt_dev[i] <= 64 entries lists_dev[i*64 + q] = (fp32 bits of
- * the stored value, column) -- every column whose value is above the row's
- * 32nd largest, ties at it in column order -- and lkey_dev[i] bounds the
- * score key (fp32 bits + 1) of every column not listed.  lists_dev: n*64
- * pairs of u32, 8-byte aligned; lcnt_dev, lkey_dev: n entries. */
+ * each row i, lcnt_dev[i] <= ACO_LIST_MAX entries lists_dev[i*ACO_LIST_MAX + q]
+ * = (fp32 bits of the stored value, column), sorted by value (descending,
+ * ties by column) -- every column whose value is above the row's
+ * ACO_LIST_TARGET-th largest value T, then columns equal to T in column order
+ * while room remains (every column when n <= ACO_LIST_MAX) -- and
+ * lkey_dev[i] bounds the score key (fp32 bits + 1) of every column not
+ * listed: T when all columns >= T are listed, T + 1 when ties at T were cut,
+ * 0 when nothing is left out.  lists_dev: n*ACO_LIST_MAX pairs of u32,
+ * 8-byte aligned; lcnt_dev, lkey_dev: n entries. */
+#define ACO_LIST_TARGET 128
+#define ACO_LIST_MAX 256
 int aco_op_build_lists(const void* P_dev, int prec, int n, int ld, void* lists_dev, int* lcnt_dev,
                        uint32_t* lkey_dev, void* stream);
 

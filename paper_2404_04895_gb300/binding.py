@@ -315,9 +315,9 @@ class Solver:
         return self
 
     def kernel_ms(self):
-        """Durations (ms) of the last iteration's kernels: build_P, construct,
-        tour_length, best, deposit."""
-        out = np.zeros(5, dtype=np.float32)
+        """Durations (ms) of the last iteration's steps: build_P, build_lists,
+        construct, tour_length, best, deposit."""
+        out = np.zeros(6, dtype=np.float32)
         call("aco_solver_kernel_ms", self._h, out.ctypes.data)
         return out
 

@@ -137,6 +137,47 @@ __device__ __forceinline__ uint32_t score_key(float bs) {
   return bs >= 0.0f ? __float_as_uint(bs) + 1u : 0u;
 }
 
+// One step's candidate-list rounds (one warp; lists from build_list_row).
+// Row cur's entries are scored 32 at a time in value order, loaded one round
+// ahead; an entry's visited bit is read while its Philox block is computed.
+// After a round, every entry not yet scored has a value <= the round's last
+// one and every unlisted column a score key <= the row's bound, so the step
+// is decided once the best score key exceeds both.  Returns the chosen
+// column, or -1 when the list cannot decide; bs/bj then hold the best
+// unvisited listed candidate (bs < 0: none), a threshold for the full scan.
+__device__ __forceinline__ int list_rounds(const uint2* __restrict__ lists, const int* __restrict__ lcnt,
+                                           const uint32_t* __restrict__ lkey, int cur,
+                                           const uint32_t* __restrict__ svis, uint2 key, uint32_t it, int k,
+                                           int t, float& bs, int& bj) {
+  const int lane = threadIdx.x & 31;
+  const uint2* __restrict__ lrow = lists + (size_t)cur * kListMax;
+  const int lc = __ldg(lcnt + cur);
+  const uint32_t lb = __ldg(lkey + cur);
+  uint2 e = __ldg(lrow + lane);  // rows are allocated whole; slots past lc hold stale data
+  uint2 e_next = __ldg(lrow + 32 + lane);
+#pragma unroll 1
+  for (int r = 0; r < kListMax / 32; ++r) {
+    if (32 * r >= lc) break;
+    const bool valid = 32 * r + lane < lc;
+    const int j = valid ? (int)e.y : 0;
+    const bool unvisited = valid && !((svis[j >> 5] >> (j & 31)) & 1u);
+    if (valid) {
+      const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it), key);
+      const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
+      const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
+      if (unvisited) better(sc, j, bs, bj);
+    }
+    const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
+    uint32_t rest = lb;
+    if (32 * (r + 1) < lc) rest = max(rest, __shfl_sync(ACO_FULL_MASK, e.x, 31) + 1u);
+    if (lk > rest)
+      return (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == lk ? (uint32_t)bj : 0x7FFFFFFFu);
+    e = e_next;
+    if (r + 2 < kListMax / 32 && 32 * (r + 2) < lc) e_next = __ldg(lrow + 32 * (r + 2) + lane);
+  }
+  return -1;
+}
+
 // MODE_STAGED: a step's chunks go global -> shared memory by cp.async (all in
 // flight regardless of registers; suits many chunks per thread).
 // MODE_DIRECT: a step's chunks go straight into registers by predicated 16-byte
@@ -248,33 +289,7 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
     // 0. candidate list of row cur, sorted by value: rounds of 32 entries; after
     //    each round the next unscored entry (or the row's bound) bounds every
     //    column not scored yet
-    if (use_list) {
-      const uint2* __restrict__ lrow = lists + (size_t)cur * kListMax;
-      uint2 e[kListMax / 32];
-#pragma unroll
-      for (int r = 0; r < kListMax / 32; ++r) e[r] = __ldg(lrow + 32 * r + lane);  // allocated rows
-      const int lc = __ldg(lcnt + cur);
-      const uint32_t lb = __ldg(lkey + cur);
-#pragma unroll
-      for (int r = 0; r < kListMax / 32; ++r) {
-        if (32 * r >= lc) break;
-        const bool valid = 32 * r + lane < lc;       // slots past the count hold stale data
-        const int j = valid ? (int)e[r].y : 0;
-        if (valid && !((svis[j >> 5] >> (j & 31)) & 1u)) {
-          const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it), key);
-          const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
-          better(__fmul_rn(uniform01(w), __uint_as_float(e[r].x)), j, bs, bj);
-        }
-        const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
-        uint32_t rest = lb;
-        if (r + 1 < kListMax / 32 && 32 * (r + 1) < lc)
-          rest = max(rest, __shfl_sync(ACO_FULL_MASK, e[r + 1 < kListMax / 32 ? r + 1 : r].x, 0) + 1u);
-        if (lk > rest) {
-          next = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == lk ? (uint32_t)bj : 0x7FFFFFFFu);
-          break;
-        }
-      }
-    }
+    if (use_list) next = list_rounds(lists, lcnt, lkey, cur, svis, key, it, k, t, bs, bj);
 
     if (next < 0) {  // full scan (seeded with the list's best candidate, if any)
 

@@ -3,11 +3,11 @@
 //
 // State is the ant's visited bitmap in shared memory (n bits) and its current
 // city; no per-lane visited registers, so the step stays short and light.
-//   list step   the unvisited entries of row cur's sorted candidate list are
-//               scored in rounds of 32 (one Philox4x32-10 block per entry);
-//               after each round the next unscored entry -- or the row's bound
-//               -- bounds every column not yet scored, and the step is decided
-//               once the best score key exceeds that bound (see build_list_row)
+//   list step   the entries of row cur's sorted candidate list are scored in
+//               rounds of 32 (one Philox4x32-10 block per entry); after each
+//               round the round's last value -- and the row's bound -- bound
+//               every column not yet scored, and the step is decided once the
+//               best score key exceeds them (list_rounds, build_list_row)
 //   full scan   (list undecided) the row's chunks with an unvisited column are
 //               staged in shared memory by cp.async; each 4-column group's raw
 //               maximum is compared with the threshold -- the list's best score,
@@ -82,33 +82,7 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
     };
 
     // ---- list step
-    if (lists) {
-      const uint2* __restrict__ lrow = lists + (size_t)cur * kListMax;
-      uint2 e[kListMax / 32];
-#pragma unroll
-      for (int r = 0; r < kListMax / 32; ++r) e[r] = __ldg(lrow + 32 * r + lane);  // allocated rows
-      const int lc = __ldg(lcnt + cur);
-      const uint32_t lb = __ldg(lkey + cur);
-#pragma unroll
-      for (int r = 0; r < kListMax / 32; ++r) {
-        if (32 * r >= lc) break;
-        const bool valid = 32 * r + lane < lc;  // slots past the count hold stale data
-        const int j = valid ? (int)e[r].y : 0;
-        if (valid && !((svis[j >> 5] >> (j & 31)) & 1u)) {
-          const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it), key);
-          const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
-          better(__fmul_rn(uniform01(w), __uint_as_float(e[r].x)), j, bs, bj);
-        }
-        const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
-        uint32_t rest = lb;
-        if (r + 1 < kListMax / 32 && 32 * (r + 1) < lc)
-          rest = max(rest, __shfl_sync(ACO_FULL_MASK, e[r + 1 < kListMax / 32 ? r + 1 : r].x, 0) + 1u);
-        if (lk > rest) {
-          next = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == lk ? (uint32_t)bj : 0x7FFFFFFFu);
-          break;
-        }
-      }
-    }
+    if (lists) next = list_rounds(lists, lcnt, lkey, cur, svis, key, it, k, t, bs, bj);
 
     // ---- compact full scan
     if (next < 0) {
@@ -150,20 +124,38 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
         }
         thr = __reduce_max_sync(ACO_FULL_MASK, bs >= 0.0f ? __float_as_uint(bs) : 0u);
       }
-      const int thr_key = (int)(thr & ~0xFFFFu);
-      // every other group whose raw maximum reaches the threshold, one per lane per round
-      uint64_t surv[2] = {0ull, 0ull};
-      for (int c = 0; c < kc; ++c)
+      const uint32_t thr_key = thr & ~0xFFFFu;
+      // every group whose raw maximum reaches the threshold and that has an
+      // unvisited column (chunks left unstaged are fully visited, so their
+      // stale shared data never passes the second test)
+      uint64_t surv0 = 0ull, surv1 = 0ull;  // groups 0..63, 64..127 of this lane
+      for (int c = 0; c < kc; ++c) {
+        const int cg = c * 32 + lane;
+        if (cg >= nchunks) break;
+        const uint4 v = srow[c * 32 + lane];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-          const int gi = c * G + g;
-          if (gkey(c, g) >= thr_key) surv[gi >> 6] |= 1ull << (gi & 63);
+          if ((E::group_max_bits(v, g) & ~0xFFFFu) < thr_key) continue;
+          const int j0 = cg * V + 4 * g;
+          if (j0 < n && group_nibble(j0) != 0xFu) {
+            const int gi = c * G + g;
+            if (gi < 64)
+              surv0 |= 1ull << gi;
+            else
+              surv1 |= 1ull << (gi - 64);
+          }
         }
-      while (__any_sync(ACO_FULL_MASK, (surv[0] | surv[1]) != 0ull)) {
-        if (surv[0] | surv[1]) {
-          const int h = surv[0] ? 0 : 1;
-          const int gi = h * 64 + __ffsll((long long)surv[h]) - 1;
-          surv[h] &= surv[h] - 1ull;
+      }
+      while (__any_sync(ACO_FULL_MASK, (surv0 | surv1) != 0ull)) {
+        if (surv0 | surv1) {
+          int gi;
+          if (surv0) {
+            gi = __ffsll((long long)surv0) - 1;
+            surv0 &= surv0 - 1ull;
+          } else {
+            gi = 64 + __ffsll((long long)surv1) - 1;
+            surv1 &= surv1 - 1ull;
+          }
           const int c = gi / G, g = gi - c * G;
           const int j0 = (c * 32 + lane) * V + 4 * g;
           score4(j0, E::group_values(srow[c * 32 + lane], g), group_nibble(j0));

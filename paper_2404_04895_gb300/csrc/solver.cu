@@ -308,7 +308,7 @@ struct aco_solver {
   bool graph_ok;
   bool use_graph;
   bool profiling;
-  cudaEvent_t ev[6];           // probes around the iteration's kernels
+  cudaEvent_t ev[7];           // probes around the iteration's kernels
 
   template <class T>
   T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
@@ -353,29 +353,30 @@ static int enqueue_iteration(aco_solver* s) {
                           p.roulette == ACO_ADAIR ? s->sched : nullptr, s->it_dev, n_sched, p.prec,
                           s->P_f, st);
   if (rc) return rc;
+  probe(1);
   const bool lists = p.cand_lists != 0;
   if (lists) rc = launch_build_lists(s->P_f, p.prec, n, s->ld, s->lists, s->lcnt, s->lkey, st);
   if (rc) return rc;
-  probe(1);
+  probe(2);
   rc = launch_construct(s->P_f, p.prec, n, s->ld, m, make_uint2((uint32_t)p.seed, (uint32_t)(p.seed >> 32)),
                         0u, s->it_dev, s->tours, s->err, s->shape, lists ? s->lists : nullptr, s->lcnt,
                         s->lkey, st);
   if (rc) return rc;
-  probe(2);
+  probe(3);
   const bool det = p.deposit == ACO_DEPOSIT_DET;
   rc = launch_tour_length(s->D, n, s->tours, m, p.Q, s->L, s->c, det ? s->nbr : nullptr, st);
   if (rc) return rc;
-  probe(3);
+  probe(4);
   rc = launch_best(s->L, s->tours, n, m, s->best_tour, s->best_len, s->it_dev, s->c, det ? s->dep : nullptr,
                    s->err, st);
   if (rc) return rc;
-  probe(4);
+  probe(5);
   if (det)
     rc = launch_deposit(s->tau, n, s->ld, s->nbr, s->c, m, p.rho, s->dep, s->err, st);
   else
     rc = launch_deposit_atomic(s->tau, n, s->ld, s->tours, s->c, m, p.rho, st);
   if (rc) return rc;
-  probe(5);
+  probe(6);
   return ACO_OK;
 }
 
@@ -539,7 +540,7 @@ int aco_destroy(aco_solver* s) {
   cudaStreamSynchronize(s->stream);
   drop_graph(s);
   if (s->profiling)
-    for (int q = 0; q < 6; ++q) cudaEventDestroy(s->ev[q]);
+    for (int q = 0; q < 7; ++q) cudaEventDestroy(s->ev[q]);
   if (s->own_ws) cudaFree(s->ws);
   delete s;
   return ACO_OK;
@@ -623,20 +624,20 @@ int aco_solver_set_profiling(aco_solver* s, int on) {
   ACO_CUDA_TRY(cudaStreamSynchronize(s->stream));
   drop_graph(s);
   if (on) {
-    for (int q = 0; q < 6; ++q) ACO_CUDA_TRY(cudaEventCreate(&s->ev[q]));
+    for (int q = 0; q < 7; ++q) ACO_CUDA_TRY(cudaEventCreate(&s->ev[q]));
   } else {
-    for (int q = 0; q < 6; ++q) cudaEventDestroy(s->ev[q]);
+    for (int q = 0; q < 7; ++q) cudaEventDestroy(s->ev[q]);
   }
   s->profiling = on != 0;
   return ACO_OK;
 }
 
-int aco_solver_kernel_ms(aco_solver* s, float* ms5) {
-  if (!s || !ms5) return set_error(ACO_ERR_ARG, "NULL argument");
+int aco_solver_kernel_ms(aco_solver* s, float* ms6) {
+  if (!s || !ms6) return set_error(ACO_ERR_ARG, "NULL argument");
   if (!s->profiling) return set_error(ACO_ERR_STATE, "profiling is off");
   if (s->it == 0) return set_error(ACO_ERR_STATE, "no iteration has run yet");
-  ACO_CUDA_TRY(cudaEventSynchronize(s->ev[5]));
-  for (int q = 0; q < 5; ++q) ACO_CUDA_TRY(cudaEventElapsedTime(&ms5[q], s->ev[q], s->ev[q + 1]));
+  ACO_CUDA_TRY(cudaEventSynchronize(s->ev[6]));
+  for (int q = 0; q < 6; ++q) ACO_CUDA_TRY(cudaEventElapsedTime(&ms6[q], s->ev[q], s->ev[q + 1]));
   return ACO_OK;
 }
 

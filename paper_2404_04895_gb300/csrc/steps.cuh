@@ -447,8 +447,8 @@ namespace aco {
 // All threads of the CTA (blockDim.x <= 256); scratch: kListScratchWords
 // shared words.
 // ---------------------------------------------------------------------------
-constexpr int kListTarget = 64;
-constexpr int kListMax = 128;
+constexpr int kListTarget = ACO_LIST_TARGET;
+constexpr int kListMax = ACO_LIST_MAX;
 constexpr int kListScratchWords = 256 + 8 + 2 * kListMax * 2;
 
 template <int PREC>

@@ -25,7 +25,7 @@ def _keys(Pv, bits, prec):
     return Pv.astype(np.float32).view(np.uint32)
 
 
-LMAX, LTARGET = 128, 64
+LMAX, LTARGET = 256, 128
 
 
 def _build(Pd, prec, n, ld):
@@ -50,7 +50,7 @@ def _P(orc, n, seed, prec, ties=False):
 
 
 @pytest.mark.parametrize("prec", [B.FP32, B.BF16, B.FP16])
-@pytest.mark.parametrize("n,ties", [(40, False), (128, False), (129, False), (500, False), (500, True),
+@pytest.mark.parametrize("n,ties", [(40, False), (256, False), (257, False), (500, False), (500, True),
                                     (2001, False)])
 def test_list_invariants(orc, prec, n, ties):
     Pv, bits = _P(orc, n, 7 + n, prec, ties)
