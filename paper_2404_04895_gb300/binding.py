@@ -168,12 +168,28 @@ def op_construct(P, prec, n, ld, m, seed, it, tours, err=None, shape=None, strea
              shape[0], shape[1], shape[2], stream_ptr(stream))
 
 
+LIST_TARGET, LIST_MAX = 128, 256   # ACO_LIST_TARGET, ACO_LIST_MAX of tensoraco.h
+
+
+def _check_lists(n, lists, lcnt, lkey):
+    """Refuse list buffers smaller than the library writes or reads."""
+    for name, t, need in (("lists", lists, n * LIST_MAX * 8), ("lcnt", lcnt, n * 4), ("lkey", lkey, n * 4)):
+        if t is None or isinstance(t, int):
+            continue
+        size = t.numel() * t.element_size() if hasattr(t, "element_size") else t.nbytes
+        if size < need:
+            raise ValueError(f"{name} holds {size} bytes; n={n} needs {need}")
+
+
 def op_build_lists(P, prec, n, ld, lists, lcnt, lkey, stream=None):
+    _check_lists(n, lists, lcnt, lkey)
     call("aco_op_build_lists", ptr(P), prec, n, ld, ptr(lists), ptr(lcnt), ptr(lkey), stream_ptr(stream))
 
 
 def op_construct_ex(P, prec, n, ld, m, seed, it, tours, lists=None, lcnt=None, lkey=None, err=None,
                     shape=(0, 0, 0), stream=None):
+    if lists is not None:
+        _check_lists(n, lists, lcnt, lkey)
     call("aco_op_construct_ex", ptr(P), prec, n, ld, m, seed, it, ptr(tours), ptr(err), ptr(lists),
          ptr(lcnt), ptr(lkey), shape[0], shape[1], shape[2], stream_ptr(stream))
 

@@ -137,43 +137,74 @@ __device__ __forceinline__ uint32_t score_key(float bs) {
   return bs >= 0.0f ? __float_as_uint(bs) + 1u : 0u;
 }
 
-// One step's candidate-list rounds (one warp; lists from build_list_row).
-// Row cur's entries are scored 32 at a time in value order, loaded one round
-// ahead; an entry's visited bit is read while its Philox block is computed.
-// After a round, every entry not yet scored has a value <= the round's last
-// one and every unlisted column a score key <= the row's bound, so the step
-// is decided once the best score key exceeds both.  Returns the chosen
-// column, or -1 when the list cannot decide; bs/bj then hold the best
-// unvisited listed candidate (bs < 0: none), a threshold for the full scan.
-__device__ __forceinline__ int list_rounds(const uint2* __restrict__ lists, const int* __restrict__ lcnt,
-                                           const uint32_t* __restrict__ lkey, int cur,
-                                           const uint32_t* __restrict__ svis, uint2 key, uint32_t it, int k,
-                                           int t, float& bs, int& bj) {
+// The first two rounds of row `row`'s candidate list and its bound, as loaded
+// by one warp (rows are allocated and written whole: slots past the count
+// hold (0, kListPad)).
+struct ListRow {
+  uint2 e, e_next;
+  uint32_t lb;
+  int row;
+};
+
+__device__ __forceinline__ ListRow load_list_row(const uint2* __restrict__ lists,
+                                                 const uint32_t* __restrict__ lkey, int row) {
   const int lane = threadIdx.x & 31;
-  const uint2* __restrict__ lrow = lists + (size_t)cur * kListMax;
-  const int lc = __ldg(lcnt + cur);
-  const uint32_t lb = __ldg(lkey + cur);
-  uint2 e = __ldg(lrow + lane);  // rows are allocated whole; slots past lc hold stale data
-  uint2 e_next = __ldg(lrow + 32 + lane);
+  const uint2* __restrict__ lrow = lists + (size_t)row * kListMax;
+  ListRow L;
+  L.e = __ldg(lrow + lane);
+  L.e_next = __ldg(lrow + 32 + lane);
+  L.lb = __ldg(lkey + row);
+  L.row = row;
+  return L;
+}
+
+// One step's candidate-list rounds (one warp; lists from build_list_row) on
+// row L.row, whose first rounds L holds.  Entries are scored 32 at a time in
+// value order, each round loaded one round ahead; an entry's visited bit is
+// read while its Philox block is computed.  After a round, every entry not
+// yet scored has a value <= the round's last one and every unlisted column a
+// score key <= the row's bound, so the step is decided once the best score
+// key exceeds both.  Returns the chosen column, or -1 when the list cannot
+// decide; bs/bj then hold the best unvisited listed candidate (bs < 0: none),
+// a threshold for the full scan.  SPEC: in the first round, also start
+// loading the list of the first unvisited entry -- the next city most of the
+// time -- into *spec (spec->row = -1 when there is none).
+template <bool SPEC>
+__device__ __forceinline__ int list_rounds(const uint2* __restrict__ lists, const uint32_t* __restrict__ lkey,
+                                           const ListRow& L, ListRow* spec, const uint32_t* __restrict__ svis,
+                                           uint2 key, uint32_t it, int k, int t, float& bs, int& bj) {
+  const int lane = threadIdx.x & 31;
+  const uint2* __restrict__ lrow = lists + (size_t)L.row * kListMax;
+  uint2 e = L.e, e_next = L.e_next;
+  // Rounds are written branch-free up to the decision so that the compiler
+  // can interleave the Philox chain with the visited test and the speculative
+  // loads; a padded slot scores column 0 and is then ignored.
 #pragma unroll 1
   for (int r = 0; r < kListMax / 32; ++r) {
-    if (32 * r >= lc) break;
-    const bool valid = 32 * r + lane < lc;
+    const bool valid = e.y != kListPad;
     const int j = valid ? (int)e.y : 0;
     const bool unvisited = valid && !((svis[j >> 5] >> (j & 31)) & 1u);
-    if (valid) {
-      const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it), key);
-      const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
-      const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
-      if (unvisited) better(sc, j, bs, bj);
+    const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it), key);
+    const unsigned vm = __ballot_sync(ACO_FULL_MASK, valid);
+    if (SPEC && r == 0) {
+      const unsigned un = __ballot_sync(ACO_FULL_MASK, unvisited);
+      const int sj = __shfl_sync(ACO_FULL_MASK, j, un ? __ffs(un) - 1 : 0);
+      *spec = load_list_row(lists, lkey, sj);  // harmless when there is no candidate
+      if (!un) spec->row = -1;
     }
+    // every entry after this round has a value <= this round's last one
+    const bool more = (vm >> 31) != 0u && r + 1 < kListMax / 32;
+    uint32_t rest = L.lb;
+    if (more) rest = max(rest, __shfl_sync(ACO_FULL_MASK, e.x, 31) + 1u);
+    const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
+    const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
+    if (unvisited) better(sc, j, bs, bj);
     const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
-    uint32_t rest = lb;
-    if (32 * (r + 1) < lc) rest = max(rest, __shfl_sync(ACO_FULL_MASK, e.x, 31) + 1u);
     if (lk > rest)
       return (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == lk ? (uint32_t)bj : 0x7FFFFFFFu);
+    if (!more) break;
     e = e_next;
-    if (r + 2 < kListMax / 32 && 32 * (r + 2) < lc) e_next = __ldg(lrow + 32 * (r + 2) + lane);
+    if (r + 2 < kListMax / 32) e_next = __ldg(lrow + 32 * (r + 2) + lane);
   }
   return -1;
 }
@@ -289,7 +320,10 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
     // 0. candidate list of row cur, sorted by value: rounds of 32 entries; after
     //    each round the next unscored entry (or the row's bound) bounds every
     //    column not scored yet
-    if (use_list) next = list_rounds(lists, lcnt, lkey, cur, svis, key, it, k, t, bs, bj);
+    if (use_list) {
+      const ListRow L = load_list_row(lists, lkey, cur);
+      next = list_rounds<false>(lists, lkey, L, nullptr, svis, key, it, k, t, bs, bj);
+    }
 
     if (next < 0) {  // full scan (seeded with the list's best candidate, if any)
 

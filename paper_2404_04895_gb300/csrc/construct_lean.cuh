@@ -68,6 +68,9 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
   }
   __syncwarp();
 
+  ListRow lr, spec;
+  lr.row = spec.row = -1;
+  if (lists) lr = load_list_row(lists, lkey, cur);
   for (int t = 1; t < n; ++t) {
     const char* __restrict__ row = P + (size_t)cur * row_bytes;
     float bs = -1.0f;
@@ -82,7 +85,7 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
     };
 
     // ---- list step
-    if (lists) next = list_rounds(lists, lcnt, lkey, cur, svis, key, it, k, t, bs, bj);
+    if (lists) next = list_rounds<true>(lists, lkey, lr, &spec, svis, key, it, k, t, bs, bj);
 
     // ---- compact full scan
     if (next < 0) {
@@ -175,6 +178,13 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
     }
     __syncwarp();
     cur = next;
+    // the next row's list: usually already in flight from the speculation
+    if (lists && t + 1 < n) {
+      if (spec.row == next)
+        lr = spec;
+      else
+        lr = load_list_row(lists, lkey, next);
+    }
   }
 }
 

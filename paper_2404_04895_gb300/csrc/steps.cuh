@@ -444,12 +444,14 @@ namespace aco {
 // score key <= key(entry r) + 1.  A step is decided by the list when its best
 // score over the entries scored so far exceeds the bound of everything else:
 // no other column can then reach (or tie) that score.
-// All threads of the CTA (blockDim.x <= 256); scratch: kListScratchWords
-// shared words.
+// Slots past the count are written as (0, kListPad), so a reader can tell a
+// listed entry from its own slot.  All threads of the CTA (blockDim.x <= 256);
+// scratch: kListScratchWords shared words.
 // ---------------------------------------------------------------------------
 constexpr int kListTarget = ACO_LIST_TARGET;
 constexpr int kListMax = ACO_LIST_MAX;
 constexpr int kListScratchWords = 256 + 8 + 2 * kListMax * 2;
+constexpr uint32_t kListPad = 0xFFFFFFFFu;  // column of the slots past the count
 
 template <int PREC>
 __device__ __forceinline__ uint32_t p_key(const void* __restrict__ row, int j) {
@@ -500,9 +502,9 @@ __device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, i
         __syncthreads();
       }
     }
-    for (int q = tid; q < n; q += nt) {
+    for (int q = tid; q < kListMax; q += nt) {
       const unsigned long long v = sk[q];
-      list[q] = make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v);
+      list[q] = q < n ? make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v) : make_uint2(0u, kListPad);
     }
     __syncthreads();
     return;
@@ -633,9 +635,9 @@ __device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, i
       __syncthreads();
     }
   }
-  for (int q = tid; q < cnt; q += nt) {
+  for (int q = tid; q < kListMax; q += nt) {
     const unsigned long long v = sk[q];
-    list[q] = make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v);
+    list[q] = q < cnt ? make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v) : make_uint2(0u, kListPad);
   }
   __syncthreads();
 }

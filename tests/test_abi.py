@@ -63,3 +63,19 @@ def test_gamma_schedule_matches_oracle(lib, orc):
             g = lib.aco_gamma(it, T, 1.5, 0.5)
             assert g == orc.gamma(it, T, 1.5, 0.5)
             assert lib.aco_inv_gamma(g) == orc.inv_gamma(g)
+
+
+def test_list_sizes_match_header_and_are_enforced():
+    import re
+    import numpy as np
+    from paper_2404_04895_gb300 import binding as B
+    text = open(os.path.join(ROOT, "include", "tensoraco.h")).read()
+    assert int(re.search(r"#define ACO_LIST_MAX (\d+)", text).group(1)) == B.LIST_MAX
+    assert int(re.search(r"#define ACO_LIST_TARGET (\d+)", text).group(1)) == B.LIST_TARGET
+    n = 50
+    ok = (np.zeros((n, B.LIST_MAX, 2), np.int32), np.zeros(n, np.int32), np.zeros(n, np.uint32))
+    B._check_lists(n, *ok)
+    with pytest.raises(ValueError):
+        B._check_lists(n, np.zeros((n, B.LIST_MAX // 2, 2), np.int32), ok[1], ok[2])
+    with pytest.raises(ValueError):
+        B._check_lists(n, ok[0], np.zeros(n - 1, np.int32), ok[2])

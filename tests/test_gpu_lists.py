@@ -66,6 +66,8 @@ def test_list_invariants(orc, prec, n, ties):
         vals = ent[:, 0].view(np.uint32).astype(np.int64)
         assert len(set(cols.tolist())) == c
         assert np.array_equal(ent[:, 0].view(np.uint32), row[cols])      # stored values
+        pad = L[i, c:].view(np.uint32)                                   # slots past the count
+        assert np.all(pad[:, 0] == 0) and np.all(pad[:, 1] == 0xFFFFFFFF)
         # sorted by value descending, ties by column ascending
         assert all((vals[q] > vals[q + 1]) or (vals[q] == vals[q + 1] and cols[q] < cols[q + 1])
                    for q in range(c - 1))
