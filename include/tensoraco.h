@@ -262,8 +262,8 @@ int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, ui
  * listed: T when all columns >= T are listed, T + 1 when ties at T were cut,
  * 0 when nothing is left out.  lists_dev: n*ACO_LIST_MAX pairs of u32,
  * 8-byte aligned; lcnt_dev, lkey_dev: n entries. */
-#define ACO_LIST_TARGET 128
-#define ACO_LIST_MAX 256
+#define ACO_LIST_TARGET 256
+#define ACO_LIST_MAX 512
 int aco_op_build_lists(const void* P_dev, int prec, int n, int ld, void* lists_dev, int* lcnt_dev,
                        uint32_t* lkey_dev, void* stream);
 

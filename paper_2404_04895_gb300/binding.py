@@ -168,7 +168,7 @@ def op_construct(P, prec, n, ld, m, seed, it, tours, err=None, shape=None, strea
              shape[0], shape[1], shape[2], stream_ptr(stream))
 
 
-LIST_TARGET, LIST_MAX = 128, 256   # ACO_LIST_TARGET, ACO_LIST_MAX of tensoraco.h
+LIST_TARGET, LIST_MAX = 256, 512   # ACO_LIST_TARGET, ACO_LIST_MAX of tensoraco.h
 
 
 def _check_lists(n, lists, lcnt, lkey):

@@ -8,11 +8,11 @@
 //               round the round's last value -- and the row's bound -- bound
 //               every column not yet scored, and the step is decided once the
 //               best score key exceeds them (list_rounds, build_list_row)
-//   full scan   (list undecided) the row's chunks with an unvisited column are
-//               staged in shared memory by cp.async; each 4-column group's raw
-//               maximum is compared with the threshold -- the list's best score,
-//               else the warp's best exact score of each lane's largest group --
-//               and only groups reaching it are scored exactly.
+//   full scan   (list undecided) the row is staged in shared memory by
+//               cp.async; each lane walks its 4-column groups against a
+//               threshold -- the warp's best listed score, raised by the lane's
+//               own best score so far -- and scores exactly only the unvisited,
+//               unlisted columns whose values reach it.
 // Either way the chosen city is argmax over unvisited j of fl32(r_j * p_j),
 // lowest j on ties, exactly as a plain scan of every candidate chooses.
 #pragma once
@@ -44,7 +44,6 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
   using E = Elem<PREC>;
   constexpr int V = E::V;
   constexpr int G = V / 4;
-  constexpr uint32_t VMASK = (1u << V) - 1u;
   const int lane = threadIdx.x & 31;
   const char* __restrict__ P = static_cast<const char*>(Pv);
   const size_t row_bytes = (size_t)ld * E::BYTES;
@@ -92,76 +91,34 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
       const uint4* __restrict__ row4 = reinterpret_cast<const uint4*>(row);
       for (int c = 0; c < kc; ++c) {
         const int cg = c * 32 + lane;
-        bool need = false;
-        if (cg < nchunks) {
-          const int j0 = cg * V;
-          uint32_t bits = (svis[j0 >> 5] >> (j0 & 31)) & VMASK;
-          if (j0 + V > n) bits |= (VMASK << (n - j0)) & VMASK;
-          need = bits != VMASK;
-        }
-        cp_async16_pred(srow + c * 32 + lane, row4 + cg, need);
+        cp_async16_pred(srow + c * 32 + lane, row4 + cg, cg < nchunks);
       }
       cp_async_wait_all();  // this lane's copies only: it reads nothing else
-      // group keys: raw maximum packed with the group index (16 bits); -1 when empty
-      auto gkey = [&](int c, int g) -> int {
-        const int cg = c * 32 + lane;
-        if (cg >= nchunks) return -1;
-        const int j0 = cg * V + 4 * g;
-        if (j0 >= n || group_nibble(j0) == 0xFu) return -1;
-        const uint32_t mb = E::group_max_bits(srow[c * 32 + lane], g);
-        return (int)((mb & ~0xFFFFu) | (uint32_t)(0xFFFF - (c * G + g)));
-      };
-      uint32_t thr = bs >= 0.0f ? __float_as_uint(bs) : 0u;
-      thr = __reduce_max_sync(ACO_FULL_MASK, thr);  // the list's best score, warp-wide
-      if (thr == 0u) {
-        // no list candidate: score each lane's largest group for a threshold
-        int top = -1;
-        for (int c = 0; c < kc; ++c)
-#pragma unroll
-          for (int g = 0; g < G; ++g) top = max(top, gkey(c, g));
-        if (top >= 0) {
-          const int gi = 0xFFFF - (top & 0xFFFF);
-          const int c = gi / G, g = gi - c * G;
-          const int j0 = (c * 32 + lane) * V + 4 * g;
-          score4(j0, E::group_values(srow[c * 32 + lane], g), group_nibble(j0));
-        }
-        thr = __reduce_max_sync(ACO_FULL_MASK, bs >= 0.0f ? __float_as_uint(bs) : 0u);
-      }
-      const uint32_t thr_key = thr & ~0xFFFFu;
-      // every group whose raw maximum reaches the threshold and that has an
-      // unvisited column (chunks left unstaged are fully visited, so their
-      // stale shared data never passes the second test)
-      uint64_t surv0 = 0ull, surv1 = 0ull;  // groups 0..63, 64..127 of this lane
-      for (int c = 0; c < kc; ++c) {
-        const int cg = c * 32 + lane;
-        if (cg >= nchunks) break;
+      // Each lane walks its groups in column order against a threshold: the
+      // warp's best listed score, raised by the lane's own best score so far.
+      // A column whose value is below it cannot win or tie (a score never
+      // exceeds its value), and a listed column -- value bits above the row's
+      // bound - 1 -- was scored by the list rounds already, all of which ran.
+      // Any other unvisited column is scored exactly at once.
+      const uint32_t thr_warp = __reduce_max_sync(ACO_FULL_MASK, bs >= 0.0f ? __float_as_uint(bs) : 0u);
+      const uint32_t hi = (lists && lr.lb) ? lr.lb - 1u : 0xFFFFFFFFu;
+      const int nown = (nchunks - lane + 31) >> 5;  // chunks of this lane
+#pragma unroll 4
+      for (int c = 0; c < nown; ++c) {
         const uint4 v = srow[c * 32 + lane];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-          if ((E::group_max_bits(v, g) & ~0xFFFFu) < thr_key) continue;
-          const int j0 = cg * V + 4 * g;
-          if (j0 < n && group_nibble(j0) != 0xFu) {
-            const int gi = c * G + g;
-            if (gi < 64)
-              surv0 |= 1ull << gi;
-            else
-              surv1 |= 1ull << (gi - 64);
-          }
-        }
-      }
-      while (__any_sync(ACO_FULL_MASK, (surv0 | surv1) != 0ull)) {
-        if (surv0 | surv1) {
-          int gi;
-          if (surv0) {
-            gi = __ffsll((long long)surv0) - 1;
-            surv0 &= surv0 - 1ull;
-          } else {
-            gi = 64 + __ffsll((long long)surv1) - 1;
-            surv1 &= surv1 - 1ull;
-          }
-          const int c = gi / G, g = gi - c * G;
+          const uint32_t thr = max(thr_warp, bs >= 0.0f ? __float_as_uint(bs) : 0u);
+          if (E::group_max_bits(v, g) < thr) continue;
           const int j0 = (c * 32 + lane) * V + 4 * g;
-          score4(j0, E::group_values(srow[c * 32 + lane], g), group_nibble(j0));
+          if (j0 >= n) continue;
+          const float4 p = E::group_values(v, g);
+          auto out = [&](float x) -> uint32_t {
+            const uint32_t b = __float_as_uint(x);
+            return (b < thr || b > hi) ? 1u : 0u;
+          };
+          const uint32_t skip = group_nibble(j0) | out(p.x) | (out(p.y) << 1) | (out(p.z) << 2) | (out(p.w) << 3);
+          if (skip != 0xFu) score4(j0, p, skip);
         }
       }
       const uint32_t wkey = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));

@@ -461,183 +461,189 @@ __device__ __forceinline__ uint32_t p_key(const void* __restrict__ row, int j) {
   return __float_as_uint(__half2float(__ushort_as_half((unsigned short)h)));
 }
 
+// Keys (fp32 bit patterns) of the KV columns of 16-byte chunk q of a row.
 template <int PREC>
-__device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, int n,
-                                               uint2* __restrict__ list, int* __restrict__ cnt_out,
-                                               uint32_t* __restrict__ bkey_out,
-                                               uint32_t* scratch) {
-  uint32_t* hist = scratch;             // [256]
-  uint32_t* sh = scratch + 256;         // [0] prefix, [1] need, [2] gt count, [3] eq count
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (n <= kListMax) {  // every column listed, bound 0; sorted below
-    for (int j = tid; j < n; j += nt) list[j] = make_uint2(p_key<PREC>(P_row, j), (uint32_t)j);
-    if (tid == 0) {
-      *cnt_out = n;
-      *bkey_out = 0u;
-    }
-    __syncthreads();
-    unsigned long long* sk = reinterpret_cast<unsigned long long*>(scratch + 256 + 8);
-    for (int q = tid; q < kListMax; q += nt) {
-      unsigned long long v = 0ull;
-      if (q < n) {
-        const uint2 e = list[q];
-        v = ((unsigned long long)e.x << 32) | (unsigned long long)(0xFFFFFFFFu - e.y);
-      }
-      sk[q] = v;
-    }
-    __syncthreads();
-    for (int size = 2; size <= kListMax; size <<= 1) {
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int q = tid; q < kListMax; q += nt) {
-          const int partner = q ^ stride;
-          if (partner > q) {
-            const bool desc = (q & size) == 0;
-            const unsigned long long a = sk[q], b = sk[partner];
-            if (desc ? (a < b) : (a > b)) {
-              sk[q] = b;
-              sk[partner] = a;
-            }
-          }
+struct RowKeys {
+  static constexpr int KV = PREC == ACO_FP32 ? 4 : 8;
+  uint32_t k[KV];
+  __device__ __forceinline__ void load(const void* __restrict__ row, int q) {
+    const uint4 d = __ldg(static_cast<const uint4*>(row) + q);
+    if (PREC == ACO_FP32) {
+      k[0] = d.x;
+      k[1] = d.y;
+      k[2] = d.z;
+      k[3] = d.w;
+    } else {
+      const uint32_t w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (PREC == ACO_BF16) {
+          k[2 * i] = w[i] << 16;
+          k[2 * i + 1] = w[i] & 0xFFFF0000u;
+        } else {
+          k[2 * i] = __float_as_uint(__half2float(__ushort_as_half((unsigned short)(w[i] & 0xFFFFu))));
+          k[2 * i + 1] = __float_as_uint(__half2float(__ushort_as_half((unsigned short)(w[i] >> 16))));
         }
-        __syncthreads();
       }
     }
-    for (int q = tid; q < kListMax; q += nt) {
-      const unsigned long long v = sk[q];
-      list[q] = q < n ? make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v) : make_uint2(0u, kListPad);
-    }
-    __syncthreads();
-    return;
   }
-  // 1. radix select of the kListTarget-th largest key T
-  if (tid == 0) {
-    sh[0] = 0u;
-    sh[1] = kListTarget;
-  }
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int b = tid; b < 256; b += nt) hist[b] = 0u;
-    __syncthreads();
-    const uint32_t prefix = sh[0];
-    const uint32_t hi_mask = shift == 24 ? 0u : (0xFFFFFFFFu << (shift + 8));
-    for (int j = tid; j < n; j += nt) {
-      const uint32_t key = p_key<PREC>(P_row, j);
-      if ((key & hi_mask) == prefix) atomicAdd(&hist[(key >> shift) & 0xFFu], 1u);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t need = sh[1], cum = 0u;
-      int digit = 0;
-      for (int b = 255; b >= 0; --b) {
-        if (cum + hist[b] >= need) {
-          digit = b;
-          break;
-        }
-        cum += hist[b];
-      }
-      sh[0] = prefix | ((uint32_t)digit << shift);
-      sh[1] = need - cum;
-    }
-    __syncthreads();
-  }
-  const uint32_t T = sh[0];
-  // 2. counts above and at T
-  if (tid == 0) {
-    sh[2] = 0u;
-    sh[3] = 0u;
-  }
-  __syncthreads();
-  uint32_t gt = 0, eq = 0;
-  for (int j = tid; j < n; j += nt) {
-    const uint32_t key = p_key<PREC>(P_row, j);
-    gt += key > T;
-    eq += key == T;
-  }
-  atomicAdd(&sh[2], gt);
-  atomicAdd(&sh[3], eq);
-  __syncthreads();
-  const uint32_t n_gt = sh[2], n_eq = sh[3];
-  const bool all_ties = n_gt + n_eq <= (uint32_t)kListMax;
-  const uint32_t eq_take = all_ties ? n_eq : (uint32_t)kListMax - n_gt;
-  // 3. compaction in column order: thread tid owns columns [tid*span, (tid+1)*span)
-  const int span = (n + nt - 1) / nt;
-  const int j0 = tid * span, j1 = min(n, j0 + span);
-  uint32_t my_gt = 0, my_eq = 0;
-  for (int j = j0; j < j1; ++j) {
-    const uint32_t key = p_key<PREC>(P_row, j);
-    my_gt += key > T;
-    my_eq += key == T;
-  }
-  // exclusive scans over threads of the two counts (warp shuffles, then warp totals)
-  const int lane = tid & 31, wid = tid >> 5;
-  uint32_t inc_gt = my_gt, inc_eq = my_eq;
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t vg = __shfl_up_sync(ACO_FULL_MASK, inc_gt, off);
-    const uint32_t ve = __shfl_up_sync(ACO_FULL_MASK, inc_eq, off);
-    if (lane >= off) {
-      inc_gt += vg;
-      inc_eq += ve;
-    }
-  }
-  __syncthreads();
-  if (lane == 31) {  // warp totals (hist is free again)
-    hist[wid] = inc_gt;
-    hist[32 + wid] = inc_eq;
-  }
-  __syncthreads();
-  uint32_t before_gt = inc_gt - my_gt, before_eq = inc_eq - my_eq;
-  for (int w = 0; w < wid; ++w) {
-    before_gt += hist[w];
-    before_eq += hist[32 + w];
-  }
-  // listed: all gt; eq in column order until eq_take
-  uint32_t pos = before_gt + min(before_eq, eq_take);
-  uint32_t eq_seen = before_eq;
-  for (int j = j0; j < j1; ++j) {
-    const uint32_t key = p_key<PREC>(P_row, j);
-    if (key > T) {
-      list[pos++] = make_uint2(key, (uint32_t)j);
-    } else if (key == T) {
-      if (eq_seen < eq_take) list[pos++] = make_uint2(key, (uint32_t)j);
-      ++eq_seen;
-    }
-  }
-  const int cnt = (int)(n_gt + eq_take);
-  if (tid == 0) {
-    *cnt_out = cnt;
-    *bkey_out = all_ties ? T : T + 1u;
-  }
-  // 4. sort the list by key, descending (ties: lower column first): bitonic
-  //    sort of kListMax 64-bit composite keys in shared memory
-  __syncthreads();
-  unsigned long long* sk = reinterpret_cast<unsigned long long*>(scratch + 256 + 8);
-  for (int q = tid; q < kListMax; q += nt) {
-    unsigned long long v = 0ull;  // padding sorts last
-    if (q < cnt) {
-      const uint2 e = list[q];
-      v = ((unsigned long long)e.x << 32) | (unsigned long long)(0xFFFFFFFFu - e.y);
-    }
-    sk[q] = v;
-  }
-  __syncthreads();
-  for (int size = 2; size <= kListMax; size <<= 1) {
+};
+
+// Bitonic sort, descending, of the first S (a power of two, <= 2 * blockDim.x)
+// 64-bit keys of sk; all threads of the CTA.
+__device__ __forceinline__ void bitonic_desc(unsigned long long* sk, int S) {
+  const int tid = threadIdx.x;
+  for (int size = 2; size <= S; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int q = tid; q < kListMax; q += nt) {
-        const int partner = q ^ stride;
-        if (partner > q) {
-          const bool desc = (q & size) == 0;
-          const unsigned long long a = sk[q], b = sk[partner];
-          if (desc ? (a < b) : (a > b)) {
-            sk[q] = b;
-            sk[partner] = a;
-          }
+      if (tid < S / 2) {
+        const int i = 2 * stride * (tid / stride) + (tid % stride);
+        const int partner = i + stride;
+        const bool desc = (i & size) == 0;
+        const unsigned long long a = sk[i], b = sk[partner];
+        if (desc ? (a < b) : (a > b)) {
+          sk[i] = b;
+          sk[partner] = a;
         }
       }
       __syncthreads();
     }
   }
+}
+
+// composite sort key: value bits high, complemented column low (ties: lower column first)
+__device__ __forceinline__ unsigned long long list_sort_key(uint32_t key, int j) {
+  return ((unsigned long long)key << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)j);
+}
+
+template <int PREC>
+__device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, int n,
+                                               uint2* __restrict__ list, int* __restrict__ cnt_out,
+                                               uint32_t* __restrict__ bkey_out,
+                                               uint32_t* scratch) {
+  using RK = RowKeys<PREC>;
+  constexpr int KV = RK::KV;
+  uint32_t* hist = scratch;                 // [256]
+  uint32_t* sh = scratch + 256;             // [0] prefix [1] need [2] above [3] count [4] eq
+  unsigned long long* sk = reinterpret_cast<unsigned long long*>(scratch + 256 + 8);  // [kListMax]
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  const int nq = (n + KV - 1) / KV;  // 16-byte chunks (rows are padded to a multiple of 8)
+  int S = 2;
+
+  if (n <= kListMax) {  // every column listed, bound 0
+    while (S < n) S <<= 1;
+    for (int q = tid; q < S; q += nt) sk[q] = q < n ? list_sort_key(p_key<PREC>(P_row, q), q) : 0ull;
+    if (tid == 0) {
+      *cnt_out = n;
+      *bkey_out = 0u;
+    }
+    __syncthreads();
+  } else {
+    // 1. radix select of the kListTarget-th largest key T, 8 bits per pass from
+    //    the top; keys above the chosen digit of a pass are above T, so their
+    //    counts add up to the number of keys > T
+    uint32_t prefix = 0u, need = kListTarget, above = 0u, n_eq = 0u;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      for (int b = tid; b < 256; b += nt) hist[b] = 0u;
+      __syncthreads();
+      const uint32_t hi_mask = shift == 24 ? 0u : (0xFFFFFFFFu << (shift + 8));
+      for (int q = tid; q < nq; q += nt) {
+        RK r;
+        r.load(P_row, q);
+#pragma unroll
+        for (int i = 0; i < KV; ++i)
+          if (q < nq && q * KV + i < n && (r.k[i] & hi_mask) == prefix) atomicAdd(hist + ((r.k[i] >> shift) & 0xFFu), 1u);
+      }
+      __syncthreads();
+      if (wid == 0) {
+        // lane l holds bins 255-8l .. 248-8l (descending); exclusive prefix of
+        // the lane sums from the top, then the lane whose run crosses `need`
+        uint32_t h[8], sum = 0u;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          h[i] = hist[255 - 8 * lane - i];
+          sum += h[i];
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const uint32_t v = __shfl_up_sync(ACO_FULL_MASK, inc, off);
+          if (lane >= off) inc += v;
+        }
+        uint32_t cum = inc - sum;
+        if (cum < need && inc >= need) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (cum + h[i] >= need) {
+              sh[0] = prefix | ((uint32_t)(255 - 8 * lane - i) << shift);
+              sh[1] = need - cum;
+              sh[2] = cum;
+              sh[4] = h[i];
+              break;
+            }
+            cum += h[i];
+          }
+        }
+      }
+      __syncthreads();
+      prefix = sh[0];
+      need = sh[1];
+      above += sh[2];
+      n_eq = sh[4];
+      __syncthreads();  // sh is rewritten by the next pass
+    }
+    const uint32_t T = prefix;
+    const uint32_t n_gt = above;
+    const bool all_ties = n_gt + n_eq <= (uint32_t)kListMax;
+    const uint32_t eq_take = all_ties ? n_eq : (uint32_t)kListMax - n_gt;
+    const int cnt = (int)(n_gt + eq_take);
+    // 2. compaction into sk in any order (the sort restores it), except that
+    //    when ties at T are cut the kept ones are the lowest columns
+    if (tid == 0) sh[3] = 0u;
+    __syncthreads();
+    for (int q = tid; q < nq; q += nt) {
+      RK r;
+      r.load(P_row, q);
+#pragma unroll
+      for (int i = 0; i < KV; ++i) {
+        const int j = q * KV + i;
+        if (j < n && (r.k[i] > T || (all_ties && r.k[i] == T))) sk[atomicAdd(sh + 3, 1u)] = list_sort_key(r.k[i], j);
+      }
+    }
+    if (!all_ties) {
+      // the first eq_take columns equal to T, in column order: each thread
+      // takes a contiguous span of columns
+      const int span = (n + nt - 1) / nt;
+      const int j0 = tid * span, j1 = min(n, j0 + span);
+      uint32_t my_eq = 0u;
+      for (int j = j0; j < j1; ++j) my_eq += p_key<PREC>(P_row, j) == T;
+      uint32_t inc = my_eq;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(ACO_FULL_MASK, inc, off);
+        if (lane >= off) inc += v;
+      }
+      __syncthreads();
+      if (lane == 31) hist[wid] = inc;  // warp totals (hist is free again)
+      __syncthreads();
+      uint32_t rank = inc - my_eq;
+      for (int w = 0; w < wid; ++w) rank += hist[w];
+      for (int j = j0; j < j1 && rank < eq_take; ++j)
+        if (p_key<PREC>(P_row, j) == T) sk[n_gt + rank++] = list_sort_key(T, j);
+    }
+    while (S < cnt) S <<= 1;
+    __syncthreads();
+    for (int q = cnt + tid; q < S; q += nt) sk[q] = 0ull;  // padding sorts last
+    if (tid == 0) {
+      *cnt_out = cnt;
+      *bkey_out = all_ties ? T : T + 1u;
+    }
+    __syncthreads();
+  }
+  // 3. sort by key descending (ties: lower column first); write every slot
+  bitonic_desc(sk, S);
   for (int q = tid; q < kListMax; q += nt) {
-    const unsigned long long v = sk[q];
-    list[q] = q < cnt ? make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v) : make_uint2(0u, kListPad);
+    const unsigned long long v = q < S ? sk[q] : 0ull;
+    list[q] = v ? make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v) : make_uint2(0u, kListPad);
   }
   __syncthreads();
 }

@@ -25,7 +25,7 @@ def _keys(Pv, bits, prec):
     return Pv.astype(np.float32).view(np.uint32)
 
 
-LMAX, LTARGET = 256, 128
+LMAX, LTARGET = B.LIST_MAX, B.LIST_TARGET
 
 
 def _build(Pd, prec, n, ld):
@@ -50,8 +50,8 @@ def _P(orc, n, seed, prec, ties=False):
 
 
 @pytest.mark.parametrize("prec", [B.FP32, B.BF16, B.FP16])
-@pytest.mark.parametrize("n,ties", [(40, False), (256, False), (257, False), (500, False), (500, True),
-                                    (2001, False)])
+@pytest.mark.parametrize("n,ties", [(40, False), (B.LIST_MAX, False), (B.LIST_MAX + 1, False), (900, False),
+                                    (900, True), (2001, False)])
 def test_list_invariants(orc, prec, n, ties):
     Pv, bits = _P(orc, n, 7 + n, prec, ties)
     ld = B.ld_of(n)
