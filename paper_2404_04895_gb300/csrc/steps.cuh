@@ -263,7 +263,7 @@ __device__ __forceinline__ int2 deposit_scale_block(const double* __restrict__ c
 // smem: deposit_smem_bytes(n, cap).
 // ---------------------------------------------------------------------------
 constexpr int kDepThreads = 256;
-constexpr int kDepCap = 2048;
+constexpr int kDepCap = 512;  // 16 KB of slots: a row's touched columns are few once tours share edges
 
 __host__ __device__ inline int deposit_cap(int n, long long m) {
   long long c = 2 * m < (long long)n ? 2 * m : (long long)n;
@@ -291,10 +291,13 @@ __device__ __forceinline__ void deposit_row_exact(float* __restrict__ row, int n
   for (int w = tid; w < nw; w += nthr) bm[w] = 0u;
   __syncthreads();
   if (mode != kDepBad) {
+    // a bit already seen set needs no atomic (a stale read only repeats one)
     for (int k = tid; k < m; k += nthr) {
       const int2 e = __ldg(nbr_row + k);
-      if ((unsigned)e.x < (unsigned)n) atomicOr(bm + (e.x >> 5), 1u << (e.x & 31));
-      if ((unsigned)e.y < (unsigned)n) atomicOr(bm + (e.y >> 5), 1u << (e.y & 31));
+      if ((unsigned)e.x < (unsigned)n && !((bm[e.x >> 5] >> (e.x & 31)) & 1u))
+        atomicOr(bm + (e.x >> 5), 1u << (e.x & 31));
+      if ((unsigned)e.y < (unsigned)n && !((bm[e.y >> 5] >> (e.y & 31)) & 1u))
+        atomicOr(bm + (e.y >> 5), 1u << (e.y & 31));
     }
   }
   __syncthreads();
