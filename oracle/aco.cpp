@@ -324,6 +324,35 @@ void orc_deposit(float* tau, int n, const int32_t* tours, const double* L, int m
   }
 }
 
+// Sec. 2.3 (tensorization of ant paths): the solution set is sorted by
+// fitness -- tour length ascending, equal lengths by ant index -- and the
+// first k paths are selected.  selected[k] = 1 for them.  k <= 0 or k >= m
+// selects every path (plain Ant System).
+void orc_select_topk(const double* L, int m, int k, uint8_t* selected) {
+  std::vector<int> order((size_t)m);
+  for (int q = 0; q < m; ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return L[a] < L[b]; });
+  const int take = (k <= 0 || k >= m) ? m : k;
+  for (int q = 0; q < m; ++q) selected[q] = 0;
+  for (int q = 0; q < take; ++q) selected[order[q]] = 1;
+}
+
+// Evaporation then the deposit of the k selected paths only (Sec. 2.3:
+// Delta M_tau sums A over the selected set P); every entry evaporates.
+void orc_deposit_topk(float* tau, int n, const int32_t* tours, const double* L, int m,
+                      float rho, float Q, int k) {
+  std::vector<uint8_t> sel((size_t)m);
+  orc_select_topk(L, m, k, sel.data());
+  std::vector<int32_t> st;
+  std::vector<double> sl;
+  for (int q = 0; q < m; ++q) {
+    if (!sel[q]) continue;
+    st.insert(st.end(), tours + (size_t)q * n, tours + (size_t)(q + 1) * n);
+    sl.push_back(L[q]);
+  }
+  orc_deposit(tau, n, st.data(), sl.data(), (int)sl.size(), rho, Q);
+}
+
 double orc_exact_sum(const double* x, int64_t count) { return exact_sum(x, (size_t)count); }
 float orc_exact_sum_f32(const double* x, int64_t count) { return exact_sum_f32(x, (size_t)count); }
 
@@ -381,7 +410,7 @@ void orc_run(const orc_params* prm, const double* D, const float* H, float* tau,
       *best_len = L[kb];
       std::memcpy(best_tour, tours.data() + (size_t)kb * n, sizeof(int32_t) * n);
     }
-    orc_deposit(tau, n, tours.data(), L.data(), m, prm->rho, prm->Q);
+    orc_deposit_topk(tau, n, tours.data(), L.data(), m, prm->rho, prm->Q, prm->topk);
   }
   if (last_tours) std::memcpy(last_tours, tours.data(), sizeof(int32_t) * tours.size());
   if (last_L) std::memcpy(last_L, L.data(), sizeof(double) * L.size());

@@ -15,7 +15,7 @@ class OrcParams(C.Structure):
     _fields_ = [("n", C.c_int), ("m", C.c_int), ("alpha", C.c_int), ("beta", C.c_int),
                 ("rho", C.c_float), ("Q", C.c_float), ("seed", C.c_uint64),
                 ("prec", C.c_int), ("adair", C.c_int), ("gamma_max", C.c_float),
-                ("gamma_min", C.c_float), ("gamma_T", C.c_int)]
+                ("gamma_min", C.c_float), ("gamma_T", C.c_int), ("topk", C.c_int)]
 
 
 def _p(a):
@@ -56,6 +56,8 @@ def lib():
             "orc_tour_lengths": (None, [v, C.c_int, v, C.c_int, v]),
             "orc_exact_sum": (f64, [v, C.c_int64]),
             "orc_exact_sum_f32": (C.c_float, [v, C.c_int64]),
+            "orc_select_topk": (None, [v, C.c_int, C.c_int, v]),
+            "orc_deposit_topk": (None, [v, C.c_int, v, v, C.c_int, C.c_float, C.c_float, C.c_int]),
             "orc_index_matrix": (None, [v, C.c_int, v]),
             "orc_deposit": (None, [v, C.c_int, v, v, C.c_int, f32, f32]),
             "orc_deposit_fp32_order": (None, [v, C.c_int, v, v, C.c_int, f32, f32, v]),
@@ -235,6 +237,22 @@ def deposit(tau, tours, L, rho, Q):
     return tau
 
 
+def select_topk(L, k):
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    sel = np.zeros(L.size, dtype=np.uint8)
+    lib().orc_select_topk(_p(L), L.size, k, _p(sel))
+    return sel.astype(bool)
+
+
+def deposit_topk(tau, tours, L, rho, Q, k):
+    tau = np.array(tau, dtype=np.float32, copy=True, order="C")
+    tours = np.ascontiguousarray(tours, dtype=np.int32)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    m, n = tours.shape
+    lib().orc_deposit_topk(_p(tau), n, _p(tours), _p(L), m, rho, Q, k)
+    return tau
+
+
 def deposit_fp32_order(tau, tours, L, rho, Q, perm=None):
     tau = np.array(tau, dtype=np.float32, copy=True, order="C")
     tours = np.ascontiguousarray(tours, dtype=np.int32)
@@ -258,12 +276,12 @@ class State:
     """Oracle solver state: tau, best tour / length, iteration counter."""
 
     def __init__(self, xy, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec=FP32,
-                 adair=False, gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0):
+                 adair=False, gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0, topk=0):
         self.xy = np.ascontiguousarray(xy, dtype=np.float32)
         n = self.xy.shape[0]
         self.prm = OrcParams(n=n, m=m, alpha=alpha, beta=beta, rho=rho, Q=Q, seed=seed,
                              prec=prec, adair=int(adair), gamma_max=gamma_max,
-                             gamma_min=gamma_min, gamma_T=gamma_T)
+                             gamma_min=gamma_min, gamma_T=gamma_T, topk=topk)
         self.D = distances(self.xy)
         self.H = heuristic(self.D, beta)
         self.tau = init_tau(n, tau0)

@@ -115,6 +115,11 @@ float orc_exact_sum_f32(const double* x, int64_t count);
 void orc_index_matrix(const int32_t* tour, int n, int32_t* I);
 void orc_deposit(float* tau, int n, const int32_t* tours, const double* L, int m,
                  float rho, float Q);
+/* Sec. 2.3: sort by length (ascending, ties by ant index), select the first
+ * k paths (k <= 0 or k >= m: all); deposit from the selected paths only. */
+void orc_select_topk(const double* L, int m, int k, uint8_t* selected);
+void orc_deposit_topk(float* tau, int n, const int32_t* tours, const double* L, int m,
+                      float rho, float Q, int k);
 /* float-atomic reading, applied in a caller-given edge order (tests only):
  * tau <- fl32(fl32(1-rho)*tau) then tau[a][b] += fl32(Q/L_k) in fp32 per
  * directed edge, edges visited in the order given by perm (length 2*m*n). */
@@ -131,6 +136,7 @@ typedef struct {
   int adair;         /* 0: IR, 1: AdaIR */
   float gamma_max, gamma_min;
   int gamma_T;       /* schedule length */
+  int topk;          /* paths that deposit: 0 = all (Ant System), else the k shortest */
 } orc_params;
 
 /* Runs iterations it0 .. it0+iters-1 in place on tau (n x n) and on the best
