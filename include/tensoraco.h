@@ -89,6 +89,13 @@ int aco_set_precision(int prec);
  * fp32 atomics in hardware order (not reproducible). */
 int aco_set_deposit(int mode);
 
+/* Deposit path selection (Sec. 2.3: the solution set is sorted by fitness
+ * and the top k paths deposit; the paper's experiments use k = n/10): the
+ * k >= 1 shortest tours of each iteration deposit (equal lengths: lower ant
+ * index first), every entry still evaporates; k = 0 (default) or k >= m:
+ * every ant deposits.  Takes effect at the next iteration. */
+int aco_set_deposit_topk(int k);
+
 /* Run k >= 0 iterations (a)-(d).  Iterations are numbered from 0 across calls.
  * Asynchronous on the bound stream. */
 int aco_iterate(int k);
@@ -132,6 +139,8 @@ typedef struct {
   float gamma_max, gamma_min;
   int gamma_T;
   int cand_lists;           /* 1: candidate-list fast path (exact), 0: full scan only */
+  int topk;                 /* paths that deposit (Sec. 2.3): 0 = all (Ant System), else the
+                               topk shortest (ties: lower ant index); >= m means all */
 } aco_params;
 
 /* Fill *p with defaults: alpha 1, beta 2, rho 0.5, Q 1, tau0 1, seed 0, FP32,
@@ -301,6 +310,12 @@ int aco_op_best(const double* L_dev, const int32_t* tours_dev, int n, int m,
  * tau_dev n x ld, 16-byte aligned, updated in place. */
 int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const double* c_dev,
                    int m, float rho, int32_t* err_dev, void* stream);
+
+/* Sec. 2.3 path selection: with the lengths L_dev (m fp64) sorted ascending
+ * (equal lengths by ant index), set c_dev[j] = 0 for every ant j outside the
+ * first k, so that aco_op_deposit deposits from the k shortest paths only.
+ * k <= 0 or k >= m: c_dev is left unchanged.  One CTA; device buffers. */
+int aco_op_select_topk(const double* L_dev, int m, int k, double* c_dev, void* stream);
 
 /* Sec. 2.3, float-atomic: tau <- fl32(fl32(1-rho) tau), then for every
  * directed tour edge (a,b) of ant k: atomicAdd(tau_ab, fl32(c_k)). */

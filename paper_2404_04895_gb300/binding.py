@@ -31,7 +31,7 @@ class Params(C.Structure):
                 ("rho", C.c_float), ("Q", C.c_float), ("tau0", C.c_float),
                 ("seed", C.c_uint64), ("prec", C.c_int), ("roulette", C.c_int),
                 ("deposit", C.c_int), ("gamma_max", C.c_float), ("gamma_min", C.c_float),
-                ("gamma_T", C.c_int), ("cand_lists", C.c_int)]
+                ("gamma_T", C.c_int), ("cand_lists", C.c_int), ("topk", C.c_int)]
 
 
 _lib = None
@@ -42,6 +42,8 @@ _SIGS = {
     "aco_set_variant": (i32, [i32, f32, f32, i32]),
     "aco_set_precision": (i32, [i32]),
     "aco_set_deposit": (i32, [i32]),
+    "aco_set_deposit_topk": (i32, [i32]),
+    "aco_op_select_topk": (i32, [v, i32, i32, v, v]),
     "aco_iterate": (i32, [i32]),
     "aco_best": (i32, [v, v]),
     "aco_get_tau": (i32, [v]),
@@ -207,6 +209,10 @@ def op_deposit(tau, n, ld, nbr, c, m, rho, err=None, stream=None):
          stream_ptr(stream))
 
 
+def op_select_topk(L, m, k, c, stream=None):
+    call("aco_op_select_topk", ptr(L), m, k, ptr(c), stream_ptr(stream))
+
+
 def op_deposit_atomic(tau, n, ld, tours, c, m, rho, stream=None):
     call("aco_op_deposit_atomic", ptr(tau), n, ld, ptr(tours), ptr(c), m, rho, stream_ptr(stream))
 
@@ -262,7 +268,7 @@ class Solver:
 
     def __init__(self, coords, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec="fp32",
                  roulette="ir", deposit="det", gamma_max=1.5, gamma_min=0.5, gamma_T=100,
-                 tau0=1.0, workspace="torch", stream=None, cand_lists=True):
+                 tau0=1.0, workspace="torch", stream=None, cand_lists=True, topk=0):
         import torch
         xy = _host(coords, np.float32)
         n = xy.shape[0]
@@ -275,6 +281,7 @@ class Solver:
         p.deposit = DEPOSIT[deposit] if isinstance(deposit, str) else deposit
         p.gamma_max, p.gamma_min, p.gamma_T = gamma_max, gamma_min, gamma_T
         p.cand_lists = int(cand_lists)
+        p.topk = int(topk)
         self.params = p
         self.n, self.m = n, m
         self.stream = stream
@@ -355,7 +362,8 @@ class Solver:
 
 
 def make_params(n, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec="fp32", roulette="ir",
-                deposit="det", gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0, cand_lists=True):
+                deposit="det", gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0, cand_lists=True,
+                topk=0):
     p = Params()
     call("aco_params_default", C.byref(p))
     p.n, p.m, p.alpha, p.beta = n, m, alpha, beta
@@ -365,6 +373,7 @@ def make_params(n, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec="fp32", roul
     p.deposit = DEPOSIT[deposit] if isinstance(deposit, str) else deposit
     p.gamma_max, p.gamma_min, p.gamma_T = gamma_max, gamma_min, gamma_T
     p.cand_lists = int(cand_lists)
+    p.topk = int(topk)
     return p
 
 

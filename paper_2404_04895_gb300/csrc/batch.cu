@@ -75,9 +75,10 @@ __global__ void __launch_bounds__(256) batch_best_kernel(const InstDev* __restri
                                                          int32_t* __restrict__ err) {
   __shared__ double sl[32];
   __shared__ int sk[33];
-  __shared__ int sred[100];
+  __shared__ int sred[300];
   const InstDev& I = insts[blockIdx.x];
   best_block(I.L, I.tours, I.n, I.m, I.best_tour, I.best_len, I.it, sl, sk);
+  select_topk_block(I.L, I.m, I.topk, I.c, sred);
   const int2 d = deposit_scale_block(I.c, I.m, sred);
   if (threadIdx.x == 0) {
     *I.dep = d;

@@ -9,6 +9,7 @@ namespace aco {
 struct InstDev {
   int n, m, ld, alpha;
   int adair, n_sched;
+  int topk;                       // paths that deposit (0: all)
   float rho, Q;
   uint2 key;                      // Philox key (seed low, high)
   const float* H;                 // eta^beta, n x ld

@@ -96,10 +96,12 @@ int launch_build_P(const float* tau, const float* H, int n, int ld, int alpha, f
                    void* P, cudaStream_t st);
 int launch_tour_length(const double* D, int n, const int32_t* tours, int m, float Q,
                        double* L, double* c, int32_t* nbr, cudaStream_t st);
-// best also derives the deposit weights' scaling into *dep when dep is non-null
+// best also keeps only the topk shortest paths' weights in c (c non-null,
+// 0 < topk < m) and derives the deposit weights' scale into *dep (non-null)
 int launch_best(const double* L, const int32_t* tours, int n, int m, int32_t* best_tour,
-                double* best_len, uint32_t* it_dev, const double* c, int2* dep, int32_t* err,
+                double* best_len, uint32_t* it_dev, double* c, int topk, int2* dep, int32_t* err,
                 cudaStream_t st);
+int launch_select_topk(const double* L, int m, int k, double* c, cudaStream_t st);
 // dep null: every CTA derives the scaling from c; err (nullable) gets
 // kErrDepositRange when the weights cannot be summed exactly
 int launch_deposit(float* tau, int n, int ld, const int32_t* nbr, const double* c, int m,

@@ -92,12 +92,13 @@ __global__ void __launch_bounds__(1024) best_kernel(const double* __restrict__ L
                                                     int m, int32_t* __restrict__ best_tour,
                                                     double* __restrict__ best_len,
                                                     uint32_t* __restrict__ it_dev,
-                                                    const double* __restrict__ c,
+                                                    double* __restrict__ c, int topk,
                                                     int2* __restrict__ dep, int32_t* __restrict__ err) {
   __shared__ double sl[32];
   __shared__ int sk[33];
-  __shared__ int sred[100];
+  __shared__ int sred[300];
   best_block(L, tours, n, m, best_tour, best_len, it_dev, sl, sk);
+  if (c) select_topk_block(L, m, topk, c, sred);
   if (dep) {
     const int2 d = deposit_scale_block(c, m, sred);
     if (threadIdx.x == 0) {
@@ -164,6 +165,14 @@ __global__ void pow_own_kernel(const float* __restrict__ x, float e, float* __re
                                int count) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < count) out[q] = pow_own(x[q], e);
+}
+
+// Sec. 2.3 selection alone (step-level call): zero the weights of all but the
+// k shortest paths.
+__global__ void __launch_bounds__(1024) select_topk_kernel(const double* __restrict__ L, int m, int k,
+                                                           double* __restrict__ c) {
+  __shared__ int sred[300];
+  select_topk_block(L, m, k, c, sred);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -233,10 +242,15 @@ int launch_tour_length(const double* D, int n, const int32_t* tours, int m, floa
 }
 
 int launch_best(const double* L, const int32_t* tours, int n, int m, int32_t* best_tour,
-                double* best_len, uint32_t* it_dev, const double* c, int2* dep, int32_t* err,
+                double* best_len, uint32_t* it_dev, double* c, int topk, int2* dep, int32_t* err,
                 cudaStream_t st) {
-  best_kernel<<<1, 1024, 0, st>>>(L, tours, n, m, best_tour, best_len, it_dev, c, dep, err);
+  best_kernel<<<1, 1024, 0, st>>>(L, tours, n, m, best_tour, best_len, it_dev, c, topk, dep, err);
   return check_launch("best_kernel");
+}
+
+int launch_select_topk(const double* L, int m, int k, double* c, cudaStream_t st) {
+  select_topk_kernel<<<1, 1024, 0, st>>>(L, m, k, c);
+  return check_launch("select_topk_kernel");
 }
 
 int prepare_deposit() {

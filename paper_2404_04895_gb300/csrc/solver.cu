@@ -169,6 +169,7 @@ static int validate(const aco_params* p) {
   if (!(p->rho >= 0.0f && p->rho <= 1.0f)) return set_error(ACO_ERR_ARG, "rho outside [0, 1]");
   if (!(p->Q > 0.0f) || !std::isfinite(p->Q)) return set_error(ACO_ERR_ARG, "Q must be finite and > 0");
   if (!(p->tau0 > 0.0f) || !std::isfinite(p->tau0)) return set_error(ACO_ERR_ARG, "tau0 must be finite and > 0");
+  if (p->topk < 0) return set_error(ACO_ERR_ARG, "topk=%d must be >= 0 (0: every path deposits)", p->topk);
   if (p->prec < ACO_FP32 || p->prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", p->prec);
   if (p->roulette != ACO_IR && p->roulette != ACO_ADAIR) return set_error(ACO_ERR_ARG, "unknown roulette %d", p->roulette);
   if (p->deposit != ACO_DEPOSIT_DET && p->deposit != ACO_DEPOSIT_ATOMIC)
@@ -245,6 +246,7 @@ int instance_bind(const aco_params& p, unsigned char* ws, InstDev* d, cudaStream
   x.n_sched = x.adair ? std::min(p.gamma_T + 1, kSchedCap) : 1;
   x.rho = p.rho;
   x.Q = p.Q;
+  x.topk = p.topk;
   x.key = make_uint2((uint32_t)p.seed, (uint32_t)(p.seed >> 32));
   float* coords = reinterpret_cast<float*>(ws + L.coords);
   x.D = reinterpret_cast<double*>(ws + L.D);
@@ -367,8 +369,8 @@ static int enqueue_iteration(aco_solver* s) {
   rc = launch_tour_length(s->D, n, s->tours, m, p.Q, s->L, s->c, det ? s->nbr : nullptr, st);
   if (rc) return rc;
   probe(4);
-  rc = launch_best(s->L, s->tours, n, m, s->best_tour, s->best_len, s->it_dev, s->c, det ? s->dep : nullptr,
-                   s->err, st);
+  rc = launch_best(s->L, s->tours, n, m, s->best_tour, s->best_len, s->it_dev, s->c, p.topk,
+                   det ? s->dep : nullptr, s->err, st);
   if (rc) return rc;
   probe(5);
   if (det)
@@ -439,6 +441,7 @@ int aco_params_default(aco_params* p) {
   p->gamma_min = 0.5f;
   p->gamma_T = 100;
   p->cand_lists = 1;
+  p->topk = 0;
   return ACO_OK;
 }
 
@@ -786,6 +789,22 @@ int aco_set_precision(int prec) {
   return ACO_OK;
 }
 
+int aco_set_deposit_topk(int k) {
+  if (k < 0) return set_error(ACO_ERR_ARG, "topk=%d must be >= 0 (0: every path deposits)", k);
+  g_pending.topk = k;
+  if (g_solver) {
+    g_solver->p.topk = k;
+    drop_graph(g_solver);
+  }
+  return ACO_OK;
+}
+
+int aco_op_select_topk(const double* L_dev, int m, int k, double* c_dev, void* stream) {
+  if (!L_dev || !c_dev) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "m out of range");
+  return launch_select_topk(L_dev, m, k, c_dev, static_cast<cudaStream_t>(stream));
+}
+
 int aco_set_deposit(int mode) {
   if (mode != ACO_DEPOSIT_DET && mode != ACO_DEPOSIT_ATOMIC) return set_error(ACO_ERR_ARG, "unknown deposit mode %d", mode);
   g_pending.deposit = mode;
@@ -915,7 +934,7 @@ int aco_op_best(const double* L_dev, const int32_t* tours_dev, int n, int m, int
                 double* best_len_dev, void* stream) {
   if (!L_dev || !tours_dev || !best_tour_dev || !best_len_dev) return set_error(ACO_ERR_ARG, "NULL argument");
   if (n < 3 || n > ACO_MAX_N || m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "n or m out of range");
-  return launch_best(L_dev, tours_dev, n, m, best_tour_dev, best_len_dev, nullptr, nullptr, nullptr, nullptr,
+  return launch_best(L_dev, tours_dev, n, m, best_tour_dev, best_len_dev, nullptr, nullptr, 0, nullptr, nullptr,
                      static_cast<cudaStream_t>(stream));
 }
 

@@ -189,6 +189,95 @@ __device__ __forceinline__ void best_block(const double* __restrict__ L,
 }
 
 // ---------------------------------------------------------------------------
+// Sec. 2.3, selection of the deposit paths: the solution set sorted by
+// length (ascending, equal lengths by ant index) and the first k kept.  The
+// weight c_j of every other ant is set to 0, so it deposits nothing.  Radix
+// select of the k-th smallest length (its fp64 bit pattern, order-preserving
+// for lengths >= 0), 8 bits per pass from the top; the kept lengths equal to
+// it are those of the lowest ant indices.  k <= 0 or k >= m keeps every ant.
+// All threads of the CTA (blockDim.x a multiple of 32, <= 1024); sred: 300
+// ints of shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void select_topk_block(const double* __restrict__ L, int m, int k,
+                                                  double* __restrict__ c, int* sred) {
+  if (k <= 0 || k >= m) return;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(sred);  // [256]
+  int* sh = sred + 256;                                // [0..1] prefix, [2] need, [3] below, [8..39] warp sums
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  unsigned long long prefix = 0ull;
+  uint32_t need = (uint32_t)k, below = 0u;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int b = tid; b < 256; b += nt) hist[b] = 0u;
+    __syncthreads();
+    const unsigned long long hi_mask = shift == 56 ? 0ull : (~0ull << (shift + 8));
+    for (int j = tid; j < m; j += nt) {
+      const unsigned long long key = (unsigned long long)__double_as_longlong(L[j]);
+      if ((key & hi_mask) == prefix) atomicAdd(hist + (int)((key >> shift) & 0xFFull), 1u);
+    }
+    __syncthreads();
+    if (wid == 0) {  // lane l holds bins 8l .. 8l+7 (ascending)
+      uint32_t h[8], sum = 0u;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        h[i] = hist[8 * lane + i];
+        sum += h[i];
+      }
+      uint32_t inc = sum;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(ACO_FULL_MASK, inc, off);
+        if (lane >= off) inc += v;
+      }
+      uint32_t cum = inc - sum;
+      if (cum < need && inc >= need) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (cum + h[i] >= need) {
+            const unsigned long long px = prefix | ((unsigned long long)(8 * lane + i) << shift);
+            sh[0] = (int)(uint32_t)px;
+            sh[1] = (int)(uint32_t)(px >> 32);
+            sh[2] = (int)(need - cum);
+            sh[3] = (int)cum;
+            break;
+          }
+          cum += h[i];
+        }
+      }
+    }
+    __syncthreads();
+    prefix = (unsigned long long)(uint32_t)sh[0] | ((unsigned long long)(uint32_t)sh[1] << 32);
+    need = (uint32_t)sh[2];
+    below += (uint32_t)sh[3];
+    __syncthreads();
+  }
+  // keep: key < T, or key == T among the first `need` such ants by index;
+  // each thread takes a contiguous run of ants, ranks by an exclusive scan
+  const unsigned long long T = prefix;
+  const int span = (m + nt - 1) / nt;
+  const int j0 = tid * span, j1 = min(m, j0 + span);
+  uint32_t my_eq = 0u;
+  for (int j = j0; j < j1; ++j) my_eq += (unsigned long long)__double_as_longlong(L[j]) == T;
+  uint32_t inc = my_eq;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(ACO_FULL_MASK, inc, off);
+    if (lane >= off) inc += v;
+  }
+  if (lane == 31) sh[8 + wid] = (int)inc;
+  __syncthreads();
+  uint32_t rank = inc - my_eq;
+  for (int w = 0; w < wid; ++w) rank += (uint32_t)sh[8 + w];
+  for (int j = j0; j < j1; ++j) {
+    const unsigned long long key = (unsigned long long)__double_as_longlong(L[j]);
+    bool keep = key < T;
+    if (key == T) keep = rank++ < need;
+    if (!keep) c[j] = 0.0;
+  }
+  __threadfence_block();
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Scaling of the deposit weights c[0..m) for the exact fixed-point sums
 // (exact.cuh): x = E0, the smallest exponent of a positive finite weight, and
 // y = mode: kDepFixed; kDepInf if some weight is +inf (a zero tour length:
@@ -291,8 +380,10 @@ __device__ __forceinline__ void deposit_row_exact(float* __restrict__ row, int n
   for (int w = tid; w < nw; w += nthr) bm[w] = 0u;
   __syncthreads();
   if (mode != kDepBad) {
-    // a bit already seen set needs no atomic (a stale read only repeats one)
+    // a bit already seen set needs no atomic (a stale read only repeats one);
+    // ants of weight 0 (not selected) leave their entries at tau'
     for (int k = tid; k < m; k += nthr) {
+      if (__ldg(c + k) == 0.0) continue;
       const int2 e = __ldg(nbr_row + k);
       if ((unsigned)e.x < (unsigned)n && !((bm[e.x >> 5] >> (e.x & 31)) & 1u))
         atomicOr(bm + (e.x >> 5), 1u << (e.x & 31));
