@@ -163,6 +163,97 @@ void orc_construct(const float* P_val, int n, uint64_t seed, uint32_t it, int k_
   (void)nthreads;
 }
 
+// ---------------------------------------------------------------------------
+// Roulette wheel (Sec. 2.4: the classical selection that IR replaces): the
+// next city is drawn with probability proportional to p_j over the unvisited
+// j.  Exact integer reading, so that every summation order agrees:
+//   e    = floor(log2 of the largest unvisited p_j)
+//   q_j  = floor(p_j * 2^(40 - e))        (the largest q lies in [2^40, 2^41))
+//   S    = sum of q_j over the unvisited j
+//   u    = words 0 (high) and 1 (low) of Philox(counter (2^30, t, k, it))
+//   v    = floor(u * S / 2^64)            (uniform integer in [0, S))
+//   next = the first unvisited j, in column order, whose running sum of q
+//          exceeds v; when S = 0 (every unvisited p is 0) the lowest
+//          unvisited j.
+// ---------------------------------------------------------------------------
+static int fp32_exponent(float p) {  // floor(log2 p) for p > 0 finite
+  uint32_t b;
+  std::memcpy(&b, &p, 4);
+  int eb = (int)((b >> 23) & 0xFF);
+  if (eb) return eb - 127;
+  // subnormal: position of the highest set fraction bit
+  int e = -127;
+  uint32_t f = b & 0x7FFFFFu;
+  while (f) {
+    ++e;
+    f >>= 1;
+  }
+  return e - 22 - 1;
+}
+
+uint64_t orc_rw_quantum(float p, int e) {
+  if (!(p > 0.0f)) return 0;
+  // p * 2^(40 - e) exactly in fp64 (p has 24 significant bits), then floor
+  double v = std::ldexp((double)p, 40 - e);
+  return (uint64_t)std::floor(v);
+}
+
+int32_t orc_select_rw(const float* row, const uint8_t* visited, int n, uint64_t seed,
+                      uint32_t it, uint32_t k, uint32_t t) {
+  float pmax = 0.0f;
+  int32_t first = -1;
+  for (int j = 0; j < n; ++j) {
+    if (visited[j]) continue;
+    if (first < 0) first = j;
+    if (row[j] > pmax) pmax = row[j];
+  }
+  if (first < 0) return -1;
+  if (!(pmax > 0.0f)) return first;
+  const int e = fp32_exponent(pmax);
+  uint64_t S = 0;
+  for (int j = 0; j < n; ++j)
+    if (!visited[j]) S += orc_rw_quantum(row[j], e);
+  uint32_t ctr[4] = {1u << 30, t, k, it};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  const uint64_t u = ((uint64_t)out[0] << 32) | (uint64_t)out[1];
+  const uint64_t v = (uint64_t)(((unsigned __int128)u * (unsigned __int128)S) >> 64);
+  uint64_t run = 0;
+  for (int j = 0; j < n; ++j) {
+    if (visited[j]) continue;
+    run += orc_rw_quantum(row[j], e);
+    if (run > v) return j;
+  }
+  return -1;  // unreachable: the running sum reaches S > v
+}
+
+static void construct_one_rw(const float* P_val, int n, uint64_t seed, uint32_t it, int k,
+                             int32_t* tour) {
+  std::vector<uint8_t> visited((size_t)n, 0);
+  int32_t cur = orc_start_city(seed, it, (uint32_t)k, n);
+  tour[0] = cur;
+  visited[cur] = 1;
+  for (int t = 1; t < n; ++t) {
+    int32_t v = orc_select_rw(P_val + (size_t)cur * n, visited.data(), n, seed, it,
+                              (uint32_t)k, (uint32_t)t);
+    tour[t] = v;
+    visited[v] = 1;
+    cur = v;
+  }
+}
+
+void orc_construct_rw(const float* P_val, int n, uint64_t seed, uint32_t it, int k_begin,
+                      int k_end, int32_t* tours, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+  for (int k = k_begin; k < k_end; ++k)
+    construct_one_rw(P_val, n, seed, it, k, tours + (size_t)(k - k_begin) * n);
+  (void)nthreads;
+}
+
 // f(s) (Eq. 3): closed tour length, the sum over t = 0..n-1 of
 // d(p_t, p_{t+1 mod n}) in fp64, taken in blocks of 32 consecutive edges:
 // each block t = 32b .. 32b+31 summed in t order, then the block sums added
@@ -401,7 +492,10 @@ void orc_run(const orc_params* prm, const double* D, const float* H, float* tau,
       inv_gamma = orc_inv_gamma(g);
     }
     orc_build_P(tau, H, n, prm->alpha, inv_gamma, prm->prec, P.data(), nullptr, nullptr);
-    orc_construct(P.data(), n, prm->seed, it, 0, m, tours.data(), nthreads);
+    if (prm->rw)
+      orc_construct_rw(P.data(), n, prm->seed, it, 0, m, tours.data(), nthreads);
+    else
+      orc_construct(P.data(), n, prm->seed, it, 0, m, tours.data(), nthreads);
     orc_tour_lengths(D, n, tours.data(), m, L.data());
     int kb = 0;
     for (int k = 1; k < m; ++k)

@@ -15,7 +15,7 @@ class OrcParams(C.Structure):
     _fields_ = [("n", C.c_int), ("m", C.c_int), ("alpha", C.c_int), ("beta", C.c_int),
                 ("rho", C.c_float), ("Q", C.c_float), ("seed", C.c_uint64),
                 ("prec", C.c_int), ("adair", C.c_int), ("gamma_max", C.c_float),
-                ("gamma_min", C.c_float), ("gamma_T", C.c_int), ("topk", C.c_int)]
+                ("gamma_min", C.c_float), ("gamma_T", C.c_int), ("topk", C.c_int), ("rw", C.c_int)]
 
 
 def _p(a):
@@ -57,6 +57,9 @@ def lib():
             "orc_exact_sum": (f64, [v, C.c_int64]),
             "orc_exact_sum_f32": (C.c_float, [v, C.c_int64]),
             "orc_select_topk": (None, [v, C.c_int, C.c_int, v]),
+            "orc_rw_quantum": (u64, [C.c_float, C.c_int]),
+            "orc_select_rw": (i32, [v, v, C.c_int, u64, u32, u32, u32]),
+            "orc_construct_rw": (None, [v, C.c_int, u64, u32, C.c_int, C.c_int, v, C.c_int]),
             "orc_deposit_topk": (None, [v, C.c_int, v, v, C.c_int, C.c_float, C.c_float, C.c_int]),
             "orc_index_matrix": (None, [v, C.c_int, v]),
             "orc_deposit": (None, [v, C.c_int, v, v, C.c_int, f32, f32]),
@@ -237,6 +240,24 @@ def deposit(tau, tours, L, rho, Q):
     return tau
 
 
+def rw_quantum(p, e):
+    return int(lib().orc_rw_quantum(float(p), int(e)))
+
+
+def select_rw(row, visited, seed, it, k, t):
+    row = np.ascontiguousarray(row, dtype=np.float32)
+    vis = np.ascontiguousarray(visited, dtype=np.uint8)
+    return int(lib().orc_select_rw(_p(row), _p(vis), row.size, seed, it, k, t))
+
+
+def construct_rw(P_val, seed, it, k_begin, k_end, nthreads=None):
+    P_val = np.ascontiguousarray(P_val, dtype=np.float32)
+    n = P_val.shape[0]
+    tours = np.empty((k_end - k_begin, n), dtype=np.int32)
+    lib().orc_construct_rw(_p(P_val), n, seed, it, k_begin, k_end, _p(tours), nthreads or default_threads())
+    return tours
+
+
 def select_topk(L, k):
     L = np.ascontiguousarray(L, dtype=np.float64)
     sel = np.zeros(L.size, dtype=np.uint8)
@@ -276,12 +297,13 @@ class State:
     """Oracle solver state: tau, best tour / length, iteration counter."""
 
     def __init__(self, xy, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec=FP32,
-                 adair=False, gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0, topk=0):
+                 adair=False, gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0, topk=0,
+                 rw=False):
         self.xy = np.ascontiguousarray(xy, dtype=np.float32)
         n = self.xy.shape[0]
         self.prm = OrcParams(n=n, m=m, alpha=alpha, beta=beta, rho=rho, Q=Q, seed=seed,
                              prec=prec, adair=int(adair), gamma_max=gamma_max,
-                             gamma_min=gamma_min, gamma_T=gamma_T, topk=topk)
+                             gamma_min=gamma_min, gamma_T=gamma_T, topk=topk, rw=int(rw))
         self.D = distances(self.xy)
         self.H = heuristic(self.D, beta)
         self.tau = init_tau(n, tau0)

@@ -104,6 +104,17 @@ int32_t orc_select_literal_adair(const float* row, const uint8_t* visited, int n
                                  uint64_t seed, uint32_t it, uint32_t k, uint32_t t,
                                  double gamma);
 
+/* Roulette wheel (Sec. 2.4, the selection IR replaces), exact integer
+ * reading: q_j = floor(p_j 2^(40-e)), e = floor(log2 max unvisited p); a
+ * 64-bit uniform u (Philox counter (2^30, t, k, it), words 0 and 1) picks
+ * v = floor(u S / 2^64), S = sum of unvisited q; the first unvisited j whose
+ * running sum exceeds v wins (S = 0: the lowest unvisited j). */
+uint64_t orc_rw_quantum(float p, int e);
+int32_t orc_select_rw(const float* row, const uint8_t* visited, int n, uint64_t seed,
+                      uint32_t it, uint32_t k, uint32_t t);
+void orc_construct_rw(const float* P_val, int n, uint64_t seed, uint32_t it, int k_begin,
+                      int k_end, int32_t* tours, int nthreads);
+
 /* ---- fitness f (Eq. 3) ---- */
 void orc_tour_lengths(const double* D, int n, const int32_t* tours, int m, double* L);
 /* exact sum of count doubles rounded once to fp64 / to fp32 (ties to even) */
@@ -137,6 +148,7 @@ typedef struct {
   float gamma_max, gamma_min;
   int gamma_T;       /* schedule length */
   int topk;          /* paths that deposit: 0 = all (Ant System), else the k shortest */
+  int rw;            /* 1: roulette-wheel construction instead of IR / AdaIR */
 } orc_params;
 
 /* Runs iterations it0 .. it0+iters-1 in place on tau (n x n) and on the best
