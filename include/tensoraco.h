@@ -52,7 +52,7 @@ extern "C" {
 #define ACO_MAX_M 1048576
 
 enum { ACO_FP32 = 0, ACO_BF16 = 1, ACO_FP16 = 2 };           /* storage of M_p */
-enum { ACO_IR = 0, ACO_ADAIR = 1 };                          /* selection, Sec. 2.4 */
+enum { ACO_IR = 0, ACO_ADAIR = 1, ACO_RW = 2 };               /* selection, Sec. 2.4 */
 enum { ACO_DEPOSIT_DET = 0, ACO_DEPOSIT_ATOMIC = 1 };        /* Delta M_tau summation */
 
 /* Text of the calling thread's last error ("" if none). Never NULL. */
@@ -71,7 +71,13 @@ const char* aco_last_error(void);
 int aco_init(const float* coords_host, int n, int m, float alpha, float beta, float rho,
              float Q, uint64_t seed);
 
-/* Selection mechanism (Sec. 2.4).  ACO_IR ignores the gammas.  ACO_ADAIR
+/* Selection mechanism (Sec. 2.4).  ACO_RW is the roulette wheel IR replaces,
+ * in an exact integer reading: with e = floor(log2 max unvisited p),
+ * q_j = floor(p_j 2^(40-e)), S the sum of the unvisited q, a 64-bit uniform u
+ * from Philox counter (2^30, t, k, it) (words 0, 1) and v = floor(u S / 2^64),
+ * the next city is the first unvisited j whose running sum of q exceeds v
+ * (S = 0: the lowest unvisited j); n <= 16384, no candidate lists, not in
+ * batches.  ACO_IR ignores the gammas.  ACO_ADAIR
  * anneals gamma from gamma_max to gamma_min over T iterations by a cosine
  * schedule (gamma_t = gmin + (gmax-gmin)/2 (1 + cos(pi t / T)), gmin after T)
  * and selects argmax(r^gamma p) in the equivalent form argmax(r p^(1/gamma)).
@@ -134,7 +140,7 @@ typedef struct {
   float rho, Q, tau0;       /* rho in [0,1], Q > 0, tau0 > 0 */
   uint64_t seed;
   int prec;                 /* ACO_FP32 / ACO_BF16 / ACO_FP16 */
-  int roulette;             /* ACO_IR / ACO_ADAIR */
+  int roulette;             /* ACO_IR / ACO_ADAIR / ACO_RW */
   int deposit;              /* ACO_DEPOSIT_DET / ACO_DEPOSIT_ATOMIC */
   float gamma_max, gamma_min;
   int gamma_T;
@@ -275,6 +281,11 @@ int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, ui
 #define ACO_LIST_MAX 512
 int aco_op_build_lists(const void* P_dev, int prec, int n, int ld, void* lists_dev, int* lcnt_dev,
                        uint32_t* lkey_dev, void* stream);
+
+/* Sec. 2.4 roulette wheel (ACO_RW above) for all m ants on M_p; n <= 16384
+ * (ACO_ERR_UNSUPPORTED beyond).  Arguments as for aco_op_construct. */
+int aco_op_construct_rw(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,
+                        int32_t* tours_dev, int32_t* err_dev, void* stream);
 
 /* aco_op_construct_shape with candidate lists (from aco_op_build_lists on the
  * same M_p; lists_dev NULL: full scan only).  The tours are the same either

@@ -9,12 +9,12 @@ import numpy as np
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 FP32, BF16, FP16 = 0, 1, 2
-IR, ADAIR = 0, 1
+IR, ADAIR, RW = 0, 1, 2
 DEPOSIT_DET, DEPOSIT_ATOMIC = 0, 1
 MAX_N = 65536
 
 PREC = {"fp32": FP32, "bf16": BF16, "fp16": FP16}
-ROULETTE = {"ir": IR, "adair": ADAIR}
+ROULETTE = {"ir": IR, "adair": ADAIR, "rw": RW}
 DEPOSIT = {"det": DEPOSIT_DET, "atomic": DEPOSIT_ATOMIC}
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtensoraco.so")
@@ -83,6 +83,7 @@ _SIGS = {
     "aco_op_fill": (i32, [v, i32, i32, f32, v]),
     "aco_op_build_P": (i32, [v, v, i32, i32, i32, f32, i32, v, v]),
     "aco_op_construct": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, v]),
+    "aco_op_construct_rw": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, v]),
     "aco_op_construct_shape": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, i32, i32, i32, v]),
     "aco_op_build_lists": (i32, [v, i32, i32, i32, v, v, v, v]),
     "aco_op_construct_ex": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, v, v, v, i32, i32, i32, v]),
@@ -186,6 +187,10 @@ def _check_lists(n, lists, lcnt, lkey):
 def op_build_lists(P, prec, n, ld, lists, lcnt, lkey, stream=None):
     _check_lists(n, lists, lcnt, lkey)
     call("aco_op_build_lists", ptr(P), prec, n, ld, ptr(lists), ptr(lcnt), ptr(lkey), stream_ptr(stream))
+
+
+def op_construct_rw(P, prec, n, ld, m, seed, it, tours, err=None, stream=None):
+    call("aco_op_construct_rw", ptr(P), prec, n, ld, m, seed, it, ptr(tours), ptr(err), stream_ptr(stream))
 
 
 def op_construct_ex(P, prec, n, ld, m, seed, it, tours, lists=None, lcnt=None, lkey=None, err=None,

@@ -79,6 +79,10 @@ int launch_batch_construct_lean(const InstDev* insts, const int* ant_off, int co
                                 int* counter, int32_t* err, int prec, int max_n, int num_sms,
                                 cudaStream_t st);
 int prepare_construct_lean();
+// Roulette-wheel construction (Sec. 2.4 baseline), n <= 16384, one warp per ant.
+int launch_construct_rw(const void* P, int prec, int n, int ld, int m, uint2 key, uint32_t it,
+                        const uint32_t* it_dev, int32_t* tours, int32_t* err, cudaStream_t st);
+int prepare_construct_rw();
 constexpr int kModeLean = 2;
 constexpr int kLeanMaxN = 16384;
 

@@ -118,6 +118,7 @@ int prepare_kernels() {
     if (!rc) rc = prepare_construct_f16();
     if (!rc) rc = prepare_deposit();
     if (!rc) rc = prepare_construct_lean();
+    if (!rc) rc = prepare_construct_rw();
   });
   return rc == ACO_OK ? ACO_OK : set_error(rc, "kernel preparation failed");
 }
@@ -171,7 +172,10 @@ static int validate(const aco_params* p) {
   if (!(p->tau0 > 0.0f) || !std::isfinite(p->tau0)) return set_error(ACO_ERR_ARG, "tau0 must be finite and > 0");
   if (p->topk < 0) return set_error(ACO_ERR_ARG, "topk=%d must be >= 0 (0: every path deposits)", p->topk);
   if (p->prec < ACO_FP32 || p->prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", p->prec);
-  if (p->roulette != ACO_IR && p->roulette != ACO_ADAIR) return set_error(ACO_ERR_ARG, "unknown roulette %d", p->roulette);
+  if (p->roulette != ACO_IR && p->roulette != ACO_ADAIR && p->roulette != ACO_RW)
+    return set_error(ACO_ERR_ARG, "unknown roulette %d", p->roulette);
+  if (p->roulette == ACO_RW && p->n > 16384)
+    return set_error(ACO_ERR_UNSUPPORTED, "roulette-wheel construction serves n <= 16384");
   if (p->deposit != ACO_DEPOSIT_DET && p->deposit != ACO_DEPOSIT_ATOMIC)
     return set_error(ACO_ERR_ARG, "unknown deposit mode %d", p->deposit);
   if (p->roulette == ACO_ADAIR) {
@@ -356,13 +360,17 @@ static int enqueue_iteration(aco_solver* s) {
                           s->P_f, st);
   if (rc) return rc;
   probe(1);
-  const bool lists = p.cand_lists != 0;
+  const bool rw = p.roulette == ACO_RW;
+  const bool lists = p.cand_lists != 0 && !rw;
   if (lists) rc = launch_build_lists(s->P_f, p.prec, n, s->ld, s->lists, s->lcnt, s->lkey, st);
   if (rc) return rc;
   probe(2);
-  rc = launch_construct(s->P_f, p.prec, n, s->ld, m, make_uint2((uint32_t)p.seed, (uint32_t)(p.seed >> 32)),
-                        0u, s->it_dev, s->tours, s->err, s->shape, lists ? s->lists : nullptr, s->lcnt,
-                        s->lkey, st);
+  const uint2 key = make_uint2((uint32_t)p.seed, (uint32_t)(p.seed >> 32));
+  if (rw)
+    rc = launch_construct_rw(s->P_f, p.prec, n, s->ld, m, key, 0u, s->it_dev, s->tours, s->err, st);
+  else
+    rc = launch_construct(s->P_f, p.prec, n, s->ld, m, key, 0u, s->it_dev, s->tours, s->err, s->shape,
+                          lists ? s->lists : nullptr, s->lcnt, s->lkey, st);
   if (rc) return rc;
   probe(3);
   const bool det = p.deposit == ACO_DEPOSIT_DET;
@@ -760,7 +768,8 @@ int aco_set_variant(int roulette, float gamma_max, float gamma_min, int T) {
   p.gamma_min = gamma_min;
   p.gamma_T = T;
   if (p.n == 0) {  // no solver yet: validate the variant fields only
-    if (roulette != ACO_IR && roulette != ACO_ADAIR) return set_error(ACO_ERR_ARG, "unknown roulette %d", roulette);
+    if (roulette != ACO_IR && roulette != ACO_ADAIR && roulette != ACO_RW)
+      return set_error(ACO_ERR_ARG, "unknown roulette %d", roulette);
     if (roulette == ACO_ADAIR && (!(gamma_max > 0 && gamma_max <= 16 && gamma_min > 0 && gamma_min <= 16) || T < 1))
       return set_error(ACO_ERR_ARG, "invalid gamma schedule");
   } else {
@@ -915,6 +924,19 @@ int aco_op_construct_ex(const void* P_dev, int prec, int n, int ld, int m, uint6
   return launch_construct(P_dev, prec, n, ld, m, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), it,
                           nullptr, tours_dev, err_dev, s, static_cast<const uint2*>(lists_dev), lcnt_dev,
                           lkey_dev, static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_construct_rw(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,
+                        int32_t* tours_dev, int32_t* err_dev, void* stream) {
+  int rc = check_mat(P_dev, n, ld, "P");
+  if (rc) return rc;
+  if (m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "m=%d outside [1, %d]", m, ACO_MAX_M);
+  if (!tours_dev) return set_error(ACO_ERR_ARG, "tours is NULL");
+  if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  rc = prepare_kernels();
+  if (rc) return rc;
+  return launch_construct_rw(P_dev, prec, n, ld, m, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), it,
+                             nullptr, tours_dev, err_dev, static_cast<cudaStream_t>(stream));
 }
 
 int aco_op_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,
