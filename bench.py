@@ -54,6 +54,8 @@ def parse():
                     help="time the full-scan construction instead of the candidate-list one")
     ap.add_argument("--no-full-scan", action="store_true",
                     help="skip the side measurement of the full-scan construction kernel")
+    ap.add_argument("--no-roulette", action="store_true",
+                    help="skip the RW / IR / AdaIR comparison on the bench workload")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched measurement (256 instances, n ~ U{100..2000}, m = n, bf16)")
     return ap.parse_args()
@@ -370,6 +372,8 @@ def run_native(args, w, dist):
         out["best_len_mean"] = {k: round(v, 6) for k, v in gaps.items()}
         out["best_len_protocol"] = f"mean over seeds 0..{args.gap_seeds - 1} after {w['iters']} iterations"
 
+    if dist.rank == 0 and not args.no_roulette:
+        out["roulette"] = run_roulette(B, torch, w, coords, seed)
     if dist.rank == 0 and not args.no_batched:
         out["batched"] = run_batched(B, torch, peak, value / dist.world if w["prec"] == "fp32" else None)
     if dist.rank == 0 and not args.no_e2e:
@@ -377,6 +381,36 @@ def run_native(args, w, dist):
     if dist.rank == 0 and not args.no_cpu_baseline and dist.world == 1:
         out["cpu_baseline"] = oracle_sample(w, coords, seed)
         out["cpu_baseline"].pop("_secs")
+    return out
+
+
+def run_roulette(B, torch, w, coords, seed, steps=10):
+    """The paper's selection ablation on the bench workload: time per
+    iteration and best length after the workload's iteration budget for the
+    roulette wheel, independent roulette and AdaIR (gamma 1.5 -> 0.5)."""
+    st = torch.cuda.Stream()
+    out = {}
+    for r in ("ir", "adair", "rw"):
+        kw = solver_kwargs(dict(w, adair=False), seed)
+        kw["roulette"] = r
+        if r == "adair":
+            kw.update(gamma_max=1.5, gamma_min=0.5, gamma_T=w["iters"])
+        s = B.Solver(coords, stream=st, **kw)
+        s.iterate(2)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            s.iterate(steps)
+            e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        s.iterate(max(0, w["iters"] - 2 - steps))
+        out[r] = {"ms_per_iter": round(ms, 3), "best_len_after_budget": s.best()[1]}
+        s.close()
+    out["protocol"] = (f"{steps} timed iterations after 2; best length after {w['iters']} iterations, "
+                       f"Philox seed {seed}; rw = exact-integer roulette wheel, one warp per ant")
     return out
 
 
