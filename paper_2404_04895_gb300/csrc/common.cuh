@@ -36,6 +36,34 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
   return c;
 }
 
+// The ten round keys of one Philox key, for callers that draw many blocks
+// under it (an ant's whole walk): the key additions leave the per-draw chain.
+struct PhiloxKeys {
+  uint2 k[10];
+};
+
+__device__ __forceinline__ PhiloxKeys philox_keys(uint2 k) {
+  PhiloxKeys ks;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    ks.k[r] = k;
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return ks;
+}
+
+__device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeys& ks) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a0 = c.x, a2 = c.z;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, a0), lo0 = 0xD2511F53u * a0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, a2), lo1 = 0xCD9E8D57u * a2;
+    c = make_uint4(hi1 ^ c.y ^ ks.k[r].x, lo1, hi0 ^ c.w ^ ks.k[r].y, lo0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
   return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
 }

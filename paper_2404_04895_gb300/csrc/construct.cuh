@@ -172,7 +172,7 @@ __device__ __forceinline__ ListRow load_list_row(const uint2* __restrict__ lists
 template <bool SPEC>
 __device__ __forceinline__ int list_rounds(const uint2* __restrict__ lists, const uint32_t* __restrict__ lkey,
                                            const ListRow& L, ListRow* spec, const uint32_t* __restrict__ svis,
-                                           uint2 key, uint32_t it, int k, int t, float& bs, int& bj) {
+                                           const PhiloxKeys& key, uint32_t it, int k, int t, float& bs, int& bj) {
   const int lane = threadIdx.x & 31;
   const uint2* __restrict__ lrow = lists + (size_t)L.row * kListMax;
   uint2 e = L.e, e_next = L.e_next;
@@ -297,6 +297,7 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
   };
 
   int cur = start_city(key, it, (uint32_t)k, n);
+  const PhiloxKeys ks = philox_keys(key);
   if (gl == 0) tour[0] = cur;
   mark(cur);
   if (use_list) {
@@ -322,7 +323,7 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
     //    column not scored yet
     if (use_list) {
       const ListRow L = load_list_row(lists, lkey, cur);
-      next = list_rounds<false>(lists, lkey, L, nullptr, svis, key, it, k, t, bs, bj);
+      next = list_rounds<false>(lists, lkey, L, nullptr, svis, ks, it, k, t, bs, bj);
     }
 
     if (next < 0) {  // full scan (seeded with the list's best candidate, if any)
@@ -376,7 +377,7 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
       const int j0 = (c * TPA + gl) * V + g * 4;
       const float4 p = MODE == MODE_DIRECT ? E::load_group(row, j0)
                                            : E::group_values(srow[c * TPA + gl], g);
-      const uint4 x = philox(make_uint4((uint32_t)(j0 >> 2), (uint32_t)t, (uint32_t)k, it), key);
+      const uint4 x = philox(make_uint4((uint32_t)(j0 >> 2), (uint32_t)t, (uint32_t)k, it), ks);
       if (!(nib & 1u)) better(__fmul_rn(uniform01(x.x), p.x), j0, bs, bj);
       if (!(nib & 2u)) better(__fmul_rn(uniform01(x.y), p.y), j0 + 1, bs, bj);
       if (!(nib & 4u)) better(__fmul_rn(uniform01(x.z), p.z), j0 + 2, bs, bj);

@@ -61,11 +61,11 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
   for (int q = lane; q < nwords; q += 32) svis[q] = 0u;
   __syncwarp();
   int cur = start_city(key, it, (uint32_t)k, n);
-  if (lane == 0) {
-    tour[0] = cur;
-    svis[cur >> 5] |= 1u << (cur & 31);
-  }
+  const PhiloxKeys ks = philox_keys(key);
+  if (lane == 0) svis[cur >> 5] |= 1u << (cur & 31);
   __syncwarp();
+  // the tour is written 32 steps at a time: lane (t mod 32) keeps step t's city
+  int tbuf = cur;
 
   ListRow lr, spec;
   lr.row = spec.row = -1;
@@ -76,7 +76,7 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
     int bj = 0x7FFFFFFF;
     int next = -1;
     auto score4 = [&](int j0, float4 p, uint32_t nib) {
-      const uint4 x = philox(make_uint4((uint32_t)(j0 >> 2), (uint32_t)t, (uint32_t)k, it), key);
+      const uint4 x = philox(make_uint4((uint32_t)(j0 >> 2), (uint32_t)t, (uint32_t)k, it), ks);
       if (!(nib & 1u)) better(__fmul_rn(uniform01(x.x), p.x), j0, bs, bj);
       if (!(nib & 2u)) better(__fmul_rn(uniform01(x.y), p.y), j0 + 1, bs, bj);
       if (!(nib & 4u)) better(__fmul_rn(uniform01(x.z), p.z), j0 + 2, bs, bj);
@@ -84,7 +84,7 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
     };
 
     // ---- list step
-    if (lists) next = list_rounds<true>(lists, lkey, lr, &spec, svis, key, it, k, t, bs, bj);
+    if (lists) next = list_rounds<true>(lists, lkey, lr, &spec, svis, ks, it, k, t, bs, bj);
 
     // ---- compact full scan
     if (next < 0) {
@@ -129,10 +129,12 @@ __device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, 
       if (lane == 0 && err) atomicExch(err, kErrConstruct);
       break;
     }
-    if (lane == 0) {
-      tour[t] = next;
-      svis[next >> 5] |= 1u << (next & 31);
+    if (lane == (t & 31)) tbuf = next;
+    if ((t & 31) == 31 || t == n - 1) {
+      const int tt = (t & ~31) + lane;
+      if (tt <= t) tour[tt] = tbuf;
     }
+    if (lane == 0) svis[next >> 5] |= 1u << (next & 31);
     __syncwarp();
     cur = next;
     // the next row's list: usually already in flight from the speculation
