@@ -167,8 +167,9 @@ __device__ __forceinline__ ListRow load_list_row(const uint2* __restrict__ lists
 // key exceeds both.  Returns the chosen column, or -1 when the list cannot
 // decide; bs/bj then hold the best unvisited listed candidate (bs < 0: none),
 // a threshold for the full scan.  SPEC: in the first round, also start
-// loading the list of the first unvisited entry -- the next city most of the
-// time -- into *spec (spec->row = -1 when there is none).
+// loading the lists of the first two unvisited entries -- one of them is the
+// next city about 9 steps in 10 -- into spec[0], spec[1] (row = -1 when
+// there is none).
 template <bool SPEC>
 __device__ __forceinline__ int list_rounds(const uint2* __restrict__ lists, const uint32_t* __restrict__ lkey,
                                            const ListRow& L, ListRow* spec, const uint32_t* __restrict__ svis,
@@ -188,9 +189,13 @@ __device__ __forceinline__ int list_rounds(const uint2* __restrict__ lists, cons
     const unsigned vm = __ballot_sync(ACO_FULL_MASK, valid);
     if (SPEC && r == 0) {
       const unsigned un = __ballot_sync(ACO_FULL_MASK, unvisited);
+      const unsigned un2 = un & (un - 1u);
       const int sj = __shfl_sync(ACO_FULL_MASK, j, un ? __ffs(un) - 1 : 0);
-      *spec = load_list_row(lists, lkey, sj);  // harmless when there is no candidate
-      if (!un) spec->row = -1;
+      const int sj2 = __shfl_sync(ACO_FULL_MASK, j, un2 ? __ffs(un2) - 1 : 0);
+      spec[0] = load_list_row(lists, lkey, sj);  // harmless when there is no candidate
+      spec[1] = load_list_row(lists, lkey, sj2);
+      if (!un) spec[0].row = -1;
+      if (!un2) spec[1].row = -1;
     }
     // every entry after this round has a value <= this round's last one
     const bool more = (vm >> 31) != 0u && r + 1 < kListMax / 32;
