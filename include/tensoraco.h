@@ -173,6 +173,19 @@ int aco_solver_device_state(aco_solver* s, float** tau, int* ld, int32_t** tours
 /* Iterations completed so far. */
 int aco_solver_iteration(aco_solver* s, uint32_t* it);
 
+/* Checkpoints.  A solver's state -- tau, the best tour and length, the
+ * iteration count, and its parameters -- as a host byte blob of
+ * aco_solver_state_bytes() bytes, ending in an FNV-1a 64-bit checksum.
+ * Everything else is derived (M_p and lists from tau, distances from the
+ * coordinates, random numbers from seed and counters), so a solver restored
+ * into one created with the same coordinates and parameters continues bit
+ * for bit as the saved one would.  aco_solver_load returns ACO_ERR_ARG for a
+ * blob of another size, format, checksum or parameter set; the solver is then
+ * unchanged.  Both synchronise the solver's stream. */
+int aco_solver_state_bytes(aco_solver* s, size_t* bytes);
+int aco_solver_save(aco_solver* s, void* host_buf, size_t bytes);
+int aco_solver_load(aco_solver* s, const void* host_buf, size_t bytes);
+
 /* Kernel timing probes.  When on, the solver records CUDA events around each
  * kernel of every iteration (inside its CUDA graph as well).  After an
  * iteration has been issued, aco_solver_kernel_ms() waits for it and writes

@@ -63,6 +63,9 @@ _SIGS = {
     "aco_solver_device_state": (i32, [v, C.POINTER(v), C.POINTER(i32), C.POINTER(v), C.POINTER(v),
                                       C.POINTER(v), C.POINTER(v)]),
     "aco_solver_iteration": (i32, [v, C.POINTER(u32)]),
+    "aco_solver_state_bytes": (i32, [v, v]),
+    "aco_solver_save": (i32, [v, v, sz]),
+    "aco_solver_load": (i32, [v, v, sz]),
     "aco_solver_set_profiling": (i32, [v, i32]),
     "aco_solver_kernel_ms": (i32, [v, v]),
     "aco_solver_set_shape": (i32, [v, i32, i32, i32]),
@@ -349,6 +352,20 @@ class Solver:
         call("aco_solver_kernel_ms", self._h, out.ctypes.data)
         return out
 
+    def state(self):
+        """The solver's checkpoint as bytes (tau, best tour/length, iteration, parameters)."""
+        nbytes = sz(0)
+        call("aco_solver_state_bytes", self._h, C.byref(nbytes))
+        buf = np.empty(nbytes.value, dtype=np.uint8)
+        call("aco_solver_save", self._h, buf.ctypes.data, nbytes.value)
+        return buf.tobytes()
+
+    def restore(self, blob):
+        """Restore a checkpoint taken from a solver with the same coordinates and parameters."""
+        buf = np.frombuffer(blob, dtype=np.uint8).copy()
+        call("aco_solver_load", self._h, buf.ctypes.data, buf.size)
+        return self
+
     def set_shape(self, warps=0, chunks=0, mode=0):
         call("aco_solver_set_shape", self._h, warps, chunks, mode)
         return self
@@ -449,6 +466,20 @@ class Batch:
         a, f, l = i32(0), sz(0), sz(0)
         call("aco_batch_info", self._h, C.byref(a), C.byref(f), C.byref(l))
         return dict(active=a.value, free_bytes=f.value, largest_block=l.value)
+
+    def state(self):
+        """The solver's checkpoint as bytes (tau, best tour/length, iteration, parameters)."""
+        nbytes = sz(0)
+        call("aco_solver_state_bytes", self._h, C.byref(nbytes))
+        buf = np.empty(nbytes.value, dtype=np.uint8)
+        call("aco_solver_save", self._h, buf.ctypes.data, nbytes.value)
+        return buf.tobytes()
+
+    def restore(self, blob):
+        """Restore a checkpoint taken from a solver with the same coordinates and parameters."""
+        buf = np.frombuffer(blob, dtype=np.uint8).copy()
+        call("aco_solver_load", self._h, buf.ctypes.data, buf.size)
+        return self
 
     def set_shape(self, warps=0, chunks=0, mode=0):
         call("aco_batch_set_shape", self._h, warps, chunks, mode)

@@ -623,6 +623,108 @@ int aco_solver_device_state(aco_solver* s, float** tau, int* ld, int32_t** tours
   return ACO_OK;
 }
 
+// ------------------------------------------------------------------ checkpoints
+// Blob: header, tau (fp32 n x n, dense), best tour (int32 n), FNV-1a 64 of
+// everything before it.  Everything else of the state is derived: M_p and the
+// lists from tau each iteration, distances and eta^beta from the coordinates,
+// random numbers from (seed, iteration, ant, step), so a restored run
+// continues bit for bit.
+namespace {
+struct CkptHeader {
+  char magic[8];      // "TACOCKP1"
+  uint32_t version;   // 1
+  uint32_t header_bytes;
+  aco_params params;  // must equal the restoring solver's
+  uint32_t it;
+  uint32_t has_best;
+  double best_len;
+};
+
+uint64_t fnv1a(const unsigned char* p, size_t bytes) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t q = 0; q < bytes; ++q) {
+    h ^= p[q];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+size_t ckpt_bytes(int n) {
+  return sizeof(CkptHeader) + sizeof(float) * (size_t)n * n + sizeof(int32_t) * (size_t)n + sizeof(uint64_t);
+}
+
+bool same_params(const aco_params& a, const aco_params& b) {
+  return a.n == b.n && a.m == b.m && a.alpha == b.alpha && a.beta == b.beta && a.rho == b.rho && a.Q == b.Q &&
+         a.tau0 == b.tau0 && a.seed == b.seed && a.prec == b.prec && a.roulette == b.roulette &&
+         a.deposit == b.deposit && a.gamma_max == b.gamma_max && a.gamma_min == b.gamma_min &&
+         a.gamma_T == b.gamma_T && a.topk == b.topk;
+}
+}  // namespace
+
+int aco_solver_state_bytes(aco_solver* s, size_t* bytes) {
+  if (!s || !bytes) return set_error(ACO_ERR_ARG, "NULL argument");
+  *bytes = ckpt_bytes(s->p.n);
+  return ACO_OK;
+}
+
+int aco_solver_save(aco_solver* s, void* host_buf, size_t bytes) {
+  if (!s || !host_buf) return set_error(ACO_ERR_ARG, "NULL argument");
+  const int n = s->p.n;
+  if (bytes < ckpt_bytes(n)) return set_error(ACO_ERR_ARG, "buffer holds %zu bytes; the state needs %zu", bytes, ckpt_bytes(n));
+  int rc = solver_sync_check(s);
+  if (rc) return rc;
+  unsigned char* out = static_cast<unsigned char*>(host_buf);
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "TACOCKP1", 8);
+  h.version = 1;
+  h.header_bytes = (uint32_t)sizeof(CkptHeader);
+  h.params = s->p;
+  h.it = s->it;
+  h.has_best = s->it > 0;
+  ACO_CUDA_TRY(cudaMemcpy(&h.best_len, s->best_len, 8, cudaMemcpyDeviceToHost));
+  std::memcpy(out, &h, sizeof(h));
+  float* tau = reinterpret_cast<float*>(out + sizeof(h));
+  ACO_CUDA_TRY(cudaMemcpy2D(tau, sizeof(float) * n, s->tau, sizeof(float) * s->ld, sizeof(float) * n, n,
+                            cudaMemcpyDeviceToHost));
+  int32_t* best = reinterpret_cast<int32_t*>(tau + (size_t)n * n);
+  ACO_CUDA_TRY(cudaMemcpy(best, s->best_tour, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+  const size_t body = ckpt_bytes(n) - sizeof(uint64_t);
+  const uint64_t sum = fnv1a(out, body);
+  std::memcpy(out + body, &sum, sizeof(sum));
+  return ACO_OK;
+}
+
+int aco_solver_load(aco_solver* s, const void* host_buf, size_t bytes) {
+  if (!s || !host_buf) return set_error(ACO_ERR_ARG, "NULL argument");
+  const int n = s->p.n;
+  if (bytes != ckpt_bytes(n)) return set_error(ACO_ERR_ARG, "checkpoint has %zu bytes; this solver's state has %zu", bytes, ckpt_bytes(n));
+  const unsigned char* in = static_cast<const unsigned char*>(host_buf);
+  CkptHeader h;
+  std::memcpy(&h, in, sizeof(h));
+  if (std::memcmp(h.magic, "TACOCKP1", 8) != 0 || h.version != 1 || h.header_bytes != sizeof(CkptHeader))
+    return set_error(ACO_ERR_ARG, "not a checkpoint of this format");
+  const size_t body = ckpt_bytes(n) - sizeof(uint64_t);
+  uint64_t sum = 0;
+  std::memcpy(&sum, in + body, sizeof(sum));
+  if (sum != fnv1a(in, body)) return set_error(ACO_ERR_ARG, "checkpoint checksum mismatch (corrupted)");
+  if (!same_params(h.params, s->p)) return set_error(ACO_ERR_ARG, "checkpoint parameters differ from the solver's");
+  int rc = solver_sync_check(s);
+  if (rc) return rc;
+  const float* tau = reinterpret_cast<const float*>(in + sizeof(h));
+  for (size_t q = 0; q < (size_t)n * n; ++q)
+    if (!(tau[q] >= 0.0f)) return set_error(ACO_ERR_ARG, "checkpoint tau entry %zu is negative or NaN", q);
+  const int32_t* best = reinterpret_cast<const int32_t*>(tau + (size_t)n * n);
+  ACO_CUDA_TRY(cudaMemcpy2D(s->tau, sizeof(float) * s->ld, tau, sizeof(float) * n, sizeof(float) * n, n,
+                            cudaMemcpyHostToDevice));
+  ACO_CUDA_TRY(cudaMemcpy(s->best_tour, best, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  const double bl = h.has_best ? h.best_len : INFINITY;
+  ACO_CUDA_TRY(cudaMemcpy(s->best_len, &bl, 8, cudaMemcpyHostToDevice));
+  ACO_CUDA_TRY(cudaMemcpy(s->it_dev, &h.it, 4, cudaMemcpyHostToDevice));
+  s->it = h.it;
+  return ACO_OK;
+}
+
 int aco_solver_iteration(aco_solver* s, uint32_t* it) {
   if (!s || !it) return set_error(ACO_ERR_ARG, "NULL argument");
   *it = s->it;

@@ -34,6 +34,8 @@ class Request:
     seed: int
     iters: int
     params: dict = dataclasses.field(default_factory=dict)
+    cancel_at: float = None  # seconds from the start of the trace; None: never
+    cancelled: bool = False
     admitted: float = None
     finished: float = None
     best_len: float = None
@@ -77,6 +79,10 @@ class Server:
         self.sleep = sleep
 
     def run(self, requests, realtime=True):
+        """Serve `requests`; returns (finished requests, wall seconds, batched
+        steps).  A request whose cancel_at has passed is dropped from the
+        queue, or, once admitted, removed between steps (its slot and memory
+        freed, no result); it is marked cancelled and not returned."""
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         active = {}
         done = []
@@ -84,6 +90,13 @@ class Server:
         steps = 0
         while pending or active:
             now = self.clock() - t0
+            # cancellations: queued requests leave the queue, admitted ones their slot
+            for r in [r for r in pending if r.cancel_at is not None and r.cancel_at <= now]:
+                r.cancelled = True
+                pending.remove(r)
+            for s in [s for s, r in active.items() if r.cancel_at is not None and r.cancel_at <= now]:
+                active.pop(s).cancelled = True
+                self.batch.remove(s)
             # admit arrived requests in order while they fit
             while pending and (pending[0].arrival <= now or not realtime):
                 r = pending[0]

@@ -96,3 +96,24 @@ def test_poisson_trace_shapes():
     assert all(r.m == min(r.n, 1024) for r in reqs)
     gaps = np.diff([r.arrival for r in reqs])
     assert np.all(gaps >= 0) and 0.005 < gaps.mean() < 0.05
+
+
+def test_cancellation_frees_slots_and_returns_no_result():
+    clock = FakeClock()
+    fb = FakeBatch(capacity=100)
+
+    class TickingBatch(FakeBatch):
+        def step(self, k):
+            super().step(k)
+            clock.t += 1.0          # one second per batched step
+
+    fb = TickingBatch(capacity=100)
+    reqs = [_req(0, 0.0, 60, 10), _req(1, 0.0, 60, 3), _req(2, 0.5, 30, 2)]
+    reqs[0].cancel_at = 2.5         # admitted, cancelled mid-run
+    reqs[2].cancel_at = 0.7         # cancelled while queued behind request 1
+    done, wall, steps = serve.Server(fb, clock=clock, sleep=clock.sleep).run(reqs)
+    assert [r.rid for r in done] == [1]
+    assert reqs[0].cancelled and reqs[2].cancelled and not reqs[1].cancelled
+    assert reqs[0].finished is None and reqs[0].tour is None
+    assert fb.used == 0 and not fb.slots           # every slot and byte returned
+    assert ("add", 2) not in fb.log and ("add", 3) not in fb.log
