@@ -371,6 +371,45 @@ static float exact_sum_f32(const double* x, size_t count) {
   return f;
 }
 
+// The exact sum of count doubles (finite, sum >= 0) rounded once to bfloat16
+// (8 significant bits, fp32's exponent range with subnormals down to 2^-133,
+// overflow past (2 - 2^-8) 2^127 to +inf; ties to even), returned as the fp32
+// value.  As for fp32: every bf16 value and half-way point is a double, so
+// rounding h = the nearest double to the sum gives the right answer unless h
+// is a half-way point itself, which the sign of the remainder then settles.
+static float exact_sum_bf16(const double* x, size_t count) {
+  std::vector<double> partials;
+  for (size_t q = 0; q < count; ++q) grow(partials, x[q]);
+  const double h = round_expansion(partials);
+  if (!(h > 0.0)) return 0.0f;
+  int e2;
+  std::frexp(h, &e2);                      // h = f 2^e2, f in [0.5, 1)
+  const int sh = std::max(e2 - 1, -126) - 7;  // exponent of the bf16 quantum at h
+  const double y = std::ldexp(h, -sh);     // exact
+  const double fl = std::floor(y);
+  double r;
+  if (y - fl == 0.5) {
+    std::vector<double> rest = partials;
+    grow(rest, -h);
+    double sign = 0.0;
+    for (double v : rest)
+      if (v != 0.0) sign = v;
+    if (sign > 0.0)
+      r = fl + 1.0;
+    else if (sign < 0.0)
+      r = fl;
+    else
+      r = std::fmod(fl, 2.0) == 0.0 ? fl : fl + 1.0;
+  } else {
+    r = std::nearbyint(y);  // round half to even (the default mode)
+  }
+  const double v = std::ldexp(r, sh);
+  if (v >= 0x1p128) return INFINITY;
+  return (float)v;
+}
+
+float orc_exact_sum_bf16(const double* x, int64_t count) { return exact_sum_bf16(x, (size_t)count); }
+
 // Eq. 2: the path and its one-step cyclic shift side by side, row t = (p_t, p_{t-1}).
 void orc_index_matrix(const int32_t* tour, int n, int32_t* I) {
   for (int t = 0; t < n; ++t) {
@@ -385,8 +424,24 @@ void orc_index_matrix(const int32_t* tour, int n, int32_t* I) {
 //   tau'_ij = fl32(keep * tau_ij) with keep = fl32(1 - rho)      (fp32 tensor)
 //   tau_ij <- tau'_ij + sum over paths of A^(k)_ij, the real sum rounded once
 //             to fp32 (ties to even); tau'_ij where no path has the edge.
+static void deposit_rounded(float* tau, int n, const int32_t* tours, const double* L, int m,
+                            float rho, float Q, bool bf16);
+
 void orc_deposit(float* tau, int n, const int32_t* tours, const double* L, int m,
                  float rho, float Q) {
+  deposit_rounded(tau, n, tours, L, m, rho, Q, false);
+}
+
+// As orc_deposit with M_tau stored in bfloat16: the same exact sum
+// fl32(keep * tau) + sum of c_k is rounded once to bf16; entries no path
+// uses become the bf16 rounding of fl32(keep * tau).
+void orc_deposit_tau_bf16(float* tau, int n, const int32_t* tours, const double* L, int m,
+                          float rho, float Q) {
+  deposit_rounded(tau, n, tours, L, m, rho, Q, true);
+}
+
+static void deposit_rounded(float* tau, int n, const int32_t* tours, const double* L, int m,
+                            float rho, float Q, bool bf16) {
   // every (entry, weight) pair, grouped by entry
   std::vector<std::pair<size_t, double>> items;
   items.reserve((size_t)2 * n * m);
@@ -406,13 +461,18 @@ void orc_deposit(float* tau, int n, const int32_t* tours, const double* L, int m
                    });
   const float keep = 1.0f - rho;
   for (size_t e = 0; e < (size_t)n * n; ++e) tau[e] = keep * tau[e];
+  std::vector<uint8_t> touched(bf16 ? (size_t)n * n : 0, 0);
   std::vector<double> group;
   for (size_t q = 0; q < items.size();) {
     const size_t e = items[q].first;
     group.assign(1, (double)tau[e]);
     while (q < items.size() && items[q].first == e) group.push_back(items[q++].second);
-    tau[e] = exact_sum_f32(group.data(), group.size());
+    tau[e] = bf16 ? exact_sum_bf16(group.data(), group.size()) : exact_sum_f32(group.data(), group.size());
+    if (bf16) touched[e] = 1;
   }
+  if (bf16)
+    for (size_t e = 0; e < (size_t)n * n; ++e)
+      if (!touched[e]) tau[e] = orc_from_bf16(orc_to_bf16(tau[e]));
 }
 
 // Sec. 2.3 (tensorization of ant paths): the solution set is sorted by
@@ -430,8 +490,16 @@ void orc_select_topk(const double* L, int m, int k, uint8_t* selected) {
 
 // Evaporation then the deposit of the k selected paths only (Sec. 2.3:
 // Delta M_tau sums A over the selected set P); every entry evaporates.
+static void deposit_topk_impl(float* tau, int n, const int32_t* tours, const double* L, int m,
+                              float rho, float Q, int k, bool bf16);
+
 void orc_deposit_topk(float* tau, int n, const int32_t* tours, const double* L, int m,
                       float rho, float Q, int k) {
+  deposit_topk_impl(tau, n, tours, L, m, rho, Q, k, false);
+}
+
+static void deposit_topk_impl(float* tau, int n, const int32_t* tours, const double* L, int m,
+                              float rho, float Q, int k, bool bf16) {
   std::vector<uint8_t> sel((size_t)m);
   orc_select_topk(L, m, k, sel.data());
   std::vector<int32_t> st;
@@ -441,7 +509,7 @@ void orc_deposit_topk(float* tau, int n, const int32_t* tours, const double* L, 
     st.insert(st.end(), tours + (size_t)q * n, tours + (size_t)(q + 1) * n);
     sl.push_back(L[q]);
   }
-  orc_deposit(tau, n, st.data(), sl.data(), (int)sl.size(), rho, Q);
+  deposit_rounded(tau, n, st.data(), sl.data(), (int)sl.size(), rho, Q, bf16);
 }
 
 double orc_exact_sum(const double* x, int64_t count) { return exact_sum(x, (size_t)count); }
@@ -504,7 +572,7 @@ void orc_run(const orc_params* prm, const double* D, const float* H, float* tau,
       *best_len = L[kb];
       std::memcpy(best_tour, tours.data() + (size_t)kb * n, sizeof(int32_t) * n);
     }
-    orc_deposit_topk(tau, n, tours.data(), L.data(), m, prm->rho, prm->Q, prm->topk);
+    deposit_topk_impl(tau, n, tours.data(), L.data(), m, prm->rho, prm->Q, prm->topk, prm->tau_bf16 != 0);
   }
   if (last_tours) std::memcpy(last_tours, tours.data(), sizeof(int32_t) * tours.size());
   if (last_L) std::memcpy(last_L, L.data(), sizeof(double) * L.size());

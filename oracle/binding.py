@@ -15,7 +15,7 @@ class OrcParams(C.Structure):
     _fields_ = [("n", C.c_int), ("m", C.c_int), ("alpha", C.c_int), ("beta", C.c_int),
                 ("rho", C.c_float), ("Q", C.c_float), ("seed", C.c_uint64),
                 ("prec", C.c_int), ("adair", C.c_int), ("gamma_max", C.c_float),
-                ("gamma_min", C.c_float), ("gamma_T", C.c_int), ("topk", C.c_int), ("rw", C.c_int)]
+                ("gamma_min", C.c_float), ("gamma_T", C.c_int), ("topk", C.c_int), ("rw", C.c_int), ("tau_bf16", C.c_int)]
 
 
 def _p(a):
@@ -56,6 +56,8 @@ def lib():
             "orc_tour_lengths": (None, [v, C.c_int, v, C.c_int, v]),
             "orc_exact_sum": (f64, [v, C.c_int64]),
             "orc_exact_sum_f32": (C.c_float, [v, C.c_int64]),
+            "orc_exact_sum_bf16": (C.c_float, [v, C.c_int64]),
+            "orc_deposit_tau_bf16": (None, [v, C.c_int, v, v, C.c_int, C.c_float, C.c_float]),
             "orc_select_topk": (None, [v, C.c_int, C.c_int, v]),
             "orc_rw_quantum": (u64, [C.c_float, C.c_int]),
             "orc_select_rw": (i32, [v, v, C.c_int, u64, u32, u32, u32]),
@@ -224,6 +226,20 @@ def exact_sum_f32(x):
     return np.float32(lib().orc_exact_sum_f32(_p(x), x.size))
 
 
+def exact_sum_bf16(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return np.float32(lib().orc_exact_sum_bf16(_p(x), x.size))
+
+
+def deposit_tau_bf16(tau, tours, L, rho, Q):
+    tau = np.array(tau, dtype=np.float32, copy=True, order="C")
+    tours = np.ascontiguousarray(tours, dtype=np.int32)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    m, n = tours.shape
+    lib().orc_deposit_tau_bf16(_p(tau), n, _p(tours), _p(L), m, rho, Q)
+    return tau
+
+
 def index_matrix(tour):
     tour = np.ascontiguousarray(tour, dtype=np.int32)
     I = np.empty((tour.size, 2), dtype=np.int32)
@@ -298,15 +314,18 @@ class State:
 
     def __init__(self, xy, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec=FP32,
                  adair=False, gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0, topk=0,
-                 rw=False):
+                 rw=False, tau_bf16=False):
         self.xy = np.ascontiguousarray(xy, dtype=np.float32)
         n = self.xy.shape[0]
         self.prm = OrcParams(n=n, m=m, alpha=alpha, beta=beta, rho=rho, Q=Q, seed=seed,
                              prec=prec, adair=int(adair), gamma_max=gamma_max,
-                             gamma_min=gamma_min, gamma_T=gamma_T, topk=topk, rw=int(rw))
+                             gamma_min=gamma_min, gamma_T=gamma_T, topk=topk, rw=int(rw),
+                             tau_bf16=int(tau_bf16))
         self.D = distances(self.xy)
         self.H = heuristic(self.D, beta)
         self.tau = init_tau(n, tau0)
+        if tau_bf16:  # tau0 stored in bfloat16
+            self.tau = (to_bf16(self.tau).astype(np.uint32) << 16).view(np.float32).reshape(n, n)
         self.it = 0
         self.best_tour = np.zeros(n, dtype=np.int32)
         self.best_len = np.array([math.inf], dtype=np.float64)

@@ -120,12 +120,18 @@ void orc_tour_lengths(const double* D, int n, const int32_t* tours, int m, doubl
 /* exact sum of count doubles rounded once to fp64 / to fp32 (ties to even) */
 double orc_exact_sum(const double* x, int64_t count);
 float orc_exact_sum_f32(const double* x, int64_t count);
+/* ... rounded once to bfloat16 (returned as its fp32 value); sums >= 0 */
+float orc_exact_sum_bf16(const double* x, int64_t count);
 
 /* ---- Sec. 2.3: index matrix, increment matrix, evaporation + deposit ---- */
 /* I of one tour (Eq. 2): rows (p_t, p_{t-1}) with cyclic predecessor; out n x 2 */
 void orc_index_matrix(const int32_t* tour, int n, int32_t* I);
 void orc_deposit(float* tau, int n, const int32_t* tours, const double* L, int m,
                  float rho, float Q);
+/* orc_deposit with M_tau stored in bfloat16: the exact sum is rounded once to
+ * bf16, untouched entries become bf16(fl32(keep * tau)). */
+void orc_deposit_tau_bf16(float* tau, int n, const int32_t* tours, const double* L, int m,
+                          float rho, float Q);
 /* Sec. 2.3: sort by length (ascending, ties by ant index), select the first
  * k paths (k <= 0 or k >= m: all); deposit from the selected paths only. */
 void orc_select_topk(const double* L, int m, int k, uint8_t* selected);
@@ -149,6 +155,7 @@ typedef struct {
   int gamma_T;       /* schedule length */
   int topk;          /* paths that deposit: 0 = all (Ant System), else the k shortest */
   int rw;            /* 1: roulette-wheel construction instead of IR / AdaIR */
+  int tau_bf16;      /* 1: M_tau stored in bfloat16 (the run's tau holds bf16 values) */
 } orc_params;
 
 /* Runs iterations it0 .. it0+iters-1 in place on tau (n x n) and on the best

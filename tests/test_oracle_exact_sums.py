@@ -161,3 +161,74 @@ def test_tour_length_blocked_error_bound(orc):
             edges = [D[p[t], p[(t + 1) % n]] for t in range(n)]
             exact = math.fsum(edges)
             assert abs(L[k] - exact) <= (32 + n / 32 + 2) * u * exact
+
+
+def _rnbf16(x: Fraction) -> np.float32:
+    """Nearest bfloat16 to the rational x >= 0 (ties to even), as fp32."""
+    if x >= Fraction(2) ** 128 - Fraction(2) ** 119:
+        return np.float32(np.inf)
+    if x == 0:
+        return np.float32(0)
+    e = math.floor(math.log2(x)) if x >= Fraction(2) ** -126 else -126
+    while Fraction(2) ** e > x:          # guard the float log2 against rounding
+        e -= 1
+    while Fraction(2) ** (e + 1) <= x and e >= -126:
+        e += 1
+    q = Fraction(2) ** (max(e, -126) - 7)
+    lo = (x // q) * q
+    hi = lo + q
+    if x - lo < hi - x:
+        r = lo
+    elif hi - x < x - lo:
+        r = hi
+    else:
+        r = lo if (lo / q) % 2 == 0 else hi
+    return np.float32(float(r))
+
+
+def test_exact_sum_bf16_matches_rational(orc):
+    rng = np.random.default_rng(16)
+    cases = []
+    for _ in range(3000):
+        k = int(rng.integers(1, 10))
+        kind = int(rng.integers(0, 4))
+        if kind == 0:
+            x = rng.uniform(1e-4, 2.0, size=k)
+        elif kind == 1:
+            x = np.exp(rng.normal(0, 20, size=k).clip(-700, 80))
+        elif kind == 2:  # a bf16 value plus half its quantum, and a push either way or none
+            bits = np.array([rng.uniform(0.5, 4.0)], np.float32).view(np.uint32) & np.uint32(0xFFFF0000)
+            a = float(bits.view(np.float32)[0])                  # a bf16 value
+            half = 2.0 ** (math.floor(math.log2(a)) - 8)         # half its quantum
+            x = np.array([a, half, [0.0, 2.0 ** -60, 2.0 ** -20][int(rng.integers(0, 3))]])
+        else:  # the subnormal bf16 range
+            x = rng.uniform(0, 2.0 ** -126, size=k)
+        cases.append(np.asarray(x, np.float64))
+    for x in cases:
+        exact = sum((Fraction(float(v)) for v in x), Fraction(0))
+        got = orc.exact_sum_bf16(x)
+        ref = _rnbf16(exact)
+        assert got == ref, (x.tolist(), got, ref)
+        assert (np.array(got, np.float32).view(np.uint32) & 0xFFFF) == 0   # a bf16 value
+
+
+def test_deposit_tau_bf16_is_rounded_exact_sum(orc):
+    rng = np.random.default_rng(17)
+    for trial in range(4):
+        n, m = int(rng.integers(3, 8)), int(rng.integers(1, 6))
+        tours = np.stack([rng.permutation(n) for _ in range(m)]).astype(np.int32)
+        L = rng.uniform(0.5, 3.0, size=m)
+        rho, Q = np.float32(rng.uniform(0, 1)), np.float32(rng.uniform(0.1, 5))
+        tau0 = (orc.to_bf16(rng.uniform(0.01, 2, size=(n, n)).astype(np.float32)).astype(np.uint32) << 16).view(np.float32)
+        got = orc.deposit_tau_bf16(tau0, tours, L, float(rho), float(Q))
+        keep = np.float32(np.float32(1) - rho)
+        acc = [[Fraction(float(np.float32(keep * tau0[i, j]))) for j in range(n)] for i in range(n)]
+        for k in range(m):
+            w = Fraction(float(np.float64(Q) / L[k]))
+            for t in range(n):
+                a, b = int(tours[k, t]), int(tours[k, t - 1])
+                acc[a][b] += w
+                acc[b][a] += w
+        for i in range(n):
+            for j in range(n):
+                assert got[i, j] == _rnbf16(acc[i][j]), (trial, i, j)
