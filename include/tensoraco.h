@@ -89,6 +89,12 @@ int aco_set_variant(int roulette, float gamma_max, float gamma_min, int T);
  * Scores are always fp32, tau always fp32.  Takes effect at the next iteration. */
 int aco_set_precision(int prec);
 
+/* Storage precision of M_tau: ACO_FP32 (default) or ACO_BF16.  With BF16 the
+ * deposit rounds fl32(keep * tau) + the exact sum of the weights once to bf16
+ * (entries no path uses: bf16(fl32(keep * tau))), tau starts at bf16(tau0),
+ * M_p widens it exactly.  Needs ACO_DEPOSIT_DET.  Next aco_init. */
+int aco_set_tau_precision(int prec);
+
 /* Deposit summation: ACO_DEPOSIT_DET gives every entry the exact sum of its
  * paths' weights added to the evaporated value, rounded once to fp32 (no
  * order; reproducible bit for bit); ACO_DEPOSIT_ATOMIC adds fl32(Q/L_k) with
@@ -147,6 +153,8 @@ typedef struct {
   int cand_lists;           /* 1: candidate-list fast path (exact), 0: full scan only */
   int topk;                 /* paths that deposit (Sec. 2.3): 0 = all (Ant System), else the
                                topk shortest (ties: lower ant index); >= m means all */
+  int tau_prec;             /* storage of M_tau: ACO_FP32 (default) or ACO_BF16 (deterministic
+                               deposit only; not in batches) */
 } aco_params;
 
 /* Fill *p with defaults: alpha 1, beta 2, rho 0.5, Q 1, tau0 1, seed 0, FP32,

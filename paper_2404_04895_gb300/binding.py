@@ -31,7 +31,8 @@ class Params(C.Structure):
                 ("rho", C.c_float), ("Q", C.c_float), ("tau0", C.c_float),
                 ("seed", C.c_uint64), ("prec", C.c_int), ("roulette", C.c_int),
                 ("deposit", C.c_int), ("gamma_max", C.c_float), ("gamma_min", C.c_float),
-                ("gamma_T", C.c_int), ("cand_lists", C.c_int), ("topk", C.c_int)]
+                ("gamma_T", C.c_int), ("cand_lists", C.c_int), ("topk", C.c_int),
+                ("tau_prec", C.c_int)]
 
 
 _lib = None
@@ -43,6 +44,7 @@ _SIGS = {
     "aco_set_precision": (i32, [i32]),
     "aco_set_deposit": (i32, [i32]),
     "aco_set_deposit_topk": (i32, [i32]),
+    "aco_set_tau_precision": (i32, [i32]),
     "aco_op_select_topk": (i32, [v, i32, i32, v, v]),
     "aco_iterate": (i32, [i32]),
     "aco_best": (i32, [v, v]),
@@ -276,7 +278,7 @@ class Solver:
 
     def __init__(self, coords, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec="fp32",
                  roulette="ir", deposit="det", gamma_max=1.5, gamma_min=0.5, gamma_T=100,
-                 tau0=1.0, workspace="torch", stream=None, cand_lists=True, topk=0):
+                 tau0=1.0, workspace="torch", stream=None, cand_lists=True, topk=0, tau_prec="fp32"):
         import torch
         xy = _host(coords, np.float32)
         n = xy.shape[0]
@@ -290,6 +292,7 @@ class Solver:
         p.gamma_max, p.gamma_min, p.gamma_T = gamma_max, gamma_min, gamma_T
         p.cand_lists = int(cand_lists)
         p.topk = int(topk)
+        p.tau_prec = PREC[tau_prec] if isinstance(tau_prec, str) else tau_prec
         self.params = p
         self.n, self.m = n, m
         self.stream = stream
@@ -385,7 +388,7 @@ class Solver:
 
 def make_params(n, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec="fp32", roulette="ir",
                 deposit="det", gamma_max=1.5, gamma_min=0.5, gamma_T=100, tau0=1.0, cand_lists=True,
-                topk=0):
+                topk=0, tau_prec="fp32"):
     p = Params()
     call("aco_params_default", C.byref(p))
     p.n, p.m, p.alpha, p.beta = n, m, alpha, beta
@@ -396,6 +399,7 @@ def make_params(n, m, alpha=1, beta=2, rho=0.5, Q=1.0, seed=0, prec="fp32", roul
     p.gamma_max, p.gamma_min, p.gamma_T = gamma_max, gamma_min, gamma_T
     p.cand_lists = int(cand_lists)
     p.topk = int(topk)
+    p.tau_prec = PREC[tau_prec] if isinstance(tau_prec, str) else tau_prec
     return p
 
 

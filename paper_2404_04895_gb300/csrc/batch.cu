@@ -452,6 +452,7 @@ int aco_batch_add(aco_batch* b, const float* coords_host, const aco_params* p, i
   if (p->prec != b->prec) return set_error(ACO_ERR_ARG, "instance precision %d differs from the batch's %d", p->prec, b->prec);
   if (iters_budget < 0) return set_error(ACO_ERR_ARG, "iters_budget must be >= 0");
   if (p->roulette == ACO_RW) return set_error(ACO_ERR_UNSUPPORTED, "batches run IR / AdaIR instances only");
+  if (p->tau_prec != ACO_FP32) return set_error(ACO_ERR_UNSUPPORTED, "batches store tau in fp32");
   int q = 0;
   while (q < (int)b->slots.size() && b->slots[q].used) ++q;
   if (q == (int)b->slots.size()) return set_error(ACO_ERR_OOM, "all %d batch slots are in use", q);

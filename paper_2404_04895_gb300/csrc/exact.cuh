@@ -158,55 +158,70 @@ ACO_HD bool any_below128(uint64_t hi, uint64_t lo, int p) {
   return (lo << (64 - p)) != 0ull;
 }
 
-// The fp32 nearest to tp + (w0 + w1 2^24 + w2 2^48) 2^E0 (ties to even), for
-// tp >= 0 (+inf allowed) and an exact nonnegative fixed-point sum.
-ACO_HD float round_sum_f32(float tp, uint64_t w0, uint64_t w1, uint64_t w2, int E0) {
+// The number nearest to tp + (w0 + w1 2^24 + w2 2^48) 2^E0 (ties to even) in
+// a binary format with MB significant bits and fp32's exponent range (MB =
+// 24: fp32; MB = 8: bfloat16), returned as its fp32 bit pattern, for tp >= 0
+// (+inf allowed) and an exact nonnegative fixed-point sum.
+template <int MB>
+ACO_HD uint32_t round_sum_bits(float tp, uint64_t w0, uint64_t w1, uint64_t w2, int E0) {
+  constexpr int LSB_MIN = -126 - (MB - 1);  // exponent of the smallest subnormal
   uint64_t ah = 0ull, al = w0;
   add128(&ah, &al, w1 >> 40, w1 << 24);
   add128(&ah, &al, w2 >> 16, w2 << 48);
-  if ((ah | al) == 0ull) return tp;
   const uint32_t tb = bits_of(tp);
+  if ((ah | al) == 0ull && MB == 24) return tb;
   const int teb = (int)(tb >> 23);
-  if (teb >= 255) return tp;  // +inf stays +inf
+  if (teb >= 255) return tb;  // +inf stays +inf
   const uint64_t mt = (uint64_t)(tb & 0x7FFFFFu) | (teb ? 0x800000ull : 0ull);
+  if ((ah | al) == 0ull && mt == 0ull) return 0u;
   const int et = (teb ? teb : 1) - 150;
   // leading-bit exponent of the larger operand; window LSB 100 places below it
-  int T = top128(ah, al) + E0;
+  int T = (ah | al) ? top128(ah, al) + E0 : -100000;
   if (mt) {
     const int tt = 63 - clz64(mt) + et;
     T = tt > T ? tt : T;
   }
   const int base = T - 100;
   bool sticky = false;
-  uint64_t sh, sl;
-  shift128(ah, al, E0 - base, &sh, &sl, &sticky);
+  uint64_t sh = 0ull, sl = 0ull;
+  if (ah | al) shift128(ah, al, E0 - base, &sh, &sl, &sticky);
   if (mt) {
     uint64_t mh, ml;
     shift128(0ull, mt, et - base, &mh, &ml, &sticky);
     add128(&sh, &sl, mh, ml);
   }
-  // keep the bits from position r up: 24 significant bits, or down to 2^-149
+  // keep the bits from position r up: MB significant bits, or down to 2^LSB_MIN
   const int top = top128(sh, sl);
-  int r = top - 23;
-  if (-149 - base > r) r = -149 - base;
-  if (r > 128) return 0.0f;  // far below the smallest subnormal
+  int r = top - (MB - 1);
+  if (LSB_MIN - base > r) r = LSB_MIN - base;
+  if (r > 128) return 0u;  // far below the smallest subnormal
   uint64_t mant_h, mant_l;
   bool dummy = false;
   shift128(sh, sl, -r, &mant_h, &mant_l, &dummy);
-  uint64_t mant = mant_l;  // < 2^24
+  uint64_t mant = mant_l;  // < 2^MB
   const uint64_t round_bit = r >= 1 ? bit128(sh, sl, r - 1) : 0ull;
   const bool below = sticky || any_below128(sh, sl, r - 1);
   if (round_bit && (below || (mant & 1ull))) mant += 1ull;
   int e_lsb = r + base;  // exponent of the kept LSB
-  if (mant >> 24) {      // carried into a 25th bit
+  if (mant >> MB) {      // carried into one more bit
     mant >>= 1;
     e_lsb += 1;
   }
-  if (mant == 0ull) return 0.0f;
-  if (mant < 0x800000ull) return float_of((uint32_t)mant);  // subnormal (e_lsb = -149)
-  const int E = e_lsb + 150;                                // biased exponent
-  if (E >= 255) return float_of(0x7F800000u);
-  return float_of(((uint32_t)E << 23) | (uint32_t)(mant & 0x7FFFFFull));
+  if (mant == 0ull) return 0u;
+  if (mant < (1ull << (MB - 1))) return (uint32_t)(mant << (LSB_MIN + 149));  // subnormal (e_lsb = LSB_MIN)
+  const int E = e_lsb + (MB - 1) + 127;                                        // biased exponent
+  if (E >= 255) return 0x7F800000u;
+  return ((uint32_t)E << 23) | ((uint32_t)(mant & ((1ull << (MB - 1)) - 1ull)) << (24 - MB));
+}
+
+// The fp32 nearest to tp + (w0 + w1 2^24 + w2 2^48) 2^E0 (ties to even).
+ACO_HD float round_sum_f32(float tp, uint64_t w0, uint64_t w1, uint64_t w2, int E0) {
+  return float_of(round_sum_bits<24>(tp, w0, w1, w2, E0));
+}
+
+// The bfloat16 nearest to the same sum (ties to even), as its 16-bit pattern.
+ACO_HD uint32_t round_sum_bf16(float tp, uint64_t w0, uint64_t w1, uint64_t w2, int E0) {
+  return round_sum_bits<8>(tp, w0, w1, w2, E0) >> 16;
 }
 
 }  // namespace aco

@@ -95,9 +95,11 @@ int prepare_kernels();  // once per process: shared-memory opt-ins (not during c
 int launch_heuristic(const float* xy, int n, int beta, double* D, float* H, int ld,
                      cudaStream_t st);
 int launch_fill(float* a, int n, int ld, float v, cudaStream_t st);
-int launch_build_P(const float* tau, const float* H, int n, int ld, int alpha, float inv_gamma,
+// tau stored in fp32 (tau_prec ACO_FP32) or bfloat16 (ACO_BF16), leading dimension ld
+int launch_build_P(const void* tau, int tau_prec, const float* H, int n, int ld, int alpha, float inv_gamma,
                    const float* inv_gamma_dev, const uint32_t* it_dev, int n_sched, int prec,
                    void* P, cudaStream_t st);
+int launch_fill_tau(void* tau, int tau_prec, int n, int ld, float v, cudaStream_t st);
 int launch_tour_length(const double* D, int n, const int32_t* tours, int m, float Q,
                        double* L, double* c, int32_t* nbr, cudaStream_t st);
 // best also keeps only the topk shortest paths' weights in c (c non-null,
@@ -108,7 +110,7 @@ int launch_best(const double* L, const int32_t* tours, int n, int m, int32_t* be
 int launch_select_topk(const double* L, int m, int k, double* c, cudaStream_t st);
 // dep null: every CTA derives the scaling from c; err (nullable) gets
 // kErrDepositRange when the weights cannot be summed exactly
-int launch_deposit(float* tau, int n, int ld, const int32_t* nbr, const double* c, int m,
+int launch_deposit(void* tau, int tau_prec, int n, int ld, const int32_t* nbr, const double* c, int m,
                    float rho, const int2* dep, int32_t* err, cudaStream_t st);
 int launch_deposit_atomic(float* tau, int n, int ld, const int32_t* tours, const double* c,
                           int m, float rho, cudaStream_t st);

@@ -37,6 +37,12 @@ __global__ void heuristic_kernel(const float* __restrict__ xy, int n, int beta,
   H[(size_t)i * ld + j] = h;
 }
 
+__global__ void fill_u16_kernel(unsigned short* __restrict__ a, size_t count, unsigned short v) {
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
+       q += (size_t)gridDim.x * blockDim.x)
+    a[q] = v;
+}
+
 __global__ void fill_kernel(float* __restrict__ a, size_t count, float v) {
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < count;
        q += (size_t)gridDim.x * blockDim.x)
@@ -46,8 +52,8 @@ __global__ void fill_kernel(float* __restrict__ a, size_t count, float v) {
 // ---------------------------------------------------------------------------
 // Single-instance wrappers around the device functions of steps.cuh.
 // ---------------------------------------------------------------------------
-template <int PREC>
-__global__ void __launch_bounds__(256) build_P_kernel(const float* __restrict__ tau,
+template <int PREC, bool TB>
+__global__ void __launch_bounds__(256) build_P_kernel(const void* __restrict__ tau,
                                                       const float* __restrict__ H, int n, int ld,
                                                       int alpha, float inv_gamma_arg,
                                                       const float* __restrict__ inv_gamma_dev,
@@ -61,8 +67,8 @@ __global__ void __launch_bounds__(256) build_P_kernel(const float* __restrict__ 
     inv_gamma = inv_gamma_dev[it < (uint32_t)n_sched ? it : (uint32_t)(n_sched - 1)];
   }
   const size_t eb = PREC == ACO_FP32 ? 4 : 2;
-  build_P_row<PREC>(tau + (size_t)i * ld, H + (size_t)i * ld, n, ld, i, alpha, inv_gamma,
-                    static_cast<char*>(Pv) + (size_t)i * ld * eb, red);
+  build_P_row<PREC, TB>(static_cast<const char*>(tau) + (size_t)i * ld * (TB ? 2 : 4), H + (size_t)i * ld, n,
+                        ld, i, alpha, inv_gamma, static_cast<char*>(Pv) + (size_t)i * ld * eb, red);
 }
 
 template <int PREC>
@@ -110,7 +116,8 @@ __global__ void __launch_bounds__(1024) best_kernel(const double* __restrict__ L
 
 // One CTA per row.  The weights' scaling comes from dep (written by the best
 // kernel) or, when dep is null, is derived by every CTA from c itself.
-__global__ void __launch_bounds__(kDepThreads) deposit_kernel(float* __restrict__ tau, int n, int ld,
+template <bool TB>
+__global__ void __launch_bounds__(kDepThreads) deposit_kernel(void* __restrict__ tau, int n, int ld,
                                                               const int32_t* __restrict__ nbr,
                                                               const double* __restrict__ c, int m,
                                                               float keep, const int2* __restrict__ dep,
@@ -125,8 +132,8 @@ __global__ void __launch_bounds__(kDepThreads) deposit_kernel(float* __restrict_
     if (d.y == kDepBad && blockIdx.x == 0 && threadIdx.x == 0 && err) atomicExch(err, kErrDepositRange);
   }
   const int a = blockIdx.x;
-  deposit_row_exact(tau + (size_t)a * ld, n, reinterpret_cast<const int2*>(nbr) + (size_t)a * m, c, m,
-                    keep, d.x, d.y, cap, smem);
+  deposit_row_exact<TB>(static_cast<char*>(tau) + (size_t)a * ld * (TB ? 2 : 4), n,
+                        reinterpret_cast<const int2*>(nbr) + (size_t)a * m, c, m, keep, d.x, d.y, cap, smem);
 }
 
 // tau <- fl32(keep * tau), keep = fl32(1 - rho): evaporation in fp32
@@ -188,6 +195,15 @@ int launch_heuristic(const float* xy, int n, int beta, double* D, float* H, int 
   return check_launch("heuristic_kernel");
 }
 
+int launch_fill_tau(void* tau, int tau_prec, int n, int ld, float v, cudaStream_t st) {
+  if (tau_prec != ACO_BF16) return launch_fill(static_cast<float*>(tau), n, ld, v, st);
+  const size_t count = (size_t)n * ld;
+  const int blocks = (int)std::min<size_t>((count + 255) / 256, 152 * 16);
+  fill_u16_kernel<<<blocks, 256, 0, st>>>(static_cast<unsigned short*>(tau), count,
+                                          __bfloat16_as_ushort(__float2bfloat16_rn(v)));
+  return check_launch("fill_u16_kernel");
+}
+
 int launch_fill(float* a, int n, int ld, float v, cudaStream_t st) {
   const size_t count = (size_t)n * ld;
   const int blocks = (int)std::min<size_t>((count + 255) / 256, 152 * 16);
@@ -195,25 +211,33 @@ int launch_fill(float* a, int n, int ld, float v, cudaStream_t st) {
   return check_launch("fill_kernel");
 }
 
-int launch_build_P(const float* tau, const float* H, int n, int ld, int alpha, float inv_gamma,
+int launch_build_P(const void* tau, int tau_prec, const float* H, int n, int ld, int alpha, float inv_gamma,
                    const float* inv_gamma_dev, const uint32_t* it_dev, int n_sched, int prec,
                    void* P, cudaStream_t st) {
+  const bool tb = tau_prec == ACO_BF16;
+#define ACO_BUILD_P(PR)                                                                                  \
+  do {                                                                                                   \
+    if (tb)                                                                                              \
+      build_P_kernel<PR, true><<<n, 256, 0, st>>>(tau, H, n, ld, alpha, inv_gamma, inv_gamma_dev, it_dev, \
+                                                  n_sched, P);                                           \
+    else                                                                                                 \
+      build_P_kernel<PR, false><<<n, 256, 0, st>>>(tau, H, n, ld, alpha, inv_gamma, inv_gamma_dev,       \
+                                                   it_dev, n_sched, P);                                  \
+  } while (0)
   switch (prec) {
     case ACO_FP32:
-      build_P_kernel<ACO_FP32><<<n, 256, 0, st>>>(tau, H, n, ld, alpha, inv_gamma, inv_gamma_dev,
-                                                 it_dev, n_sched, P);
+      ACO_BUILD_P(ACO_FP32);
       break;
     case ACO_BF16:
-      build_P_kernel<ACO_BF16><<<n, 256, 0, st>>>(tau, H, n, ld, alpha, inv_gamma, inv_gamma_dev,
-                                                 it_dev, n_sched, P);
+      ACO_BUILD_P(ACO_BF16);
       break;
     case ACO_FP16:
-      build_P_kernel<ACO_FP16><<<n, 256, 0, st>>>(tau, H, n, ld, alpha, inv_gamma, inv_gamma_dev,
-                                                 it_dev, n_sched, P);
+      ACO_BUILD_P(ACO_FP16);
       break;
     default:
       return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
   }
+#undef ACO_BUILD_P
   return check_launch("build_P_kernel");
 }
 
@@ -254,17 +278,22 @@ int launch_select_topk(const double* L, int m, int k, double* c, cudaStream_t st
 }
 
 int prepare_deposit() {
-  ACO_CUDA_TRY(cudaFuncSetAttribute(deposit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  ACO_CUDA_TRY(cudaFuncSetAttribute(deposit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)deposit_smem_bytes(ACO_MAX_N, kDepCap)));
+  ACO_CUDA_TRY(cudaFuncSetAttribute(deposit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)deposit_smem_bytes(ACO_MAX_N, kDepCap)));
   return ACO_OK;
 }
 
-int launch_deposit(float* tau, int n, int ld, const int32_t* nbr, const double* c, int m,
+int launch_deposit(void* tau, int tau_prec, int n, int ld, const int32_t* nbr, const double* c, int m,
                    float rho, const int2* dep, int32_t* err, cudaStream_t st) {
   const int cap = deposit_cap(n, m);
   const size_t smem = deposit_smem_bytes(n, cap);
   const float keep = 1.0f - rho;
-  deposit_kernel<<<n, kDepThreads, smem, st>>>(tau, n, ld, nbr, c, m, keep, dep, cap, err);
+  if (tau_prec == ACO_BF16)
+    deposit_kernel<true><<<n, kDepThreads, smem, st>>>(tau, n, ld, nbr, c, m, keep, dep, cap, err);
+  else
+    deposit_kernel<false><<<n, kDepThreads, smem, st>>>(tau, n, ld, nbr, c, m, keep, dep, cap, err);
   return check_launch("deposit_kernel");
 }
 

@@ -80,5 +80,5 @@ extern "C" int aco_op_deposit_tours_noalloc(float* tau_dev, int n, int ld, const
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc = launch_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c, nbr, st);
   if (rc) return rc;
-  return launch_deposit(tau_dev, n, ld, nbr, c, m, rho, nullptr, nullptr, st);
+  return launch_deposit(tau_dev, ACO_FP32, n, ld, nbr, c, m, rho, nullptr, nullptr, st);
 }

@@ -171,6 +171,10 @@ static int validate(const aco_params* p) {
   if (!(p->Q > 0.0f) || !std::isfinite(p->Q)) return set_error(ACO_ERR_ARG, "Q must be finite and > 0");
   if (!(p->tau0 > 0.0f) || !std::isfinite(p->tau0)) return set_error(ACO_ERR_ARG, "tau0 must be finite and > 0");
   if (p->topk < 0) return set_error(ACO_ERR_ARG, "topk=%d must be >= 0 (0: every path deposits)", p->topk);
+  if (p->tau_prec != ACO_FP32 && p->tau_prec != ACO_BF16)
+    return set_error(ACO_ERR_UNSUPPORTED, "tau is stored in fp32 or bf16 (tau_prec %d)", p->tau_prec);
+  if (p->tau_prec == ACO_BF16 && p->deposit != ACO_DEPOSIT_DET)
+    return set_error(ACO_ERR_UNSUPPORTED, "bf16 tau needs the deterministic deposit");
   if (p->prec < ACO_FP32 || p->prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", p->prec);
   if (p->roulette != ACO_IR && p->roulette != ACO_ADAIR && p->roulette != ACO_RW)
     return set_error(ACO_ERR_ARG, "unknown roulette %d", p->roulette);
@@ -271,7 +275,7 @@ int instance_bind(const aco_params& p, unsigned char* ws, InstDev* d, cudaStream
   x.lkey = reinterpret_cast<uint32_t*>(ws + L.lkey);
   ACO_CUDA_TRY(cudaMemcpyAsync(coords, coords_host, sizeof(float) * 2 * p.n, cudaMemcpyHostToDevice, st));
   rc = launch_heuristic(coords, p.n, p.beta, const_cast<double*>(x.D), const_cast<float*>(x.H), ld, st);
-  if (!rc) rc = launch_fill(x.tau, p.n, ld, p.tau0, st);
+  if (!rc) rc = launch_fill_tau(x.tau, p.tau_prec, p.n, ld, p.tau0, st);
   if (rc) return rc;
   const double inf = INFINITY;
   const uint32_t zero = 0;
@@ -355,7 +359,7 @@ static int enqueue_iteration(aco_solver* s) {
     if (s->profiling) cudaEventRecordWithFlags(s->ev[q], st, cudaEventRecordExternal);
   };
   probe(0);
-  int rc = launch_build_P(s->tau, s->H, n, s->ld, p.alpha, 1.0f,
+  int rc = launch_build_P(s->tau, p.tau_prec, s->H, n, s->ld, p.alpha, 1.0f,
                           p.roulette == ACO_ADAIR ? s->sched : nullptr, s->it_dev, n_sched, p.prec,
                           s->P_f, st);
   if (rc) return rc;
@@ -382,7 +386,7 @@ static int enqueue_iteration(aco_solver* s) {
   if (rc) return rc;
   probe(5);
   if (det)
-    rc = launch_deposit(s->tau, n, s->ld, s->nbr, s->c, m, p.rho, s->dep, s->err, st);
+    rc = launch_deposit(s->tau, p.tau_prec, n, s->ld, s->nbr, s->c, m, p.rho, s->dep, s->err, st);
   else
     rc = launch_deposit_atomic(s->tau, n, s->ld, s->tours, s->c, m, p.rho, st);
   if (rc) return rc;
@@ -530,7 +534,7 @@ int aco_create(aco_solver** out, const float* coords_host, const aco_params* p, 
   if (cudaMemcpyAsync(s->coords, coords_host, sizeof(float) * 2 * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return fail(cuda_error(cudaGetLastError(), "copy coords"));
   rc = launch_heuristic(s->coords, n, p->beta, s->D, s->H, s->ld, st);
-  if (!rc) rc = launch_fill(s->tau, n, s->ld, p->tau0, st);
+  if (!rc) rc = launch_fill_tau(s->tau, p->tau_prec, n, s->ld, p->tau0, st);
   if (rc) return fail(rc);
   const double inf = INFINITY;
   const uint32_t zero = 0;
@@ -586,13 +590,50 @@ int aco_solver_best(aco_solver* s, int32_t* tour_host, double* len_host) {
   return ACO_OK;
 }
 
+// tau (n x n, dense fp32) from the device, whatever its storage
+static int copy_tau_out(aco_solver* s, float* tau_host) {
+  const int n = s->p.n;
+  if (s->p.tau_prec != ACO_BF16) {
+    ACO_CUDA_TRY(cudaMemcpy2D(tau_host, sizeof(float) * n, s->tau, sizeof(float) * s->ld, sizeof(float) * n, n,
+                              cudaMemcpyDeviceToHost));
+    return ACO_OK;
+  }
+  std::vector<uint16_t> h((size_t)n * n);
+  ACO_CUDA_TRY(cudaMemcpy2D(h.data(), sizeof(uint16_t) * n, s->tau, sizeof(uint16_t) * s->ld,
+                            sizeof(uint16_t) * n, n, cudaMemcpyDeviceToHost));
+  for (size_t q = 0; q < h.size(); ++q) {
+    const uint32_t b = (uint32_t)h[q] << 16;
+    std::memcpy(tau_host + q, &b, 4);
+  }
+  return ACO_OK;
+}
+
+// tau to the device (dense fp32 host values; bf16 storage takes their high halves,
+// exact for values that came from bf16)
+static int copy_tau_in(aco_solver* s, const float* tau_host) {
+  const int n = s->p.n;
+  if (s->p.tau_prec != ACO_BF16) {
+    ACO_CUDA_TRY(cudaMemcpy2D(s->tau, sizeof(float) * s->ld, tau_host, sizeof(float) * n, sizeof(float) * n, n,
+                              cudaMemcpyHostToDevice));
+    return ACO_OK;
+  }
+  std::vector<uint16_t> h((size_t)n * n);
+  for (size_t q = 0; q < h.size(); ++q) {
+    uint32_t b;
+    std::memcpy(&b, tau_host + q, 4);
+    if (b & 0xFFFFu) return set_error(ACO_ERR_ARG, "tau entry %zu is not a bfloat16 value", q);
+    h[q] = (uint16_t)(b >> 16);
+  }
+  ACO_CUDA_TRY(cudaMemcpy2D(s->tau, sizeof(uint16_t) * s->ld, h.data(), sizeof(uint16_t) * n,
+                            sizeof(uint16_t) * n, n, cudaMemcpyHostToDevice));
+  return ACO_OK;
+}
+
 int aco_solver_get_tau(aco_solver* s, float* tau_host) {
   if (!s || !tau_host) return set_error(ACO_ERR_ARG, "NULL argument");
   int rc = solver_sync_check(s);
   if (rc) return rc;
-  ACO_CUDA_TRY(cudaMemcpy2D(tau_host, sizeof(float) * s->p.n, s->tau, sizeof(float) * s->ld,
-                            sizeof(float) * s->p.n, s->p.n, cudaMemcpyDeviceToHost));
-  return ACO_OK;
+  return copy_tau_out(s, tau_host);
 }
 
 int aco_solver_get_tours(aco_solver* s, int32_t* tours_host) {
@@ -657,7 +698,7 @@ bool same_params(const aco_params& a, const aco_params& b) {
   return a.n == b.n && a.m == b.m && a.alpha == b.alpha && a.beta == b.beta && a.rho == b.rho && a.Q == b.Q &&
          a.tau0 == b.tau0 && a.seed == b.seed && a.prec == b.prec && a.roulette == b.roulette &&
          a.deposit == b.deposit && a.gamma_max == b.gamma_max && a.gamma_min == b.gamma_min &&
-         a.gamma_T == b.gamma_T && a.topk == b.topk;
+         a.gamma_T == b.gamma_T && a.topk == b.topk && a.tau_prec == b.tau_prec;
 }
 }  // namespace
 
@@ -685,8 +726,8 @@ int aco_solver_save(aco_solver* s, void* host_buf, size_t bytes) {
   ACO_CUDA_TRY(cudaMemcpy(&h.best_len, s->best_len, 8, cudaMemcpyDeviceToHost));
   std::memcpy(out, &h, sizeof(h));
   float* tau = reinterpret_cast<float*>(out + sizeof(h));
-  ACO_CUDA_TRY(cudaMemcpy2D(tau, sizeof(float) * n, s->tau, sizeof(float) * s->ld, sizeof(float) * n, n,
-                            cudaMemcpyDeviceToHost));
+  rc = copy_tau_out(s, tau);
+  if (rc) return rc;
   int32_t* best = reinterpret_cast<int32_t*>(tau + (size_t)n * n);
   ACO_CUDA_TRY(cudaMemcpy(best, s->best_tour, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
   const size_t body = ckpt_bytes(n) - sizeof(uint64_t);
@@ -715,8 +756,8 @@ int aco_solver_load(aco_solver* s, const void* host_buf, size_t bytes) {
   for (size_t q = 0; q < (size_t)n * n; ++q)
     if (!(tau[q] >= 0.0f)) return set_error(ACO_ERR_ARG, "checkpoint tau entry %zu is negative or NaN", q);
   const int32_t* best = reinterpret_cast<const int32_t*>(tau + (size_t)n * n);
-  ACO_CUDA_TRY(cudaMemcpy2D(s->tau, sizeof(float) * s->ld, tau, sizeof(float) * n, sizeof(float) * n, n,
-                            cudaMemcpyHostToDevice));
+  rc = copy_tau_in(s, tau);
+  if (rc) return rc;
   ACO_CUDA_TRY(cudaMemcpy(s->best_tour, best, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
   const double bl = h.has_best ? h.best_len : INFINITY;
   ACO_CUDA_TRY(cudaMemcpy(s->best_len, &bl, 8, cudaMemcpyHostToDevice));
@@ -900,6 +941,12 @@ int aco_set_precision(int prec) {
   return ACO_OK;
 }
 
+int aco_set_tau_precision(int prec) {
+  if (prec != ACO_FP32 && prec != ACO_BF16) return set_error(ACO_ERR_UNSUPPORTED, "tau is stored in fp32 or bf16");
+  g_pending.tau_prec = prec;
+  return ACO_OK;
+}
+
 int aco_set_deposit_topk(int k) {
   if (k < 0) return set_error(ACO_ERR_ARG, "topk=%d must be >= 0 (0: every path deposits)", k);
   g_pending.topk = k;
@@ -980,7 +1027,7 @@ int aco_op_build_P(const float* tau_dev, const float* H_dev, int n, int ld, int 
   if (rc) return rc;
   if (alpha < 0 || alpha > 8) return set_error(ACO_ERR_UNSUPPORTED, "alpha must be an integer in [0, 8]");
   if (!(inv_gamma > 0.0f) || !std::isfinite(inv_gamma)) return set_error(ACO_ERR_ARG, "inv_gamma must be > 0");
-  return launch_build_P(tau_dev, H_dev, n, ld, alpha, inv_gamma, nullptr, nullptr, 1, prec, P_dev,
+  return launch_build_P(tau_dev, ACO_FP32, H_dev, n, ld, alpha, inv_gamma, nullptr, nullptr, 1, prec, P_dev,
                         static_cast<cudaStream_t>(stream));
 }
 
@@ -1071,7 +1118,7 @@ int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const 
   if (!(rho >= 0.0f && rho <= 1.0f)) return set_error(ACO_ERR_ARG, "rho outside [0, 1]");
   rc = prepare_kernels();
   if (rc) return rc;
-  return launch_deposit(tau_dev, n, ld, nbr_dev, c_dev, m, rho, nullptr, err_dev,
+  return launch_deposit(tau_dev, ACO_FP32, n, ld, nbr_dev, c_dev, m, rho, nullptr, err_dev,
                         static_cast<cudaStream_t>(stream));
 }
 

@@ -26,19 +26,28 @@ __device__ __forceinline__ float p_entry(float tau, float h, int i, int j, int n
   return x;
 }
 
-template <int PREC>
-__device__ __forceinline__ void build_P_row(const float* __restrict__ tau_row,
+// Columns 4q .. 4q+3 of a tau row stored in fp32 (TB false) or bfloat16 (TB
+// true), widened to fp32 (exact).
+template <bool TB>
+__device__ __forceinline__ float4 load_tau4(const void* __restrict__ row, int q) {
+  if (!TB) return __ldg(reinterpret_cast<const float4*>(row) + q);
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(row) + q);
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                     __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+}
+
+template <int PREC, bool TB = false>
+__device__ __forceinline__ void build_P_row(const void* __restrict__ tau_row,
                                             const float* __restrict__ H_row, int n, int ld, int i,
                                             int alpha, float inv_gamma, void* __restrict__ P_row,
                                             float* red /* [32] shared */) {
-  const float4* t4 = reinterpret_cast<const float4*>(tau_row);
   const float4* h4 = reinterpret_cast<const float4*>(H_row);
   const int nq = ld >> 2;
   float scale = 1.0f;
   if (PREC == ACO_FP16) {
     float mx = 0.0f;
     for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-      const float4 a = __ldg(t4 + q), b = __ldg(h4 + q);
+      const float4 a = load_tau4<TB>(tau_row, q), b = __ldg(h4 + q);
       const int j = 4 * q;
       mx = fmaxf(mx, p_entry(a.x, b.x, i, j, n, alpha, inv_gamma));
       mx = fmaxf(mx, p_entry(a.y, b.y, i, j + 1, n, alpha, inv_gamma));
@@ -60,7 +69,7 @@ __device__ __forceinline__ void build_P_row(const float* __restrict__ tau_row,
     scale = __uint_as_float((uint32_t)(127 - e) << 23);
   }
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    const float4 a = __ldg(t4 + q), b = __ldg(h4 + q);
+    const float4 a = load_tau4<TB>(tau_row, q), b = __ldg(h4 + q);
     const int j = 4 * q;
     const float x0 = p_entry(a.x, b.x, i, j, n, alpha, inv_gamma);
     const float x1 = p_entry(a.y, b.y, i, j + 1, n, alpha, inv_gamma);
@@ -364,7 +373,8 @@ __host__ __device__ inline size_t deposit_smem_bytes(int n, int cap) {
   return (size_t)cap * 32 + nw * 8 + 33 * 4;
 }
 
-__device__ __forceinline__ void deposit_row_exact(float* __restrict__ row, int n,
+template <bool TB = false>
+__device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int n,
                                                   const int2* __restrict__ nbr_row,
                                                   const double* __restrict__ c, int m, float keep,
                                                   int E0, int mode, int cap, unsigned char* smem) {
@@ -433,7 +443,8 @@ __device__ __forceinline__ void deposit_row_exact(float* __restrict__ row, int n
     return (int)base[j >> 5] + __popc(bm[j >> 5] & ((1u << (j & 31)) - 1u));
   };
 
-  float4* row4 = reinterpret_cast<float4*>(row);
+  float* row = static_cast<float*>(row_v);                // fp32 storage
+  unsigned short* rowh = static_cast<unsigned short*>(row_v);  // bf16 storage
   const int npass = D > 0 ? (D + cap - 1) / cap : 1;
   for (int p = 0; p < npass; ++p) {
     const int s0 = p * cap;
@@ -480,7 +491,8 @@ __device__ __forceinline__ void deposit_row_exact(float* __restrict__ row, int n
     }
     __syncthreads();
 
-    // 4. the row: tau' everywhere on the first pass, rounded sums on touched entries
+    // 4. the row: tau' everywhere on the first pass, rounded sums on touched
+    //    entries; stored in fp32, or in bf16 (rounded once, to nearest even)
     for (int q = tid; 4 * q < n; q += nthr) {
       const int j0 = 4 * q;
       const uint32_t nib = (bm[j0 >> 5] >> (j0 & 31)) & 0xFu;
@@ -488,31 +500,56 @@ __device__ __forceinline__ void deposit_row_exact(float* __restrict__ row, int n
       const bool full = j0 + 4 <= n;
       float v[4];
       if (full) {
-        const float4 x = row4[q];
+        const float4 x = load_tau4<TB>(row_v, q);
         v[0] = x.x;
         v[1] = x.y;
         v[2] = x.z;
         v[3] = x.w;
       } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = j0 + i < n ? row[j0 + i] : 0.0f;
+        for (int i = 0; i < 4; ++i)
+          v[i] = j0 + i < n ? (TB ? __uint_as_float((uint32_t)rowh[j0 + i] << 16) : row[j0 + i]) : 0.0f;
       }
+      uint32_t out[4];  // fp32 bits, or bf16 bits in the low half
+      bool write[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const float tp = __fmul_rn(keep, v[i]);
+        write[i] = true;
         if (!((nib >> i) & 1u)) {
-          if (p == 0) v[i] = tp;
+          if (p == 0) {
+            out[i] = TB ? (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(tp)) : __float_as_uint(tp);
+          } else {
+            write[i] = false;
+          }
           continue;
         }
         const int sl = slot_of(j0 + i) - s0;
-        if (sl < 0 || sl >= cap) continue;  // summed in another pass
+        if (sl < 0 || sl >= cap) {  // summed in another pass
+          write[i] = false;
+          continue;
+        }
         const unsigned long long* a = acc + 4 * sl;
-        v[i] = (mode == kDepInf && a[3]) ? INFINITY : round_sum_f32(tp, a[0], a[1], a[2], E0);
+        if (mode == kDepInf && a[3])
+          out[i] = TB ? 0x7F80u : 0x7F800000u;
+        else
+          out[i] = TB ? round_sum_bf16(tp, a[0], a[1], a[2], E0)
+                      : __float_as_uint(round_sum_f32(tp, a[0], a[1], a[2], E0));
       }
-      if (full) {
-        row4[q] = make_float4(v[0], v[1], v[2], v[3]);
+      // entries not written in this pass keep their stored bits
+      if (full && write[0] && write[1] && write[2] && write[3]) {
+        if (TB)
+          reinterpret_cast<uint2*>(row_v)[q] = make_uint2(out[0] | (out[1] << 16), out[2] | (out[3] << 16));
+        else
+          reinterpret_cast<uint4*>(row_v)[q] = make_uint4(out[0], out[1], out[2], out[3]);
       } else {
-        for (int i = 0; i < 4 && j0 + i < n; ++i) row[j0 + i] = v[i];
+        for (int i = 0; i < 4 && j0 + i < n; ++i)
+          if (write[i]) {
+            if (TB)
+              rowh[j0 + i] = (unsigned short)out[i];
+            else
+              row[j0 + i] = __uint_as_float(out[i]);
+          }
       }
     }
     __syncthreads();
