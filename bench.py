@@ -241,9 +241,9 @@ def run_native(args, w, dist):
     st = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    def timed_run(prec, steps, warmup, lists, profile=True):
+    def timed_run(prec, steps, warmup, lists, profile=True, tau_prec="fp32"):
         kw = solver_kwargs(dict(w, prec=prec), seed)
-        s = B.Solver(coords, stream=st, cand_lists=lists, **kw)
+        s = B.Solver(coords, stream=st, cand_lists=lists, tau_prec=tau_prec, **kw)
         if profile:
             s.set_profiling(True)
         s.iterate(warmup)
@@ -346,28 +346,33 @@ def run_native(args, w, dist):
         # BF16 / FP16 M_p against fp32 on the same GPU: throughput and best-length gap
         variants = {}
         gaps = {}
-        for prec in ("fp32", "bf16", "fp16"):
-            if prec != w["prec"]:
-                t, kv, _ = timed_run(prec, min(args.steps, 30), 3, lists)
+        # (M_p precision, tau precision) pairs beside the main line
+        forms = [("fp32", "fp32"), ("bf16", "fp32"), ("fp16", "fp32"), ("bf16", "bf16")]
+        for prec, tprec in forms:
+            name = prec if tprec == "fp32" else f"{prec}_P_{tprec}_tau"
+            if (prec, tprec) != (w["prec"], "fp32"):
                 steps_v = min(args.steps, 30)
+                t, kv, _ = timed_run(prec, steps_v, 3, lists, tau_prec=tprec)
                 cms = kv[2] / steps_v
                 bpv = 4 if prec == "fp32" else 2
                 ach = m * n * (n - 1) / 2 * bpv / (cms / 1e3) / 1e9
-                variants[prec] = {"ms_per_step": round(t / steps_v, 4),
+                variants[name] = {"ms_per_step": round(t / steps_v, 4),
                                   "value": round(ant_steps / (t / steps_v / 1e3), 1),
                                   "construct_ms": round(cms, 4), "construct_alg_GBps": round(ach, 1),
-                                  "frac_of_hbm": round(ach / peak, 4)}
+                                  "frac_of_hbm": round(ach / peak, 4),
+                                  "kernel_ms": dict(zip(STEPS, [round(x / steps_v, 4) for x in kv]))}
             # best length after the workload's full iteration budget, mean over seeds
             lens = []
             for sd in range(args.gap_seeds):
-                s = B.Solver(coords, stream=st, cand_lists=lists, **solver_kwargs(dict(w, prec=prec), sd))
+                s = B.Solver(coords, stream=st, cand_lists=lists, tau_prec=tprec,
+                             **solver_kwargs(dict(w, prec=prec), sd))
                 s.iterate(w["iters"])
                 lens.append(s.best()[1])
                 s.close()
-            gaps[prec] = float(np.mean(lens))
-        for prec in gaps:
-            if prec != "fp32":
-                variants.setdefault(prec, {})["best_len_gap_vs_fp32"] = round(gaps[prec] / gaps["fp32"] - 1, 5)
+            gaps[name] = float(np.mean(lens))
+        for name in gaps:
+            if name != "fp32":
+                variants.setdefault(name, {})["best_len_gap_vs_fp32"] = round(gaps[name] / gaps["fp32"] - 1, 5)
         out["variants"] = variants
         out["best_len_mean"] = {k: round(v, 6) for k, v in gaps.items()}
         out["best_len_protocol"] = f"mean over seeds 0..{args.gap_seeds - 1} after {w['iters']} iterations"
