@@ -343,6 +343,18 @@ int aco_op_best(const double* L_dev, const int32_t* tours_dev, int n, int m,
 int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const double* c_dev,
                    int m, float rho, int32_t* err_dev, void* stream);
 
+/* Selection frequencies of independent roulette on one row (the Bernoulli
+ * trials of the paper's AdaIR visualisation, Sec. 4.3.1): for each of
+ * `trials` trials, r_j from Philox4x32-10 with key seed and counter
+ * (j >> 2, tr mod 2^32, tr div 2^32, salt), word j & 3, mapped as in the
+ * construction; the unvisited j maximising fl32(r_j * q_dev[j]) (lowest j on
+ * ties) gets counts_dev[j] += 1.  q_dev: n fp32 (for AdaIR the row raised to
+ * 1/gamma); visited_dev: n bytes, nonzero = excluded (nullable); counts_dev:
+ * n u64, accumulated into (zero it first).  n <= 4096. */
+int aco_op_selection_counts(const float* q_dev, const uint8_t* visited_dev, int n,
+                            unsigned long long trials, uint64_t seed, uint32_t salt,
+                            unsigned long long* counts_dev, void* stream);
+
 /* Sec. 2.3 path selection: with the lengths L_dev (m fp64) sorted ascending
  * (equal lengths by ant index), set c_dev[j] = 0 for every ant j outside the
  * first k, so that aco_op_deposit deposits from the k shortest paths only.

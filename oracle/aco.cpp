@@ -254,6 +254,32 @@ void orc_construct_rw(const float* P_val, int n, uint64_t seed, uint32_t it, int
   (void)nthreads;
 }
 
+// Selection frequencies of independent roulette on one row (the Bernoulli
+// trials of the AdaIR visualisation, Sec. 4.3.1): trial tr draws r_j from
+// Philox counter (j >> 2, tr mod 2^32, tr div 2^32, salt), word j & 3, and
+// the unvisited j maximising fl32(r_j * q_j) (lowest j on ties) wins;
+// counts[j] += its wins.
+void orc_selection_counts(const float* q, const uint8_t* visited, int n, uint64_t trials,
+                          uint64_t seed, uint32_t salt, uint64_t* counts) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (uint64_t tr = 0; tr < trials; ++tr) {
+    int32_t best_j = -1;
+    float best = 0.0f;
+    for (int j = 0; j < n; ++j) {
+      if (visited && visited[j]) continue;
+      const uint32_t ctr[4] = {(uint32_t)(j >> 2), (uint32_t)tr, (uint32_t)(tr >> 32), salt};
+      uint32_t out[4];
+      orc_philox4x32_10(ctr, key, out);
+      const float score = orc_uniform(out[j & 3]) * q[j];
+      if (best_j < 0 || score > best || (score == best && j < best_j)) {
+        best = score;
+        best_j = j;
+      }
+    }
+    if (best_j >= 0) counts[best_j] += 1;
+  }
+}
+
 // f(s) (Eq. 3): closed tour length, the sum over t = 0..n-1 of
 // d(p_t, p_{t+1 mod n}) in fp64, taken in blocks of 32 consecutive edges:
 // each block t = 32b .. 32b+31 summed in t order, then the block sums added

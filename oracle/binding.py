@@ -59,6 +59,7 @@ def lib():
             "orc_exact_sum_bf16": (C.c_float, [v, C.c_int64]),
             "orc_deposit_tau_bf16": (None, [v, C.c_int, v, v, C.c_int, C.c_float, C.c_float]),
             "orc_select_topk": (None, [v, C.c_int, C.c_int, v]),
+            "orc_selection_counts": (None, [v, v, C.c_int, u64, u64, u32, v]),
             "orc_rw_quantum": (u64, [C.c_float, C.c_int]),
             "orc_select_rw": (i32, [v, v, C.c_int, u64, u32, u32, u32]),
             "orc_construct_rw": (None, [v, C.c_int, u64, u32, C.c_int, C.c_int, v, C.c_int]),
@@ -272,6 +273,14 @@ def construct_rw(P_val, seed, it, k_begin, k_end, nthreads=None):
     tours = np.empty((k_end - k_begin, n), dtype=np.int32)
     lib().orc_construct_rw(_p(P_val), n, seed, it, k_begin, k_end, _p(tours), nthreads or default_threads())
     return tours
+
+
+def selection_counts(q, trials, seed, salt=0, visited=None):
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    vis = None if visited is None else np.ascontiguousarray(visited, dtype=np.uint8)
+    counts = np.zeros(q.size, dtype=np.uint64)
+    lib().orc_selection_counts(_p(q), None if vis is None else _p(vis), q.size, trials, seed, salt, _p(counts))
+    return counts
 
 
 def select_topk(L, k):

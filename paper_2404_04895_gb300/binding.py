@@ -46,6 +46,7 @@ _SIGS = {
     "aco_set_deposit_topk": (i32, [i32]),
     "aco_set_tau_precision": (i32, [i32]),
     "aco_op_select_topk": (i32, [v, i32, i32, v, v]),
+    "aco_op_selection_counts": (i32, [v, v, i32, C.c_ulonglong, u64, u32, v, v]),
     "aco_iterate": (i32, [i32]),
     "aco_best": (i32, [v, v]),
     "aco_get_tau": (i32, [v]),
@@ -217,6 +218,10 @@ def op_best(L, tours, n, m, best_tour, best_len, stream=None):
 def op_deposit(tau, n, ld, nbr, c, m, rho, err=None, stream=None):
     call("aco_op_deposit", ptr(tau), n, ld, ptr(nbr), ptr(c), m, rho, ptr(err) if err is not None else None,
          stream_ptr(stream))
+
+
+def op_selection_counts(q, n, trials, seed, counts, salt=0, visited=None, stream=None):
+    call("aco_op_selection_counts", ptr(q), ptr(visited), n, trials, seed, salt, ptr(counts), stream_ptr(stream))
 
 
 def op_select_topk(L, m, k, c, stream=None):
