@@ -53,14 +53,18 @@ __device__ __forceinline__ PhiloxKeys philox_keys(uint2 k) {
   return ks;
 }
 
+// Round r (0..9) of Philox4x32-10 on counter block c, for callers that
+// interleave the rounds with other work.
+__device__ __forceinline__ void philox_round(uint4& c, const PhiloxKeys& ks, int r) {
+  const uint32_t a0 = c.x, a2 = c.z;
+  const uint32_t hi0 = __umulhi(0xD2511F53u, a0), lo0 = 0xD2511F53u * a0;
+  const uint32_t hi1 = __umulhi(0xCD9E8D57u, a2), lo1 = 0xCD9E8D57u * a2;
+  c = make_uint4(hi1 ^ c.y ^ ks.k[r].x, lo1, hi0 ^ c.w ^ ks.k[r].y, lo0);
+}
+
 __device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeys& ks) {
 #pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t a0 = c.x, a2 = c.z;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, a0), lo0 = 0xD2511F53u * a0;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, a2), lo1 = 0xCD9E8D57u * a2;
-    c = make_uint4(hi1 ^ c.y ^ ks.k[r].x, lo1, hi0 ^ c.w ^ ks.k[r].y, lo0);
-  }
+  for (int r = 0; r < 10; ++r) philox_round(c, ks, r);
   return c;
 }
 

@@ -1,81 +1,98 @@
 // Lean tour construction: candidate lists first, a compact full scan only
-// when the list cannot decide a step (Sec. 2.2 + 2.4).  One warp walks NA
-// ants (kLeanAnts for a single instance, 1 in batches).
+// when the list cannot decide a step (Sec. 2.2 + 2.4).  One warp walks one
+// ant.
 //
-// State per ant is its visited bitmap in shared memory (n bits), its current
-// city and the first rounds of its current row's list.
+// State per ant is one visited flag byte per city in shared memory (marking a
+// city is a single byte store, not a read-modify-write of a bitmap word), its
+// current city and the first rounds of its current row's list.
 //   list step   the entries of row cur's sorted candidate list are scored in
 //               rounds of 32 (one Philox4x32-10 block per entry); after each
 //               round the round's last value -- and the row's bound -- bound
 //               every column not yet scored, and the step is decided once the
 //               best score key exceeds them (build_list_row).  The first
 //               round is one straight-line block (the argmax's two warp
-//               reductions run whether or not the round decides).
+//               reductions run whether or not the round decides), its Philox
+//               rounds interleaved with the speculation below so that each
+//               fills the other's waits; a later round whose entries are all
+//               visited changes no score and costs no Philox block.
 //   speculation in the first round the warp starts loading the lists of the
 //               first two unvisited entries, one of which is usually next
 //   full scan   (list undecided) the row is staged in shared memory by
-//               cp.async; each lane walks its 4-column groups against a
-//               threshold -- the warp's best listed score, raised by the lane's
-//               own best score so far -- and scores exactly only the unvisited,
-//               unlisted columns whose values reach it.
+//               cp.async; the warp walks it in blocks of 4 chunks per lane, a
+//               branch-free test of every group against the lane's threshold
+//               -- the warp's best listed score, raised by the lane's own best
+//               score so far -- and scores exactly, only in blocks where some
+//               lane has a group that reaches it, the unvisited, unlisted
+//               columns whose values do.
 // Either way the chosen city is argmax over unvisited j of fl32(r_j * p_j),
 // lowest j on ties, exactly as a plain scan of every candidate chooses.
+//
+// One ant per warp: two ants per warp were measured 1.75x slower on GB300
+// (n = 5000, m = 1024), and a second warp per ant that speculates while the
+// first decides 1.45x slower -- the step is one latency-bound chain, and
+// handing the speculated rows across warps through shared memory costs more
+// than the speculation it moves.
 #pragma once
 
 #include "construct.cuh"
 
 namespace aco {
 
-// Dynamic shared memory of the lean kernel for n cities at element size eb
-// and na ants per warp: the staged row (chunks rounded to whole warps) and one
-// visited bitmap per ant.
-__host__ __device__ inline size_t lean_bitmap_bytes(int n) { return (size_t)((n + 127) / 128) * 16; }
+// Visited flags of one ant: one byte per city, rounded to 16 bytes (bytes past
+// n stay 0; the scan masks columns >= n itself).
+__host__ __device__ inline size_t lean_flag_bytes(int n) { return (size_t)((n + 15) / 16) * 16; }
 
-__host__ __device__ inline size_t lean_smem_bytes(int n, int eb, int na = 1) {
+// Dynamic shared memory of the lean kernel for n cities at element size eb:
+// the staged row (chunks rounded to whole warps) and the visited flags.
+__host__ __device__ inline size_t lean_smem_bytes(int n, int eb) {
   const int V = 16 / eb;
   const int chunks = (n + V - 1) / V;
   const int kc = (chunks + 31) / 32;
-  return (size_t)kc * 32 * 16 + (size_t)na * lean_bitmap_bytes(n);
+  return (size_t)kc * 32 * 16 + lean_flag_bytes(n);
 }
 
-// Largest n the lean kernel serves (shared memory and 2 x 64-bit group masks).
-__host__ __device__ inline int lean_max_n(int eb) { return eb == 4 ? 16384 : 16384; }
+// Largest n the lean kernel serves (shared memory: 64 KB row + 16 KB flags).
+__host__ __device__ inline int lean_max_n(int) { return 16384; }
 
-// Ants per warp of the single-instance lean kernel.  Two ants per warp were
-// measured 1.75x slower on GB300 (n = 5000, m = 1024): the warp-wide
-// ballots, shuffles and reductions keep the two walks' chains from
-// overlapping, and either ant's rare slow path stalls both.
-constexpr int kLeanAnts = 1;
+__device__ __forceinline__ bool lean_visited(const volatile uint8_t* fl, int j) { return fl[j] != 0; }
 
 // Rounds 1, 2, ... of a step's list after an undecided first round whose last
-// entry was listed (so that more may follow); as list_rounds.
+// entry was listed (so that more may follow); as list_rounds, with entries
+// loaded two rounds ahead.
 __device__ __forceinline__ int lean_more_rounds(const uint2* __restrict__ lists, const ListRow& L,
-                                                const uint32_t* __restrict__ svis, const PhiloxKeys& ks,
-                                                uint32_t it, int k, int t, float& bs, int& bj) {
+                                                const volatile uint8_t* fl, const PhiloxKeys& ks, uint32_t it,
+                                                int k, int t, float& bs, int& bj) {
   const int lane = threadIdx.x & 31;
+  constexpr int R = kListMax / 32;
   const uint2* __restrict__ lrow = lists + (size_t)L.row * kListMax;
   uint2 e = L.e_next;
-  uint2 e_next = kListMax / 32 > 2 ? __ldg(lrow + 64 + lane) : e;
+  uint2 e2 = R > 2 ? __ldg(lrow + 64 + lane) : e;
+  uint2 e3 = R > 3 ? __ldg(lrow + 96 + lane) : e;
+  uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
 #pragma unroll 1
-  for (int r = 1; r < kListMax / 32; ++r) {
+  for (int r = 1; r < R; ++r) {
     const bool valid = e.y != kListPad;
     const unsigned vm = __ballot_sync(ACO_FULL_MASK, valid);
     if (vm == 0u) break;  // past the last entry
     const int j = valid ? (int)e.y : 0;
-    const bool unvisited = valid && !((svis[j >> 5] >> (j & 31)) & 1u);
-    const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it), ks);
-    const bool more = (vm >> 31) != 0u && r + 1 < kListMax / 32;
+    const bool unvisited = valid && !lean_visited(fl, j);
+    const unsigned un = __ballot_sync(ACO_FULL_MASK, unvisited);
+    const bool more = (vm >> 31) != 0u && r + 1 < R;
     uint32_t rest = L.lb;
     if (more) rest = max(rest, __shfl_sync(ACO_FULL_MASK, e.x, 31) + 1u);
-    const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
-    const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
-    if (unvisited) better(sc, j, bs, bj);
-    const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
+    if (un) {  // a round whose entries are all visited changes no score
+      const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it), ks);
+      const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
+      const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
+      if (unvisited) better(sc, j, bs, bj);
+      lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
+    }
     if (lk > rest)
       return (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == lk ? (uint32_t)bj : 0x7FFFFFFFu);
     if (!more) break;
-    e = e_next;
-    if (r + 2 < kListMax / 32) e_next = __ldg(lrow + 32 * (r + 2) + lane);
+    e = e2;
+    e2 = e3;
+    if (r + 3 < R) e3 = __ldg(lrow + 32 * (r + 3) + lane);
   }
   return -1;
 }
@@ -86,7 +103,7 @@ __device__ __forceinline__ int lean_more_rounds(const uint2* __restrict__ lists,
 // have and still be unlisted.  Returns the argmax (lowest column on ties).
 template <int PREC>
 __device__ __forceinline__ int lean_full_scan(const char* __restrict__ row, int n, uint32_t hi,
-                                              const uint32_t* __restrict__ svis, uint4* __restrict__ srow,
+                                              const volatile uint8_t* fl, uint4* __restrict__ srow,
                                               const PhiloxKeys& ks, uint32_t it, int k, int t, float& bs,
                                               int& bj) {
   using E = Elem<PREC>;
@@ -95,9 +112,11 @@ __device__ __forceinline__ int lean_full_scan(const char* __restrict__ row, int 
   const int lane = threadIdx.x & 31;
   const int nchunks = (n + V - 1) / V;
   const int kc = (nchunks + 31) / 32;
-  // visited bits of the 4 columns of the group starting at j (columns >= n count as visited)
+  // visited flags of the 4 columns of the group starting at j (a multiple of
+  // 4) as bits 0..3; columns >= n count as visited
   auto group_nibble = [&](int j) -> uint32_t {
-    uint32_t nib = (svis[j >> 5] >> (j & 31)) & 0xFu;
+    const uint32_t w = *reinterpret_cast<const volatile uint32_t*>(fl + j);
+    uint32_t nib = (((w & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
     if (j + 4 > n) nib |= (0xFu << max(0, n - j)) & 0xFu;
     return nib;
   };
@@ -114,29 +133,42 @@ __device__ __forceinline__ int lean_full_scan(const char* __restrict__ row, int 
     cp_async16_pred(srow + c * 32 + lane, row4 + cg, cg < nchunks);
   }
   cp_async_wait_all();  // this lane's copies only: it reads nothing else
-  // Each lane walks its groups in column order against a threshold: the
-  // warp's best listed score, raised by the lane's own best score so far.
-  // A column whose value is below it cannot win or tie (a score never
-  // exceeds its value), and a listed column -- value bits above hi -- was
-  // scored by the list rounds already, all of which ran.
+  // A column whose value is below the threshold cannot win or tie (a score
+  // never exceeds its value), and a listed column -- value bits above hi --
+  // was scored by the list rounds already, all of which ran.
   const uint32_t thr_warp = __reduce_max_sync(ACO_FULL_MASK, bs >= 0.0f ? __float_as_uint(bs) : 0u);
   const int nown = (nchunks - lane + 31) >> 5;  // chunks of this lane
-#pragma unroll 4
-  for (int c = 0; c < nown; ++c) {
-    const uint4 v = srow[c * 32 + lane];
+  for (int c0 = 0; c0 < kc; c0 += 4) {
+    uint4 v[4];
+    uint32_t hit = 0u;
+    const uint32_t thr0 = max(thr_warp, bs >= 0.0f ? __float_as_uint(bs) : 0u);
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const uint32_t thr = max(thr_warp, bs >= 0.0f ? __float_as_uint(bs) : 0u);
-      if (E::group_max_bits(v, g) < thr) continue;
-      const int j0 = (c * 32 + lane) * V + 4 * g;
-      if (j0 >= n) continue;
-      const float4 p = E::group_values(v, g);
-      auto out = [&](float x) -> uint32_t {
-        const uint32_t b = __float_as_uint(x);
-        return (b < thr || b > hi) ? 1u : 0u;
-      };
-      const uint32_t skip = group_nibble(j0) | out(p.x) | (out(p.y) << 1) | (out(p.z) << 2) | (out(p.w) << 3);
-      if (skip != 0xFu) score4(j0, p, skip);
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u;
+      v[u] = c < nown ? srow[c * 32 + lane] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        hit |= (c < nown && E::group_max_bits(v[u], g) >= thr0) ? (1u << (u * G + g)) : 0u;
+    }
+    if (__any_sync(ACO_FULL_MASK, hit != 0u)) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          if (!((hit >> (u * G + g)) & 1u)) continue;
+          const uint32_t thr = max(thr_warp, bs >= 0.0f ? __float_as_uint(bs) : 0u);
+          if (E::group_max_bits(v[u], g) < thr) continue;
+          const int j0 = ((c0 + u) * 32 + lane) * V + 4 * g;
+          if (j0 >= n) continue;
+          const float4 p = E::group_values(v[u], g);
+          auto out = [&](float x) -> uint32_t {
+            const uint32_t b = __float_as_uint(x);
+            return (b < thr || b > hi) ? 1u : 0u;
+          };
+          const uint32_t skip = group_nibble(j0) | out(p.x) | (out(p.y) << 1) | (out(p.z) << 2) | (out(p.w) << 3);
+          if (skip != 0xFu) score4(j0, p, skip);
+        }
+      }
     }
   }
   const uint32_t wkey = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
@@ -145,124 +177,107 @@ __device__ __forceinline__ int lean_full_scan(const char* __restrict__ row, int 
   return next;
 }
 
-// NA ants walked by one warp: ants k[q], tours tour[q], bitmaps svis[q].
-template <int PREC, int NA>
-__device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv, int n, int ld, uint2 key,
-                                                    uint32_t it, const int* k, int32_t* const* tour,
-                                                    int32_t* __restrict__ err,
-                                                    const uint2* __restrict__ lists,
-                                                    const uint32_t* __restrict__ lkey,
-                                                    uint4* __restrict__ srow, uint32_t* const* svis) {
+// Ant k's walk (one warp): tour row `tour`, visited flags `flags`, staged-row
+// buffer `srow`.
+template <int PREC>
+__device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, int n, int ld, uint2 key,
+                                                   uint32_t it, int k, int32_t* __restrict__ tour,
+                                                   int32_t* __restrict__ err, const uint2* __restrict__ lists,
+                                                   const uint32_t* __restrict__ lkey, uint4* __restrict__ srow,
+                                                   uint8_t* flags) {
   using E = Elem<PREC>;
   const int lane = threadIdx.x & 31;
   const char* __restrict__ P = static_cast<const char*>(Pv);
   const size_t row_bytes = (size_t)ld * E::BYTES;
-  const int nwords = (n + 31) / 32;
   const PhiloxKeys ks = philox_keys(key);
+  volatile uint8_t* fl = flags;
 
-  int cur[NA], tbuf[NA];
-  ListRow lr[NA], sp[NA][2];
-#pragma unroll
-  for (int q = 0; q < NA; ++q) {
-    for (int w = lane; w < nwords; w += 32) svis[q][w] = 0u;
-    cur[q] = start_city(key, it, (uint32_t)k[q], n);
-    tbuf[q] = cur[q];  // the tour is written 32 steps at a time: lane (t mod 32) keeps step t
-    lr[q].row = sp[q][0].row = sp[q][1].row = -1;
-  }
+  uint32_t* fw = reinterpret_cast<uint32_t*>(flags);
+  for (int w = lane; w < (int)(lean_flag_bytes(n) / 4); w += 32) fw[w] = 0u;
+  int cur = start_city(key, it, (uint32_t)k, n);
+  int tbuf = cur;  // the tour is written 32 steps at a time: lane (t mod 32) keeps step t
   __syncwarp();
-#pragma unroll
-  for (int q = 0; q < NA; ++q) {
-    if (lane == 0) svis[q][cur[q] >> 5] |= 1u << (cur[q] & 31);
-    if (lists) lr[q] = load_list_row(lists, lkey, cur[q]);
-  }
+  fl[cur] = 1;
+  ListRow lr, sp0, sp1;
+  lr.row = sp0.row = sp1.row = -1;
+  if (lists) lr = load_list_row(lists, lkey, cur);
   __syncwarp();
 
   for (int t = 1; t < n; ++t) {
-    int next[NA];
-    float bs[NA];
-    int bj[NA];
-    bool more[NA];
-    // ---- first list round of every ant: one straight-line block
-#pragma unroll
-    for (int q = 0; q < NA; ++q) {
-      bs[q] = -1.0f;
-      bj[q] = 0x7FFFFFFF;
-      next[q] = -1;
-      more[q] = false;
-      if (lists) {
-        const uint2 e = lr[q].e;
-        const bool valid = e.y != kListPad;
-        const int j = valid ? (int)e.y : 0;
-        const bool unvisited = valid && !((svis[q][j >> 5] >> (j & 31)) & 1u);
-        const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k[q], it), ks);
-        const unsigned vm = __ballot_sync(ACO_FULL_MASK, valid);
-        const unsigned un = __ballot_sync(ACO_FULL_MASK, unvisited);
-        const unsigned un2 = un & (un - 1u);
-        const int sj = __shfl_sync(ACO_FULL_MASK, j, un ? __ffs(un) - 1 : 0);
-        const int sj2 = __shfl_sync(ACO_FULL_MASK, j, un2 ? __ffs(un2) - 1 : 0);
-        sp[q][0] = load_list_row(lists, lkey, sj);  // harmless when there is no candidate
-        sp[q][1] = load_list_row(lists, lkey, sj2);
-        if (!un) sp[q][0].row = -1;
-        if (!un2) sp[q][1].row = -1;
-        // every entry after this round has a value <= this round's last one
-        more[q] = (vm >> 31) != 0u && kListMax / 32 > 1;
-        uint32_t rest = lr[q].lb;
-        if (more[q]) rest = max(rest, __shfl_sync(ACO_FULL_MASK, e.x, 31) + 1u);
-        const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
-        const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
-        if (unvisited) better(sc, j, bs[q], bj[q]);
-        const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs[q]));
-        const int win = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs[q]) == lk ? (uint32_t)bj[q] : 0x7FFFFFFFu);
-        if (lk > rest) next[q] = win;
-      }
+    float bs = -1.0f;
+    int bj = 0x7FFFFFFF;
+    int next = -1;
+    bool more = false;
+    // ---- first list round: one straight-line block
+    if (lists) {
+      const uint2 e = lr.e;
+      const bool valid = e.y != kListPad;
+      const int j = valid ? (int)e.y : 0;
+      uint4 x = make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it);
+      const bool unvisited = valid && !lean_visited(fl, j);
+      philox_round(x, ks, 0);
+      philox_round(x, ks, 1);
+      philox_round(x, ks, 2);
+      const unsigned vm = __ballot_sync(ACO_FULL_MASK, valid);
+      const unsigned un = __ballot_sync(ACO_FULL_MASK, unvisited);
+      philox_round(x, ks, 3);
+      philox_round(x, ks, 4);
+      const unsigned un2 = un & (un - 1u);
+      // no candidate: lane -1 reads lane 31 (mod 32), and the row is dropped below
+      const int sj = __shfl_sync(ACO_FULL_MASK, j, __ffs(un) - 1);
+      philox_round(x, ks, 5);
+      philox_round(x, ks, 6);
+      const int sj2 = __shfl_sync(ACO_FULL_MASK, j, __ffs(un2) - 1);
+      philox_round(x, ks, 7);
+      sp0 = load_list_row(lists, lkey, sj);
+      sp1 = load_list_row(lists, lkey, sj2);
+      if (!un) sp0.row = -1;
+      if (!un2) sp1.row = -1;
+      // every entry after this round has a value <= this round's last one
+      more = (vm >> 31) != 0u && kListMax / 32 > 1;
+      uint32_t rest = lr.lb;
+      if (more) rest = max(rest, __shfl_sync(ACO_FULL_MASK, e.x, 31) + 1u);
+      philox_round(x, ks, 8);
+      philox_round(x, ks, 9);
+      const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
+      const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
+      if (unvisited) better(sc, j, bs, bj);
+      const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
+      const int win = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == lk ? (uint32_t)bj : 0x7FFFFFFFu);
+      if (lk > rest) next = win;
     }
-    // ---- later rounds and full scans, ant by ant (rare)
-#pragma unroll
-    for (int q = 0; q < NA; ++q) {
-      if (next[q] < 0 && lists && more[q])
-        next[q] = lean_more_rounds(lists, lr[q], svis[q], ks, it, k[q], t, bs[q], bj[q]);
-      if (next[q] < 0) {
-        const uint32_t hi = (lists && lr[q].lb) ? lr[q].lb - 1u : 0xFFFFFFFFu;
-        next[q] = lean_full_scan<PREC>(P + (size_t)cur[q] * row_bytes, n, hi, svis[q], srow, ks, it, k[q], t,
-                                       bs[q], bj[q]);
-      }
+    // ---- later rounds and the full scan (rare)
+    if (next < 0 && lists && more) next = lean_more_rounds(lists, lr, fl, ks, it, k, t, bs, bj);
+    if (next < 0) {
+      const uint32_t hi = (lists && lr.lb) ? lr.lb - 1u : 0xFFFFFFFFu;
+      next = lean_full_scan<PREC>(P + (size_t)cur * row_bytes, n, hi, fl, srow, ks, it, k, t, bs, bj);
     }
     // ---- bookkeeping
-    bool bad = false;
-#pragma unroll
-    for (int q = 0; q < NA; ++q) bad = bad || next[q] < 0 || next[q] >= n;
-    if (bad) {  // no unvisited city found: cannot happen for valid input
+    if (next < 0 || next >= n) {  // no unvisited city found: cannot happen for valid input
       if (lane == 0 && err) atomicExch(err, kErrConstruct);
       break;
     }
-#pragma unroll
-    for (int q = 0; q < NA; ++q) {
-      if (lane == (t & 31)) tbuf[q] = next[q];
-      if ((t & 31) == 31 || t == n - 1) {
-        const int tt = (t & ~31) + lane;
-        if (tt <= t) tour[q][tt] = tbuf[q];
-      }
-      if (lane == 0) svis[q][next[q] >> 5] |= 1u << (next[q] & 31);
+    if (lane == (t & 31)) tbuf = next;
+    if ((t & 31) == 31 || t == n - 1) {
+      const int tt = (t & ~31) + lane;
+      if (tt <= t) tour[tt] = tbuf;
     }
+    fl[next] = 1;  // every lane stores the same byte
     __syncwarp();
-#pragma unroll
-    for (int q = 0; q < NA; ++q) {
-      cur[q] = next[q];
-      // the next row's list: usually already in flight from the speculation
-      if (lists && t + 1 < n) {
-        if (sp[q][0].row == next[q])
-          lr[q] = sp[q][0];
-        else if (sp[q][1].row == next[q])
-          lr[q] = sp[q][1];
-        else
-          lr[q] = load_list_row(lists, lkey, next[q]);
-      }
+    cur = next;
+    // the next row's list: usually already in flight from the speculation
+    if (lists && t + 1 < n) {
+      if (sp0.row == next)
+        lr = sp0;
+      else if (sp1.row == next)
+        lr = sp1;
+      else
+        lr = load_list_row(lists, lkey, next);
     }
   }
 }
 
-// One warp per kLeanAnts ants (the last warp of an odd m walks its ant twice
-// and writes the same tour twice).
+// One warp per ant.
 template <int PREC>
 __global__ void __launch_bounds__(32) construct_lean_kernel(
     const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it_arg,
@@ -270,22 +285,13 @@ __global__ void __launch_bounds__(32) construct_lean_kernel(
     const uint2* __restrict__ lists, const int* __restrict__ lcnt, const uint32_t* __restrict__ lkey) {
   extern __shared__ __align__(16) uint4 lsm[];
   (void)lcnt;
-  const int k0 = blockIdx.x * kLeanAnts;
-  if (k0 >= m) return;
+  const int k = blockIdx.x;
+  if (k >= m) return;
   const int eb = PREC == ACO_FP32 ? 4 : 2;
   const int chunks = (n + 16 / eb - 1) / (16 / eb);
-  char* bitmaps = reinterpret_cast<char*>(lsm + ((chunks + 31) / 32) * 32);
-  int k[kLeanAnts];
-  int32_t* tour[kLeanAnts];
-  uint32_t* svis[kLeanAnts];
-#pragma unroll
-  for (int q = 0; q < kLeanAnts; ++q) {
-    k[q] = min(k0 + q, m - 1);
-    tour[q] = tours + (size_t)k[q] * n;
-    svis[q] = reinterpret_cast<uint32_t*>(bitmaps + q * lean_bitmap_bytes(n));
-  }
+  uint8_t* flags = reinterpret_cast<uint8_t*>(lsm + ((chunks + 31) / 32) * 32);
   const uint32_t it = it_dev ? *it_dev : it_arg;
-  construct_ants_lean<PREC, kLeanAnts>(Pv, n, ld, key, it, k, tour, err, lists, lkey, lsm, svis);
+  construct_ant_lean<PREC>(Pv, n, ld, key, it, k, tours + (size_t)k * n, err, lists, lkey, lsm, flags);
 }
 
 // Multi-instance form: persistent warps pull (instance, ant) items.
@@ -296,7 +302,7 @@ __global__ void __launch_bounds__(32) batch_construct_lean_kernel(
   extern __shared__ __align__(16) uint4 lsm[];
   const int eb = PREC == ACO_FP32 ? 4 : 2;
   const int max_chunks = (max_n + 16 / eb - 1) / (16 / eb);
-  uint32_t* svis = reinterpret_cast<uint32_t*>(lsm + ((max_chunks + 31) / 32) * 32);
+  uint8_t* flags = reinterpret_cast<uint8_t*>(lsm + ((max_chunks + 31) / 32) * 32);
   const int base = __ldg(ant_off);
   for (;;) {
     int item = 0;
@@ -305,10 +311,10 @@ __global__ void __launch_bounds__(32) batch_construct_lean_kernel(
     if (item >= total) break;
     const int i = find_instance(ant_off, count, base + item);
     const InstDev& I = insts[i];
-    int k[1] = {base + item - __ldg(ant_off + i)};
-    int32_t* tour[1] = {I.tours + (size_t)k[0] * I.n};
-    uint32_t* sv[1] = {svis};
-    construct_ants_lean<PREC, 1>(I.P, I.n, I.ld, I.key, *I.it, k, tour, err, I.lists, I.lkey, lsm, sv);
+    const int k = base + item - __ldg(ant_off + i);
+    construct_ant_lean<PREC>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err, I.lists, I.lkey,
+                             lsm, flags);
+    __syncwarp();  // the flags and the staged row are reused by the next item
   }
 }
 
