@@ -9,8 +9,8 @@ int launch_construct_lean(const void* P, int prec, int n, int ld, int m, uint2 k
                           const int* lcnt, const uint32_t* lkey, cudaStream_t st) {
   const int eb = prec == ACO_FP32 ? 4 : 2;
   if (n > lean_max_n(eb)) return set_error(ACO_ERR_UNSUPPORTED, "lean construction serves n <= %d", lean_max_n(eb));
-  const size_t smem = lean_smem_bytes(n, eb);
-  const int grid = m;
+  const size_t smem = lean_smem_bytes(n, eb, kLeanAnts);
+  const int grid = (m + kLeanAnts - 1) / kLeanAnts;
   switch (prec) {
     case ACO_FP32:
       construct_lean_kernel<ACO_FP32><<<grid, 32, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err, lists,
@@ -68,7 +68,7 @@ int launch_batch_construct_lean(const InstDev* insts, const int* ant_off, int co
 }
 
 int prepare_construct_lean() {
-  const int most = (int)lean_smem_bytes(lean_max_n(4), 4);
+  const int most = (int)lean_smem_bytes(lean_max_n(4), 4, kLeanAnts);
   cudaError_t e = cudaFuncSetAttribute(construct_lean_kernel<ACO_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(construct_lean_kernel<ACO_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);

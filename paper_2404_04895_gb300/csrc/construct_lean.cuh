@@ -1,6 +1,6 @@
 // Lean tour construction: candidate lists first, a compact full scan only
 // when the list cannot decide a step (Sec. 2.2 + 2.4).  One warp walks one
-// ant.
+// ant (kLeanAnts).
 //
 // State per ant is one visited flag byte per city in shared memory (marking a
 // city is a single byte store, not a read-modify-write of a bitmap word), its
@@ -38,30 +38,41 @@
 
 namespace aco {
 
+// Visited flag of city j (one byte per city, at `flags`) and its marking.
+__device__ __forceinline__ bool lean_visited(const uint32_t* flags, int j) {
+  return reinterpret_cast<const volatile uint8_t*>(flags)[j] != 0;
+}
+__device__ __forceinline__ void lean_mark(uint32_t* flags, int j) { reinterpret_cast<volatile uint8_t*>(flags)[j] = 1; }
+
 // Visited flags of one ant: one byte per city, rounded to 16 bytes (bytes past
 // n stay 0; the scan masks columns >= n itself).
 __host__ __device__ inline size_t lean_flag_bytes(int n) { return (size_t)((n + 15) / 16) * 16; }
 
-// Dynamic shared memory of the lean kernel for n cities at element size eb:
-// the staged row (chunks rounded to whole warps) and the visited flags.
-__host__ __device__ inline size_t lean_smem_bytes(int n, int eb) {
+// Dynamic shared memory of the lean kernel for n cities at element size eb
+// and na ants per warp: the staged row (chunks rounded to whole warps) and one
+// set of visited flags per ant.
+__host__ __device__ inline size_t lean_smem_bytes(int n, int eb, int na = 1) {
   const int V = 16 / eb;
   const int chunks = (n + V - 1) / V;
   const int kc = (chunks + 31) / 32;
-  return (size_t)kc * 32 * 16 + lean_flag_bytes(n);
+  return (size_t)kc * 32 * 16 + (size_t)na * lean_flag_bytes(n);
 }
 
 // Largest n the lean kernel serves (shared memory: 64 KB row + 16 KB flags).
 __host__ __device__ inline int lean_max_n(int) { return 16384; }
 
-__device__ __forceinline__ bool lean_visited(const volatile uint8_t* fl, int j) { return fl[j] != 0; }
+// Ants per warp of the single-instance lean kernel.  Two ants per warp were
+// measured 1.75x slower on GB300 (n = 5000, m = 1024): the warp-wide
+// ballots, shuffles and reductions keep the two walks' chains from
+// overlapping, and either ant's rare slow path stalls both.
+constexpr int kLeanAnts = 1;
 
 // Rounds 1, 2, ... of a step's list after an undecided first round whose last
 // entry was listed (so that more may follow); as list_rounds, with entries
 // loaded two rounds ahead.
 __device__ __forceinline__ int lean_more_rounds(const uint2* __restrict__ lists, const ListRow& L,
-                                                const volatile uint8_t* fl, const PhiloxKeys& ks, uint32_t it,
-                                                int k, int t, float& bs, int& bj) {
+                                                 const uint32_t* __restrict__ svis, const PhiloxKeys& ks,
+                                                 uint32_t it, int k, int t, float& bs, int& bj) {
   const int lane = threadIdx.x & 31;
   constexpr int R = kListMax / 32;
   const uint2* __restrict__ lrow = lists + (size_t)L.row * kListMax;
@@ -75,7 +86,7 @@ __device__ __forceinline__ int lean_more_rounds(const uint2* __restrict__ lists,
     const unsigned vm = __ballot_sync(ACO_FULL_MASK, valid);
     if (vm == 0u) break;  // past the last entry
     const int j = valid ? (int)e.y : 0;
-    const bool unvisited = valid && !lean_visited(fl, j);
+    const bool unvisited = valid && !lean_visited(svis, j);
     const unsigned un = __ballot_sync(ACO_FULL_MASK, unvisited);
     const bool more = (vm >> 31) != 0u && r + 1 < R;
     uint32_t rest = L.lb;
@@ -103,7 +114,7 @@ __device__ __forceinline__ int lean_more_rounds(const uint2* __restrict__ lists,
 // have and still be unlisted.  Returns the argmax (lowest column on ties).
 template <int PREC>
 __device__ __forceinline__ int lean_full_scan(const char* __restrict__ row, int n, uint32_t hi,
-                                              const volatile uint8_t* fl, uint4* __restrict__ srow,
+                                              const uint32_t* __restrict__ svis, uint4* __restrict__ srow,
                                               const PhiloxKeys& ks, uint32_t it, int k, int t, float& bs,
                                               int& bj) {
   using E = Elem<PREC>;
@@ -115,8 +126,8 @@ __device__ __forceinline__ int lean_full_scan(const char* __restrict__ row, int 
   // visited flags of the 4 columns of the group starting at j (a multiple of
   // 4) as bits 0..3; columns >= n count as visited
   auto group_nibble = [&](int j) -> uint32_t {
-    const uint32_t w = *reinterpret_cast<const volatile uint32_t*>(fl + j);
-    uint32_t nib = (((w & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
+    const uint32_t wv = *reinterpret_cast<const volatile uint32_t*>(reinterpret_cast<const uint8_t*>(svis) + j);
+    uint32_t nib = (((wv & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
     if (j + 4 > n) nib |= (0xFu << max(0, n - j)) & 0xFu;
     return nib;
   };
@@ -133,11 +144,16 @@ __device__ __forceinline__ int lean_full_scan(const char* __restrict__ row, int 
     cp_async16_pred(srow + c * 32 + lane, row4 + cg, cg < nchunks);
   }
   cp_async_wait_all();  // this lane's copies only: it reads nothing else
-  // A column whose value is below the threshold cannot win or tie (a score
-  // never exceeds its value), and a listed column -- value bits above hi --
-  // was scored by the list rounds already, all of which ran.
-  const uint32_t thr_warp = __reduce_max_sync(ACO_FULL_MASK, bs >= 0.0f ? __float_as_uint(bs) : 0u);
+  // Each lane walks its groups in column order against a threshold: the
+  // warp's best listed score, raised by the lane's own best score so far.
+  // A column whose value is below it cannot win or tie (a score never
+  // exceeds its value), and a listed column -- value bits above hi -- was
+  // scored by the list rounds already, all of which ran.
+  uint32_t thr_warp = __reduce_max_sync(ACO_FULL_MASK, bs >= 0.0f ? __float_as_uint(bs) : 0u);
   const int nown = (nchunks - lane + 31) >> 5;  // chunks of this lane
+  // blocks of 4 chunks: a branch-free test of every group; the per-column
+  // work runs only in blocks where some lane has a group that reaches its
+  // threshold (a warp-uniform branch)
   for (int c0 = 0; c0 < kc; c0 += 4) {
     uint4 v[4];
     uint32_t hit = 0u;
@@ -177,107 +193,135 @@ __device__ __forceinline__ int lean_full_scan(const char* __restrict__ row, int 
   return next;
 }
 
-// Ant k's walk (one warp): tour row `tour`, visited flags `flags`, staged-row
-// buffer `srow`.
-template <int PREC>
-__device__ __forceinline__ void construct_ant_lean(const void* __restrict__ Pv, int n, int ld, uint2 key,
-                                                   uint32_t it, int k, int32_t* __restrict__ tour,
-                                                   int32_t* __restrict__ err, const uint2* __restrict__ lists,
-                                                   const uint32_t* __restrict__ lkey, uint4* __restrict__ srow,
-                                                   uint8_t* flags) {
+// NA ants walked by one warp: ants k[q], tours tour[q], visited flags svis[q].
+template <int PREC, int NA>
+__device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv, int n, int ld, uint2 key,
+                                                    uint32_t it, const int* k, int32_t* const* tour,
+                                                    int32_t* __restrict__ err,
+                                                    const uint2* __restrict__ lists,
+                                                    const uint32_t* __restrict__ lkey,
+                                                    uint4* __restrict__ srow, uint32_t* const* svis) {
   using E = Elem<PREC>;
   const int lane = threadIdx.x & 31;
   const char* __restrict__ P = static_cast<const char*>(Pv);
   const size_t row_bytes = (size_t)ld * E::BYTES;
   const PhiloxKeys ks = philox_keys(key);
-  volatile uint8_t* fl = flags;
 
-  uint32_t* fw = reinterpret_cast<uint32_t*>(flags);
-  for (int w = lane; w < (int)(lean_flag_bytes(n) / 4); w += 32) fw[w] = 0u;
-  int cur = start_city(key, it, (uint32_t)k, n);
-  int tbuf = cur;  // the tour is written 32 steps at a time: lane (t mod 32) keeps step t
+  int cur[NA], tbuf[NA];
+  ListRow lr[NA], sp[NA][2];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    for (int w = lane; w < (int)(lean_flag_bytes(n) / 4); w += 32) svis[q][w] = 0u;
+    cur[q] = start_city(key, it, (uint32_t)k[q], n);
+    tbuf[q] = cur[q];  // the tour is written 32 steps at a time: lane (t mod 32) keeps step t
+    lr[q].row = sp[q][0].row = sp[q][1].row = -1;
+  }
   __syncwarp();
-  fl[cur] = 1;
-  ListRow lr, sp0, sp1;
-  lr.row = sp0.row = sp1.row = -1;
-  if (lists) lr = load_list_row(lists, lkey, cur);
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    if (lane == 0) lean_mark(svis[q], cur[q]);
+    if (lists) lr[q] = load_list_row(lists, lkey, cur[q]);
+  }
   __syncwarp();
 
   for (int t = 1; t < n; ++t) {
-    float bs = -1.0f;
-    int bj = 0x7FFFFFFF;
-    int next = -1;
-    bool more = false;
-    // ---- first list round: one straight-line block
-    if (lists) {
-      const uint2 e = lr.e;
-      const bool valid = e.y != kListPad;
-      const int j = valid ? (int)e.y : 0;
-      uint4 x = make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it);
-      const bool unvisited = valid && !lean_visited(fl, j);
-      philox_round(x, ks, 0);
-      philox_round(x, ks, 1);
-      philox_round(x, ks, 2);
-      const unsigned vm = __ballot_sync(ACO_FULL_MASK, valid);
-      const unsigned un = __ballot_sync(ACO_FULL_MASK, unvisited);
-      philox_round(x, ks, 3);
-      philox_round(x, ks, 4);
-      const unsigned un2 = un & (un - 1u);
-      // no candidate: lane -1 reads lane 31 (mod 32), and the row is dropped below
-      const int sj = __shfl_sync(ACO_FULL_MASK, j, __ffs(un) - 1);
-      philox_round(x, ks, 5);
-      philox_round(x, ks, 6);
-      const int sj2 = __shfl_sync(ACO_FULL_MASK, j, __ffs(un2) - 1);
-      philox_round(x, ks, 7);
-      sp0 = load_list_row(lists, lkey, sj);
-      sp1 = load_list_row(lists, lkey, sj2);
-      if (!un) sp0.row = -1;
-      if (!un2) sp1.row = -1;
-      // every entry after this round has a value <= this round's last one
-      more = (vm >> 31) != 0u && kListMax / 32 > 1;
-      uint32_t rest = lr.lb;
-      if (more) rest = max(rest, __shfl_sync(ACO_FULL_MASK, e.x, 31) + 1u);
-      philox_round(x, ks, 8);
-      philox_round(x, ks, 9);
-      const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
-      const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
-      if (unvisited) better(sc, j, bs, bj);
-      const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
-      const int win = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs) == lk ? (uint32_t)bj : 0x7FFFFFFFu);
-      if (lk > rest) next = win;
+    int next[NA];
+    float bs[NA];
+    int bj[NA];
+    bool more[NA];
+    // ---- first list round of every ant: one straight-line block
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      bs[q] = -1.0f;
+      bj[q] = 0x7FFFFFFF;
+      next[q] = -1;
+      more[q] = false;
+      if (lists) {
+        const uint2 e = lr[q].e;
+        const bool valid = e.y != kListPad;
+        const int j = valid ? (int)e.y : 0;
+        uint4 xc = make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k[q], it);
+        const bool unvisited = valid && !lean_visited(svis[q], j);
+        philox_round(xc, ks, 0);
+        philox_round(xc, ks, 1);
+        philox_round(xc, ks, 2);
+        const unsigned vm = __ballot_sync(ACO_FULL_MASK, valid);
+        const unsigned un = __ballot_sync(ACO_FULL_MASK, unvisited);
+        philox_round(xc, ks, 3);
+        philox_round(xc, ks, 4);
+        const unsigned un2 = un & (un - 1u);
+        const int sj = __shfl_sync(ACO_FULL_MASK, j, __ffs(un) - 1);
+        philox_round(xc, ks, 5);
+        philox_round(xc, ks, 6);
+        const int sj2 = __shfl_sync(ACO_FULL_MASK, j, __ffs(un2) - 1);
+        philox_round(xc, ks, 7);
+        sp[q][0] = load_list_row(lists, lkey, sj);
+        sp[q][1] = load_list_row(lists, lkey, sj2);
+        if (!un) sp[q][0].row = -1;
+        if (!un2) sp[q][1].row = -1;
+        more[q] = (vm >> 31) != 0u && kListMax / 32 > 1;
+        uint32_t rest = lr[q].lb;
+        if (more[q]) rest = max(rest, __shfl_sync(ACO_FULL_MASK, e.x, 31) + 1u);
+        philox_round(xc, ks, 8);
+        philox_round(xc, ks, 9);
+        const uint4 x = xc;
+        const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
+        const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
+        if (unvisited) better(sc, j, bs[q], bj[q]);
+        const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs[q]));
+        const int win = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs[q]) == lk ? (uint32_t)bj[q] : 0x7FFFFFFFu);
+        if (lk > rest) next[q] = win;
+      }
     }
-    // ---- later rounds and the full scan (rare)
-    if (next < 0 && lists && more) next = lean_more_rounds(lists, lr, fl, ks, it, k, t, bs, bj);
-    if (next < 0) {
-      const uint32_t hi = (lists && lr.lb) ? lr.lb - 1u : 0xFFFFFFFFu;
-      next = lean_full_scan<PREC>(P + (size_t)cur * row_bytes, n, hi, fl, srow, ks, it, k, t, bs, bj);
+    // ---- later rounds and full scans, ant by ant (rare)
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+
+      if (next[q] < 0 && lists && more[q])
+        next[q] = lean_more_rounds(lists, lr[q], svis[q], ks, it, k[q], t, bs[q], bj[q]);
+      if (next[q] < 0) {
+        const uint32_t hi = (lists && lr[q].lb) ? lr[q].lb - 1u : 0xFFFFFFFFu;
+        next[q] = lean_full_scan<PREC>(P + (size_t)cur[q] * row_bytes, n, hi, svis[q], srow, ks, it, k[q], t,
+                                       bs[q], bj[q]);
+      }
     }
     // ---- bookkeeping
-    if (next < 0 || next >= n) {  // no unvisited city found: cannot happen for valid input
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) bad = bad || next[q] < 0 || next[q] >= n;
+    if (bad) {  // no unvisited city found: cannot happen for valid input
       if (lane == 0 && err) atomicExch(err, kErrConstruct);
       break;
     }
-    if (lane == (t & 31)) tbuf = next;
-    if ((t & 31) == 31 || t == n - 1) {
-      const int tt = (t & ~31) + lane;
-      if (tt <= t) tour[tt] = tbuf;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      if (lane == (t & 31)) tbuf[q] = next[q];
+      if ((t & 31) == 31 || t == n - 1) {
+        const int tt = (t & ~31) + lane;
+        if (tt <= t) tour[q][tt] = tbuf[q];
+      }
+      lean_mark(svis[q], next[q]);
     }
-    fl[next] = 1;  // every lane stores the same byte
     __syncwarp();
-    cur = next;
-    // the next row's list: usually already in flight from the speculation
-    if (lists && t + 1 < n) {
-      if (sp0.row == next)
-        lr = sp0;
-      else if (sp1.row == next)
-        lr = sp1;
-      else
-        lr = load_list_row(lists, lkey, next);
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      cur[q] = next[q];
+      // the next row's list: usually already in flight from the speculation
+      if (lists && t + 1 < n) {
+        if (sp[q][0].row == next[q]) {
+          lr[q] = sp[q][0];
+        } else if (sp[q][1].row == next[q]) {
+          lr[q] = sp[q][1];
+        } else {
+          lr[q] = load_list_row(lists, lkey, next[q]);
+        }
+      }
     }
   }
 }
 
-// One warp per ant.
+// One warp per kLeanAnts ants (the last warp of an odd m walks its ant twice
+// and writes the same tour twice).
 template <int PREC>
 __global__ void __launch_bounds__(32) construct_lean_kernel(
     const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it_arg,
@@ -285,13 +329,22 @@ __global__ void __launch_bounds__(32) construct_lean_kernel(
     const uint2* __restrict__ lists, const int* __restrict__ lcnt, const uint32_t* __restrict__ lkey) {
   extern __shared__ __align__(16) uint4 lsm[];
   (void)lcnt;
-  const int k = blockIdx.x;
-  if (k >= m) return;
+  const int k0 = blockIdx.x * kLeanAnts;
+  if (k0 >= m) return;
   const int eb = PREC == ACO_FP32 ? 4 : 2;
   const int chunks = (n + 16 / eb - 1) / (16 / eb);
-  uint8_t* flags = reinterpret_cast<uint8_t*>(lsm + ((chunks + 31) / 32) * 32);
+  char* bitmaps = reinterpret_cast<char*>(lsm + ((chunks + 31) / 32) * 32);
+  int k[kLeanAnts];
+  int32_t* tour[kLeanAnts];
+  uint32_t* svis[kLeanAnts];
+#pragma unroll
+  for (int q = 0; q < kLeanAnts; ++q) {
+    k[q] = min(k0 + q, m - 1);
+    tour[q] = tours + (size_t)k[q] * n;
+    svis[q] = reinterpret_cast<uint32_t*>(bitmaps + q * lean_flag_bytes(n));
+  }
   const uint32_t it = it_dev ? *it_dev : it_arg;
-  construct_ant_lean<PREC>(Pv, n, ld, key, it, k, tours + (size_t)k * n, err, lists, lkey, lsm, flags);
+  construct_ants_lean<PREC, kLeanAnts>(Pv, n, ld, key, it, k, tour, err, lists, lkey, lsm, svis);
 }
 
 // Multi-instance form: persistent warps pull (instance, ant) items.
@@ -302,7 +355,7 @@ __global__ void __launch_bounds__(32) batch_construct_lean_kernel(
   extern __shared__ __align__(16) uint4 lsm[];
   const int eb = PREC == ACO_FP32 ? 4 : 2;
   const int max_chunks = (max_n + 16 / eb - 1) / (16 / eb);
-  uint8_t* flags = reinterpret_cast<uint8_t*>(lsm + ((max_chunks + 31) / 32) * 32);
+  uint32_t* svis = reinterpret_cast<uint32_t*>(lsm + ((max_chunks + 31) / 32) * 32);
   const int base = __ldg(ant_off);
   for (;;) {
     int item = 0;
@@ -311,10 +364,10 @@ __global__ void __launch_bounds__(32) batch_construct_lean_kernel(
     if (item >= total) break;
     const int i = find_instance(ant_off, count, base + item);
     const InstDev& I = insts[i];
-    const int k = base + item - __ldg(ant_off + i);
-    construct_ant_lean<PREC>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err, I.lists, I.lkey,
-                             lsm, flags);
-    __syncwarp();  // the flags and the staged row are reused by the next item
+    int k[1] = {base + item - __ldg(ant_off + i)};
+    int32_t* tour[1] = {I.tours + (size_t)k[0] * I.n};
+    uint32_t* sv[1] = {svis};
+    construct_ants_lean<PREC, 1>(I.P, I.n, I.ld, I.key, *I.it, k, tour, err, I.lists, I.lkey, lsm, sv);
   }
 }
 
