@@ -72,9 +72,12 @@ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
   return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
-// r in (0,1): ((x >> 8) | 1) * 2^-24, exact.
+// r in (0,1): ((x >> 8) | 1) * 2^-24, exact.  Built without an int-to-float
+// conversion: with a = x >> 9, the float 1 + a 2^-23 (a as its mantissa)
+// minus (1 - 2^-24) is a 2^-23 + 2^-24 = (2a + 1) 2^-24, representable, so
+// the single addition is exact.
 __device__ __forceinline__ float uniform01(uint32_t x) {
-  return __fmul_rn(__uint2float_rn((x >> 8) | 1u), 0x1p-24f);
+  return __fadd_rn(__uint_as_float(0x3F800000u | (x >> 9)), 0x1p-24f - 1.0f);
 }
 
 // T_start of ant k: Lemire multiply-shift of word 0 of counter (0, 0, k, it).
