@@ -196,7 +196,7 @@ struct aco_batch {
   int* d_counter = nullptr;
   int32_t* d_err = nullptr;
   std::vector<int> active;      // slot ids, n descending
-  int total_rows = 0, total_ants = 0, max_n = 0;
+  int total_rows = 0, total_ants = 0, min_n = 0, max_n = 0;
   size_t dep_smem = 0;          // deposit shared memory of the largest instance
   ConstructShape shape{0, 0, 0};  // forced shape for every class ({0,0,0}: per class)
   struct Class {
@@ -249,6 +249,7 @@ static int batch_refresh(aco_batch* b) {
   std::vector<InstDev> insts(cnt);
   std::vector<int> row_off(cnt + 1, 0), ant_off(cnt + 1, 0);
   b->max_n = 0;
+  b->min_n = cnt > 0 ? b->slots[b->active[0]].p.n : 0;
   b->dep_smem = 0;
   for (int q = 0; q < cnt; ++q) {
     const Slot& s = b->slots[b->active[q]];
@@ -256,6 +257,7 @@ static int batch_refresh(aco_batch* b) {
     row_off[q + 1] = row_off[q] + s.p.n;
     ant_off[q + 1] = ant_off[q] + s.p.m;
     b->max_n = std::max(b->max_n, s.p.n);
+    b->min_n = std::min(b->min_n, s.p.n);
     b->dep_smem = std::max(b->dep_smem, deposit_smem_bytes(s.p.n, deposit_cap(s.p.n, s.p.m)));
   }
   b->total_rows = row_off[cnt];
@@ -326,7 +328,7 @@ static int batch_enqueue(aco_batch* b) {
   ACO_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int) * std::max<size_t>(1, b->classes.size()), st));
   if (b->lean) {  // one persistent lean launch over every ant of every instance
     const int rc = launch_batch_construct_lean(b->d_insts, b->d_ant_off, cnt, b->total_ants, b->d_counter,
-                                               b->d_err, b->prec, b->max_n, b->num_sms, st);
+                                               b->d_err, b->prec, b->min_n, b->max_n, b->num_sms, st);
     if (rc) return rc;
   }
   for (size_t ci = 0; ci < (b->lean ? 0 : b->classes.size()); ++ci) {

@@ -4,6 +4,42 @@
 
 namespace aco {
 
+namespace {
+
+template <int PREC, bool FULL0>
+void launch_lean(int grid, size_t smem, cudaStream_t st, const void* P, int n, int ld, int m, uint2 key,
+                 uint32_t it, const uint32_t* it_dev, int32_t* tours, int32_t* err, const uint2* lists,
+                 const int* lcnt, const uint32_t* lkey) {
+  construct_lean_kernel<PREC, FULL0><<<grid, 32, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err, lists, lcnt,
+                                                             lkey);
+}
+
+template <int PREC, bool FULL0>
+cudaError_t launch_batch_lean(int grid, size_t smem, cudaStream_t st, const InstDev* insts, const int* ant_off,
+                              int count, int total, int* counter, int32_t* err, int max_n, int num_sms) {
+  int blocks = 0;
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_construct_lean_kernel<PREC, FULL0>, 32, smem);
+  if (e != cudaSuccess) return e;
+  grid = (blocks < 1 ? 1 : blocks) * num_sms;
+  if (grid > total) grid = total;
+  if (grid < 1) grid = 1;
+  batch_construct_lean_kernel<PREC, FULL0><<<grid, 32, smem, st>>>(insts, ant_off, count, total, counter, err, max_n);
+  return cudaGetLastError();
+}
+
+template <int PREC, bool FULL0>
+cudaError_t allow_smem(int most) {
+  cudaError_t e = cudaFuncSetAttribute(construct_lean_kernel<PREC, FULL0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_construct_lean_kernel<PREC, FULL0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             most);
+  return e;
+}
+
+}  // namespace
+
 int launch_construct_lean(const void* P, int prec, int n, int ld, int m, uint2 key, uint32_t it,
                           const uint32_t* it_dev, int32_t* tours, int32_t* err, const uint2* lists,
                           const int* lcnt, const uint32_t* lkey, cudaStream_t st) {
@@ -11,18 +47,19 @@ int launch_construct_lean(const void* P, int prec, int n, int ld, int m, uint2 k
   if (n > lean_max_n(eb)) return set_error(ACO_ERR_UNSUPPORTED, "lean construction serves n <= %d", lean_max_n(eb));
   const size_t smem = lean_smem_bytes(n, eb, kLeanAnts);
   const int grid = (m + kLeanAnts - 1) / kLeanAnts;
+  const bool full0 = n >= 32;  // every list then has >= 32 entries
   switch (prec) {
     case ACO_FP32:
-      construct_lean_kernel<ACO_FP32><<<grid, 32, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err, lists,
-                                                              lcnt, lkey);
+      (full0 ? launch_lean<ACO_FP32, true> : launch_lean<ACO_FP32, false>)(grid, smem, st, P, n, ld, m, key, it,
+                                                                         it_dev, tours, err, lists, lcnt, lkey);
       break;
     case ACO_BF16:
-      construct_lean_kernel<ACO_BF16><<<grid, 32, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err, lists,
-                                                              lcnt, lkey);
+      (full0 ? launch_lean<ACO_BF16, true> : launch_lean<ACO_BF16, false>)(grid, smem, st, P, n, ld, m, key, it,
+                                                                         it_dev, tours, err, lists, lcnt, lkey);
       break;
     case ACO_FP16:
-      construct_lean_kernel<ACO_FP16><<<grid, 32, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err, lists,
-                                                              lcnt, lkey);
+      (full0 ? launch_lean<ACO_FP16, true> : launch_lean<ACO_FP16, false>)(grid, smem, st, P, n, ld, m, key, it,
+                                                                         it_dev, tours, err, lists, lcnt, lkey);
       break;
     default:
       return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
@@ -32,54 +69,37 @@ int launch_construct_lean(const void* P, int prec, int n, int ld, int m, uint2 k
 }
 
 int launch_batch_construct_lean(const InstDev* insts, const int* ant_off, int count, int total,
-                                int* counter, int32_t* err, int prec, int max_n, int num_sms,
+                                int* counter, int32_t* err, int prec, int min_n, int max_n, int num_sms,
                                 cudaStream_t st) {
   const int eb = prec == ACO_FP32 ? 4 : 2;
   if (max_n > lean_max_n(eb)) return set_error(ACO_ERR_UNSUPPORTED, "lean construction serves n <= %d", lean_max_n(eb));
   const size_t smem = lean_smem_bytes(max_n, eb);
-  int blocks = 0;
-  cudaError_t e = cudaSuccess;
+  const bool full0 = min_n >= 32;
+  cudaError_t e;
   switch (prec) {
     case ACO_FP32:
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_construct_lean_kernel<ACO_FP32>, 32, smem);
+      e = (full0 ? launch_batch_lean<ACO_FP32, true> : launch_batch_lean<ACO_FP32, false>)(
+          0, smem, st, insts, ant_off, count, total, counter, err, max_n, num_sms);
       break;
     case ACO_BF16:
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_construct_lean_kernel<ACO_BF16>, 32, smem);
+      e = (full0 ? launch_batch_lean<ACO_BF16, true> : launch_batch_lean<ACO_BF16, false>)(
+          0, smem, st, insts, ant_off, count, total, counter, err, max_n, num_sms);
       break;
     default:
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_construct_lean_kernel<ACO_FP16>, 32, smem);
+      e = (full0 ? launch_batch_lean<ACO_FP16, true> : launch_batch_lean<ACO_FP16, false>)(
+          0, smem, st, insts, ant_off, count, total, counter, err, max_n, num_sms);
   }
-  if (e != cudaSuccess) return cuda_error(e, "occupancy query (lean)");
-  int grid = (blocks < 1 ? 1 : blocks) * num_sms;
-  if (grid > total) grid = total;
-  if (grid < 1) grid = 1;
-  switch (prec) {
-    case ACO_FP32:
-      batch_construct_lean_kernel<ACO_FP32><<<grid, 32, smem, st>>>(insts, ant_off, count, total, counter, err, max_n);
-      break;
-    case ACO_BF16:
-      batch_construct_lean_kernel<ACO_BF16><<<grid, 32, smem, st>>>(insts, ant_off, count, total, counter, err, max_n);
-      break;
-    default:
-      batch_construct_lean_kernel<ACO_FP16><<<grid, 32, smem, st>>>(insts, ant_off, count, total, counter, err, max_n);
-  }
-  e = cudaGetLastError();
   return e == cudaSuccess ? ACO_OK : cuda_error(e, "batch_construct_lean_kernel launch");
 }
 
 int prepare_construct_lean() {
   const int most = (int)lean_smem_bytes(lean_max_n(4), 4, kLeanAnts);
-  cudaError_t e = cudaFuncSetAttribute(construct_lean_kernel<ACO_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(construct_lean_kernel<ACO_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(construct_lean_kernel<ACO_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(batch_construct_lean_kernel<ACO_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(batch_construct_lean_kernel<ACO_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(batch_construct_lean_kernel<ACO_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  cudaError_t e = allow_smem<ACO_FP32, false>(most);
+  if (e == cudaSuccess) e = allow_smem<ACO_FP32, true>(most);
+  if (e == cudaSuccess) e = allow_smem<ACO_BF16, false>(most);
+  if (e == cudaSuccess) e = allow_smem<ACO_BF16, true>(most);
+  if (e == cudaSuccess) e = allow_smem<ACO_FP16, false>(most);
+  if (e == cudaSuccess) e = allow_smem<ACO_FP16, true>(most);
   return e == cudaSuccess ? ACO_OK : cuda_error(e, "cudaFuncSetAttribute(lean)");
 }
 

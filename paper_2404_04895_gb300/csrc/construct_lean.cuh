@@ -194,7 +194,10 @@ __device__ __forceinline__ int lean_full_scan(const char* __restrict__ row, int 
 }
 
 // NA ants walked by one warp: ants k[q], tours tour[q], visited flags svis[q].
-template <int PREC, int NA>
+// FULL0: every list has >= 32 entries (n >= 32: a list holds at least
+// min(kListTarget, n) of the row's n columns), so its first round has no
+// padded slot.
+template <int PREC, int NA, bool FULL0>
 __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv, int n, int ld, uint2 key,
                                                     uint32_t it, const int* k, int32_t* const* tour,
                                                     int32_t* __restrict__ err,
@@ -207,19 +210,21 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
   const size_t row_bytes = (size_t)ld * E::BYTES;
   const PhiloxKeys ks = philox_keys(key);
 
-  int cur[NA], tbuf[NA];
+  int cur[NA];
   ListRow lr[NA], sp[NA][2];
 #pragma unroll
   for (int q = 0; q < NA; ++q) {
     for (int w = lane; w < (int)(lean_flag_bytes(n) / 4); w += 32) svis[q][w] = 0u;
     cur[q] = start_city(key, it, (uint32_t)k[q], n);
-    tbuf[q] = cur[q];  // the tour is written 32 steps at a time: lane (t mod 32) keeps step t
     lr[q].row = sp[q][0].row = sp[q][1].row = -1;
   }
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < NA; ++q) {
-    if (lane == 0) lean_mark(svis[q], cur[q]);
+    if (lane == 0) {
+      lean_mark(svis[q], cur[q]);
+      tour[q][0] = cur[q];
+    }
     if (lists) lr[q] = load_list_row(lists, lkey, cur[q]);
   }
   __syncwarp();
@@ -238,14 +243,14 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
       more[q] = false;
       if (lists) {
         const uint2 e = lr[q].e;
-        const bool valid = e.y != kListPad;
-        const int j = valid ? (int)e.y : 0;
+        const bool valid = FULL0 || e.y != kListPad;
+        const int j = FULL0 ? (int)e.y : (valid ? (int)e.y : 0);
         uint4 xc = make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k[q], it);
         const bool unvisited = valid && !lean_visited(svis[q], j);
         philox_round(xc, ks, 0);
         philox_round(xc, ks, 1);
         philox_round(xc, ks, 2);
-        const unsigned vm = __ballot_sync(ACO_FULL_MASK, valid);
+        const unsigned vm = FULL0 ? 0xFFFFFFFFu : __ballot_sync(ACO_FULL_MASK, valid);
         const unsigned un = __ballot_sync(ACO_FULL_MASK, unvisited);
         philox_round(xc, ks, 3);
         philox_round(xc, ks, 4);
@@ -295,11 +300,7 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
     }
 #pragma unroll
     for (int q = 0; q < NA; ++q) {
-      if (lane == (t & 31)) tbuf[q] = next[q];
-      if ((t & 31) == 31 || t == n - 1) {
-        const int tt = (t & ~31) + lane;
-        if (tt <= t) tour[q][tt] = tbuf[q];
-      }
+      if (lane == 0) tour[q][t] = next[q];
       lean_mark(svis[q], next[q]);
     }
     __syncwarp();
@@ -307,7 +308,7 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
     for (int q = 0; q < NA; ++q) {
       cur[q] = next[q];
       // the next row's list: usually already in flight from the speculation
-      if (lists && t + 1 < n) {
+      if (lists) {  // after the last step: one unused load of a valid row
         if (sp[q][0].row == next[q]) {
           lr[q] = sp[q][0];
         } else if (sp[q][1].row == next[q]) {
@@ -321,8 +322,8 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
 }
 
 // One warp per kLeanAnts ants (the last warp of an odd m walks its ant twice
-// and writes the same tour twice).
-template <int PREC>
+// and writes the same tour twice).  FULL0 as construct_ants_lean (n >= 32).
+template <int PREC, bool FULL0>
 __global__ void __launch_bounds__(32) construct_lean_kernel(
     const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it_arg,
     const uint32_t* __restrict__ it_dev, int32_t* __restrict__ tours, int32_t* __restrict__ err,
@@ -344,11 +345,12 @@ __global__ void __launch_bounds__(32) construct_lean_kernel(
     svis[q] = reinterpret_cast<uint32_t*>(bitmaps + q * lean_flag_bytes(n));
   }
   const uint32_t it = it_dev ? *it_dev : it_arg;
-  construct_ants_lean<PREC, kLeanAnts>(Pv, n, ld, key, it, k, tour, err, lists, lkey, lsm, svis);
+  construct_ants_lean<PREC, kLeanAnts, FULL0>(Pv, n, ld, key, it, k, tour, err, lists, lkey, lsm, svis);
 }
 
-// Multi-instance form: persistent warps pull (instance, ant) items.
-template <int PREC>
+// Multi-instance form: persistent warps pull (instance, ant) items.  FULL0:
+// every instance has n >= 32.
+template <int PREC, bool FULL0>
 __global__ void __launch_bounds__(32) batch_construct_lean_kernel(
     const InstDev* __restrict__ insts, const int* __restrict__ ant_off, int count, int total,
     int* __restrict__ counter, int32_t* __restrict__ err, int max_n) {
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(32) batch_construct_lean_kernel(
     int k[1] = {base + item - __ldg(ant_off + i)};
     int32_t* tour[1] = {I.tours + (size_t)k[0] * I.n};
     uint32_t* sv[1] = {svis};
-    construct_ants_lean<PREC, 1>(I.P, I.n, I.ld, I.key, *I.it, k, tour, err, I.lists, I.lkey, lsm, sv);
+    construct_ants_lean<PREC, 1, FULL0>(I.P, I.n, I.ld, I.key, *I.it, k, tour, err, I.lists, I.lkey, lsm, sv);
   }
 }
 

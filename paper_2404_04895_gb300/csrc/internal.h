@@ -76,7 +76,7 @@ int launch_construct_lean(const void* P, int prec, int n, int ld, int m, uint2 k
                           const uint32_t* it_dev, int32_t* tours, int32_t* err, const uint2* lists,
                           const int* lcnt, const uint32_t* lkey, cudaStream_t st);
 int launch_batch_construct_lean(const InstDev* insts, const int* ant_off, int count, int total,
-                                int* counter, int32_t* err, int prec, int max_n, int num_sms,
+                                int* counter, int32_t* err, int prec, int min_n, int max_n, int num_sms,
                                 cudaStream_t st);
 int prepare_construct_lean();
 // Roulette-wheel construction (Sec. 2.4 baseline), n <= 16384, one warp per ant.
