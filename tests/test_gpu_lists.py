@@ -111,6 +111,24 @@ def test_construct_with_lists_equals_full_scan_and_oracle(orc, prec, n, m):
         assert np.array_equal(host(t_list), ref), shp
 
 
+@pytest.mark.parametrize("prec", [B.FP32, B.BF16, B.FP16])
+@pytest.mark.parametrize("n", [31, 32, 33, 40])
+def test_lean_kernel_around_full_first_round(orc, prec, n):
+    """n >= 32 selects the lean instantiation whose first list round has no
+    padded slot (every list then holds >= 32 entries); both sides of the
+    switch give the oracle's tours."""
+    m = 37
+    Pv, bits = _P(orc, n, 11 + n, prec)
+    ld = B.ld_of(n)
+    Pd = P_device(Pv, bits, prec, ld)
+    lists, lcnt, lkey = _build(Pd, prec, n, ld)
+    assert int(host(lcnt).min()) >= min(n, 32)
+    ref = orc.construct(Pv, 9, 4, 0, m)
+    t = torch.zeros((m, n), dtype=torch.int32, device="cuda")
+    B.op_construct_ex(Pd, prec, n, ld, m, 9, 4, t, lists, lcnt, lkey, shape=(1, 0, 2))
+    assert np.array_equal(host(t), ref)
+
+
 def test_tie_heavy_rows_with_lists(orc):
     n, m = 300, 50
     Pv, bits = _P(orc, n, 1, B.FP32, ties=True)
