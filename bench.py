@@ -415,7 +415,7 @@ def run_roulette(B, torch, w, coords, seed, steps=10):
         out[r] = {"ms_per_iter": round(ms, 3), "best_len_after_budget": s.best()[1]}
         s.close()
     out["protocol"] = (f"{steps} timed iterations after 2; best length after {w['iters']} iterations, "
-                       f"Philox seed {seed}; rw = exact-integer roulette wheel, one warp per ant")
+                       f"Philox seed {seed}; rw = exact-integer roulette wheel, one 256-thread CTA per ant, the row staged by one TMA bulk copy per step")
     return out
 
 

@@ -11,11 +11,14 @@
 // Integer sums do not depend on their order, so the warp's parallel scan
 // picks the same city as the oracle's sequential one.
 //
-// One warp per ant (n <= 16384).  Per step the row is staged in shared memory
-// by cp.async; lane l owns the contiguous columns [l*B, (l+1)*B), B odd so
-// that the lanes' reads fall in different banks; two passes over the block
-// (maximum, then quanta), an exclusive warp scan of the lanes' 64-bit sums,
-// and the lane whose range holds v walks its block in column order.
+// One CTA of kRwThreads threads per ant (n <= 16384).  Per step the row is
+// staged in shared memory by one TMA bulk copy (cp.async.bulk, completion on
+// an mbarrier); thread q owns the contiguous columns [q*B, (q+1)*B), B a
+// multiple of 4 with B/4 odd, read 4 columns at a time (one vector load of
+// values, one word of flags) so that the threads of a load phase hit
+// different banks; two passes over the block (maximum, then quanta), a
+// block-wide exclusive scan of the threads' 64-bit sums, and the thread whose
+// range holds v walks its block in column order.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -28,21 +31,74 @@ namespace aco {
 namespace {
 
 constexpr int kRwMaxN = 16384;
+constexpr int kRwThreads = 256;
+constexpr uint32_t kRwSpin = 1u << 20;  // bound on one mbarrier wait (polls)
 
-__host__ __device__ inline int rw_block(int n) { return ((n + 31) / 32) | 1; }
+__host__ __device__ inline int rw_block(int n) {
+  const int q = (n + kRwThreads - 1) / kRwThreads;  // columns per thread, at least
+  return 4 * (((q + 3) / 4) | 1);
+}
+__host__ __device__ inline size_t rw_row_bytes(int n, int eb) { return ((size_t)n * eb + 15) / 16 * 16; }
+__host__ __device__ inline size_t rw_flag_bytes(int n) { return ((size_t)n + 15) / 16 * 16; }
+// control block after the row and the flags: the mbarrier (8 bytes, 16
+// reserved), the warps' 64-bit sums, maxima and lowest unvisited columns, the
+// chosen column
+constexpr int kRwCtlBytes = 16 + 8 * (kRwThreads / 32) + 4 * (kRwThreads / 32) + 4 * (kRwThreads / 32) + 4;
+static_assert(kRwCtlBytes <= 256, "control block");
+// staged row, visited flags (one byte per city), control block
+__host__ __device__ inline size_t rw_smem_bytes(int n, int eb) { return rw_row_bytes(n, eb) + rw_flag_bytes(n) + 256; }
 
-__host__ __device__ inline size_t rw_smem_bytes(int n, int eb) {
-  const size_t row = ((size_t)n * eb + 15) / 16 * 16;
-  return row + (size_t)((n + 31) / 32) * 4;
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// fp32 bit pattern of the stored element j of a staged row
+// One bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory, completing on the mbarrier.  The proxy fence
+// orders this thread's (and, after a CTA barrier, every thread's) earlier
+// generic accesses to the buffer before the copy's writes.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Waits until the mbarrier's phase `parity` has completed, for at most
+// kRwSpin polls; false if it has not.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kRwSpin; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// fp32 bit patterns of the stored elements j..j+3 of a staged row (j a
+// multiple of 4: a 16- or 8-byte aligned load)
 template <int PREC>
-__device__ __forceinline__ uint32_t rw_bits(const void* srow, int j) {
-  if (PREC == ACO_FP32) return static_cast<const uint32_t*>(srow)[j];
-  const uint32_t h = static_cast<const unsigned short*>(srow)[j];
-  if (PREC == ACO_BF16) return h << 16;
-  return __float_as_uint(__half2float(__ushort_as_half((unsigned short)h)));
+__device__ __forceinline__ void rw_bits4(const void* srow, int j, uint32_t b[4]) {
+  if (PREC == ACO_FP32) {
+    const uint4 v = *reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(srow) + j);
+    b[0] = v.x;
+    b[1] = v.y;
+    b[2] = v.z;
+    b[3] = v.w;
+  } else {
+    const uint2 v = *reinterpret_cast<const uint2*>(static_cast<const unsigned short*>(srow) + j);
+    const uint32_t h[4] = {v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      b[i] = PREC == ACO_BF16 ? h[i] << 16 : __float_as_uint(__half2float(__ushort_as_half((unsigned short)h[i])));
+  }
 }
 
 // floor(log2 p) of a positive finite fp32 bit pattern
@@ -68,102 +124,142 @@ __device__ __forceinline__ uint64_t shfl_up_u64(uint64_t x, int off) {
   return ((uint64_t)hi << 32) | lo;
 }
 
-__device__ __forceinline__ uint64_t shfl_u64(uint64_t x, int src) {
-  const uint32_t lo = __shfl_sync(ACO_FULL_MASK, (uint32_t)x, src);
-  const uint32_t hi = __shfl_sync(ACO_FULL_MASK, (uint32_t)(x >> 32), src);
-  return ((uint64_t)hi << 32) | lo;
-}
-
 template <int PREC>
-__global__ void __launch_bounds__(32) construct_rw_kernel(const void* __restrict__ Pv, int n, int ld, int m,
-                                                          uint2 key, uint32_t it_arg,
-                                                          const uint32_t* __restrict__ it_dev,
-                                                          int32_t* __restrict__ tours, int32_t* __restrict__ err) {
+__global__ void __launch_bounds__(kRwThreads) construct_rw_kernel(const void* __restrict__ Pv, int n, int ld, int m,
+                                                                  uint2 key, uint32_t it_arg,
+                                                                  const uint32_t* __restrict__ it_dev,
+                                                                  int32_t* __restrict__ tours,
+                                                                  int32_t* __restrict__ err) {
   extern __shared__ __align__(16) uint4 rsm[];
   const int k = blockIdx.x;
   if (k >= m) return;
-  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kRwThreads / 32;
   constexpr int EB = PREC == ACO_FP32 ? 4 : 2;
   const uint32_t it = it_dev ? *it_dev : it_arg;
-  const int nchunks = (n * EB + 15) / 16;
-  uint32_t* svis = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(rsm) + (size_t)nchunks * 16);
-  const int nwords = (n + 31) / 32;
+  char* sbase = reinterpret_cast<char*>(rsm);
+  const uint32_t row_bytes = (uint32_t)rw_row_bytes(n, EB);  // <= ld * EB: a row's padded span
+  volatile uint8_t* flags = reinterpret_cast<uint8_t*>(sbase + row_bytes);
+  char* ctl = sbase + row_bytes + rw_flag_bytes(n);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ctl);
+  unsigned long long* wsum = reinterpret_cast<unsigned long long*>(ctl + 16);  // [NW]
+  uint32_t* wmax = reinterpret_cast<uint32_t*>(ctl + 16 + 8 * NW);              // [NW]
+  int* wfirst = reinterpret_cast<int*>(ctl + 16 + 12 * NW);                     // [NW]
+  volatile int* spick = reinterpret_cast<int*>(ctl + 16 + 16 * NW);
+  const uint32_t sbar = smem_addr(bar), srow = smem_addr(sbase);
   const int B = rw_block(n);
-  const int j0 = min(n, lane * B), j1 = min(n, j0 + B);
+  const int j0 = min(n, tid * B), j1 = min(n, j0 + B);
   int32_t* tour = tours + (size_t)k * n;
-  const size_t row_bytes = (size_t)ld * EB;
+  const char* __restrict__ P = static_cast<const char*>(Pv);
+  const size_t row_stride = (size_t)ld * EB;
 
-  for (int q = lane; q < nwords; q += 32) svis[q] = 0u;
-  __syncwarp();
+  for (int q = tid; q < (int)rw_flag_bytes(n); q += kRwThreads) flags[q] = 0;
+  if (tid == 0) mbar_init(sbar, 1u);
   int cur = start_city(key, it, (uint32_t)k, n);
-  if (lane == 0) {
+  __syncthreads();
+  if (tid == 0) {
+    flags[cur] = 1;
     tour[0] = cur;
-    svis[cur >> 5] |= 1u << (cur & 31);
   }
-  __syncwarp();
-
+  uint32_t phase = 0u;
   for (int t = 1; t < n; ++t) {
-    const uint4* __restrict__ row4 = reinterpret_cast<const uint4*>(static_cast<const char*>(Pv) + (size_t)cur * row_bytes);
-    for (int c = lane; c < nchunks; c += 32) cp_async16_pred(rsm + c, row4 + c, true);
-    cp_async_wait_all();
-    __syncwarp();  // every lane's copies have landed
-
-    // pass 1: the largest unvisited value; each lane's first unvisited column
+    if (tid == 0) bulk_load(srow, P + (size_t)cur * row_stride, row_bytes, sbar);
+    const bool landed = mbar_wait(sbar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!landed)) {  // a copy that never lands: report, wait once more, stop
+      if (tid == 0 && err) atomicExch(err, kErrConstruct);
+      mbar_wait(sbar, phase ^ 1u);
+      return;
+    }
+    // pass 1: the largest unvisited value; the lowest unvisited column
     uint32_t mx = 0u;
     int first = 0x7FFFFFFF;
-    for (int j = j0; j < j1; ++j) {
-      if ((svis[j >> 5] >> (j & 31)) & 1u) continue;
-      first = min(first, j);
-      mx = max(mx, rw_bits<PREC>(rsm, j));
+    for (int j = j0; j < j1; j += 4) {
+      const uint32_t f = *reinterpret_cast<const volatile uint32_t*>(flags + j);
+      uint32_t b[4];
+      rw_bits4<PREC>(sbase, j, b);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (j + i >= j1 || ((f >> (8 * i)) & 0xFFu)) continue;
+        first = min(first, j + i);
+        mx = max(mx, b[i]);
+      }
     }
     mx = __reduce_max_sync(ACO_FULL_MASK, mx);
-    const int lowest = (int)__reduce_min_sync(ACO_FULL_MASK, (uint32_t)first);
-    int next = -1;
+    first = (int)__reduce_min_sync(ACO_FULL_MASK, (uint32_t)first);
+    if (lane == 0) {
+      wmax[warp] = mx;
+      wfirst[warp] = first;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      mx = max(mx, wmax[w]);
+      first = min(first, wfirst[w]);
+    }
+    int next;
     if (mx == 0u) {
-      next = lowest < n ? lowest : -1;  // every unvisited value is 0
+      next = first < n ? first : -1;  // every unvisited value is 0
     } else {
       const int e = rw_exponent(mx);
-      // pass 2: this lane's sum of quanta, then an exclusive warp scan
+      // pass 2: this thread's sum of quanta, then a block-wide exclusive scan
       uint64_t s = 0ull;
-      for (int j = j0; j < j1; ++j)
-        if (!((svis[j >> 5] >> (j & 31)) & 1u)) s += rw_quantum(rw_bits<PREC>(rsm, j), e);
+      for (int j = j0; j < j1; j += 4) {
+        const uint32_t f = *reinterpret_cast<const volatile uint32_t*>(flags + j);
+        uint32_t b[4];
+        rw_bits4<PREC>(sbase, j, b);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (j + i < j1 && !((f >> (8 * i)) & 0xFFu)) s += rw_quantum(b[i], e);
+      }
       uint64_t inc = s;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
         const uint64_t v = shfl_up_u64(inc, off);
         if (lane >= off) inc += v;
       }
-      const uint64_t S = shfl_u64(inc, 31);
-      const uint64_t excl = inc - s;
+      if (lane == 31) wsum[warp] = inc;
+      __syncthreads();
+      uint64_t below = 0ull, S = 0ull;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint64_t x = wsum[w];
+        if (w < warp) below += x;
+        S += x;
+      }
+      const uint64_t incl = below + inc, excl = incl - s;
       const uint4 x = philox(make_uint4(1u << 30, (uint32_t)t, (uint32_t)k, it), key);
       const uint64_t u = ((uint64_t)x.x << 32) | (uint64_t)x.y;
       const uint64_t v = __umul64hi(u, S);
-      const bool mine = excl <= v && v < inc;
-      int pick = -1;
-      if (mine) {
+      if (excl <= v && v < incl) {  // exactly one thread: the ranges partition [0, S)
         uint64_t run = excl;
-        for (int j = j0; j < j1; ++j) {
-          if ((svis[j >> 5] >> (j & 31)) & 1u) continue;
-          run += rw_quantum(rw_bits<PREC>(rsm, j), e);
-          if (run > v) {
-            pick = j;
-            break;
+        int pick = -1;
+        for (int j = j0; j < j1 && pick < 0; j += 4) {
+          const uint32_t f = *reinterpret_cast<const volatile uint32_t*>(flags + j);
+          uint32_t b[4];
+          rw_bits4<PREC>(sbase, j, b);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (pick >= 0 || j + i >= j1 || ((f >> (8 * i)) & 0xFFu)) continue;
+            run += rw_quantum(b[i], e);
+            if (run > v) pick = j + i;
           }
         }
+        *spick = pick;
       }
-      const unsigned own = __ballot_sync(ACO_FULL_MASK, mine);
-      next = own ? __shfl_sync(ACO_FULL_MASK, pick, __ffs(own) - 1) : -1;
+      __syncthreads();
+      next = *spick;
     }
     if (next < 0 || next >= n) {  // cannot happen for valid input
-      if (lane == 0 && err) atomicExch(err, kErrConstruct);
+      if (tid == 0 && err) atomicExch(err, kErrConstruct);
       break;
     }
-    if (lane == 0) {
+    if (tid == 0) {
+      flags[next] = 1;
       tour[t] = next;
-      svis[next >> 5] |= 1u << (next & 31);
     }
-    __syncwarp();  // the bitmap update, and the staged row is free again
     cur = next;
+    __syncthreads();  // the flag is set, and every read of the staged row and the sums is done
   }
 }
 
@@ -176,13 +272,13 @@ int launch_construct_rw(const void* P, int prec, int n, int ld, int m, uint2 key
   const size_t smem = rw_smem_bytes(n, eb);
   switch (prec) {
     case ACO_FP32:
-      construct_rw_kernel<ACO_FP32><<<m, 32, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err);
+      construct_rw_kernel<ACO_FP32><<<m, kRwThreads, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err);
       break;
     case ACO_BF16:
-      construct_rw_kernel<ACO_BF16><<<m, 32, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err);
+      construct_rw_kernel<ACO_BF16><<<m, kRwThreads, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err);
       break;
     case ACO_FP16:
-      construct_rw_kernel<ACO_FP16><<<m, 32, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err);
+      construct_rw_kernel<ACO_FP16><<<m, kRwThreads, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err);
       break;
     default:
       return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
