@@ -6,12 +6,26 @@ namespace aco {
 
 namespace {
 
-template <int PREC, bool FULL0>
+template <int PREC, bool FULL0, bool LISTS>
 void launch_lean(int grid, size_t smem, cudaStream_t st, const void* P, int n, int ld, int m, uint2 key,
                  uint32_t it, const uint32_t* it_dev, int32_t* tours, int32_t* err, const uint2* lists,
                  const int* lcnt, const uint32_t* lkey) {
-  construct_lean_kernel<PREC, FULL0><<<grid, 32, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err, lists, lcnt,
-                                                             lkey);
+  construct_lean_kernel<PREC, FULL0, LISTS><<<grid, 32, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err, lists,
+                                                                    lcnt, lkey);
+}
+
+// the lean kernel for this precision: lists and a full first round, lists
+// only, or compact scans only
+template <int PREC>
+void launch_lean_for(bool lists, bool full0, int grid, size_t smem, cudaStream_t st, const void* P, int n, int ld,
+                     int m, uint2 key, uint32_t it, const uint32_t* it_dev, int32_t* tours, int32_t* err,
+                     const uint2* L, const int* lcnt, const uint32_t* lkey) {
+  if (!lists)
+    launch_lean<PREC, false, false>(grid, smem, st, P, n, ld, m, key, it, it_dev, tours, err, L, lcnt, lkey);
+  else if (full0)
+    launch_lean<PREC, true, true>(grid, smem, st, P, n, ld, m, key, it, it_dev, tours, err, L, lcnt, lkey);
+  else
+    launch_lean<PREC, false, true>(grid, smem, st, P, n, ld, m, key, it, it_dev, tours, err, L, lcnt, lkey);
 }
 
 template <int PREC, bool FULL0>
@@ -30,8 +44,11 @@ cudaError_t launch_batch_lean(int grid, size_t smem, cudaStream_t st, const Inst
 
 template <int PREC, bool FULL0>
 cudaError_t allow_smem(int most) {
-  cudaError_t e = cudaFuncSetAttribute(construct_lean_kernel<PREC, FULL0>,
+  cudaError_t e = cudaFuncSetAttribute(construct_lean_kernel<PREC, FULL0, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  if (e == cudaSuccess && !FULL0)
+    e = cudaFuncSetAttribute(construct_lean_kernel<PREC, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             most);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(batch_construct_lean_kernel<PREC, FULL0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              most);
@@ -48,18 +65,19 @@ int launch_construct_lean(const void* P, int prec, int n, int ld, int m, uint2 k
   const size_t smem = lean_smem_bytes(n, eb, kLeanAnts);
   const int grid = (m + kLeanAnts - 1) / kLeanAnts;
   const bool full0 = n >= 32;  // every list then has >= 32 entries
+  const bool has_lists = lists != nullptr;
   switch (prec) {
     case ACO_FP32:
-      (full0 ? launch_lean<ACO_FP32, true> : launch_lean<ACO_FP32, false>)(grid, smem, st, P, n, ld, m, key, it,
-                                                                         it_dev, tours, err, lists, lcnt, lkey);
+      launch_lean_for<ACO_FP32>(has_lists, full0, grid, smem, st, P, n, ld, m, key, it, it_dev, tours, err, lists,
+                                lcnt, lkey);
       break;
     case ACO_BF16:
-      (full0 ? launch_lean<ACO_BF16, true> : launch_lean<ACO_BF16, false>)(grid, smem, st, P, n, ld, m, key, it,
-                                                                         it_dev, tours, err, lists, lcnt, lkey);
+      launch_lean_for<ACO_BF16>(has_lists, full0, grid, smem, st, P, n, ld, m, key, it, it_dev, tours, err, lists,
+                                lcnt, lkey);
       break;
     case ACO_FP16:
-      (full0 ? launch_lean<ACO_FP16, true> : launch_lean<ACO_FP16, false>)(grid, smem, st, P, n, ld, m, key, it,
-                                                                         it_dev, tours, err, lists, lcnt, lkey);
+      launch_lean_for<ACO_FP16>(has_lists, full0, grid, smem, st, P, n, ld, m, key, it, it_dev, tours, err, lists,
+                                lcnt, lkey);
       break;
     default:
       return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
