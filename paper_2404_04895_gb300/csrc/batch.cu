@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <vector>
 
@@ -41,8 +42,12 @@ __global__ void __launch_bounds__(256) batch_build_P_kernel(const InstDev* __res
     inv_gamma = I.sched[it < (uint32_t)I.n_sched ? it : (uint32_t)(I.n_sched - 1)];
   }
   const size_t eb = PREC == ACO_FP32 ? 4 : 2;
-  build_P_row<PREC>(I.tau + (size_t)row * I.ld, I.H + (size_t)row * I.ld, I.n, I.ld, row, I.alpha,
-                    inv_gamma, static_cast<char*>(I.P) + (size_t)row * I.ld * eb, red);
+  void* P_row = static_cast<char*>(I.P) + (size_t)row * I.ld * eb;
+  const char* tau_row = reinterpret_cast<const char*>(I.tau) + (size_t)row * I.ld * (I.tau_bf16 ? 2 : 4);
+  if (I.tau_bf16)
+    build_P_row<PREC, true>(tau_row, I.H + (size_t)row * I.ld, I.n, I.ld, row, I.alpha, inv_gamma, P_row, red);
+  else
+    build_P_row<PREC, false>(tau_row, I.H + (size_t)row * I.ld, I.n, I.ld, row, I.alpha, inv_gamma, P_row, red);
 }
 
 template <int PREC>
@@ -95,8 +100,12 @@ __global__ void __launch_bounds__(kDepThreads) batch_deposit_kernel(const InstDe
   const InstDev& I = insts[i];
   const int a = r - __ldg(row_off + i);
   const int2 d = *I.dep;
-  deposit_row_exact(I.tau + (size_t)a * I.ld, I.n, reinterpret_cast<const int2*>(I.nbr) + (size_t)a * I.m,
-                    I.c, I.m, 1.0f - I.rho, d.x, d.y, deposit_cap(I.n, I.m), smem);
+  const int2* nbr_row = reinterpret_cast<const int2*>(I.nbr) + (size_t)a * I.m;
+  char* tau_row = reinterpret_cast<char*>(I.tau) + (size_t)a * I.ld * (I.tau_bf16 ? 2 : 4);
+  if (I.tau_bf16)
+    deposit_row_exact<true>(tau_row, I.n, nbr_row, I.c, I.m, 1.0f - I.rho, d.x, d.y, deposit_cap(I.n, I.m), smem);
+  else
+    deposit_row_exact<false>(tau_row, I.n, nbr_row, I.c, I.m, 1.0f - I.rho, d.x, d.y, deposit_cap(I.n, I.m), smem);
 }
 
 // ------------------------------------------------------------------ arena
@@ -454,7 +463,6 @@ int aco_batch_add(aco_batch* b, const float* coords_host, const aco_params* p, i
   if (p->prec != b->prec) return set_error(ACO_ERR_ARG, "instance precision %d differs from the batch's %d", p->prec, b->prec);
   if (iters_budget < 0) return set_error(ACO_ERR_ARG, "iters_budget must be >= 0");
   if (p->roulette == ACO_RW) return set_error(ACO_ERR_UNSUPPORTED, "batches run IR / AdaIR instances only");
-  if (p->tau_prec != ACO_FP32) return set_error(ACO_ERR_UNSUPPORTED, "batches store tau in fp32");
   int q = 0;
   while (q < (int)b->slots.size() && b->slots[q].used) ++q;
   if (q == (int)b->slots.size()) return set_error(ACO_ERR_OOM, "all %d batch slots are in use", q);
@@ -544,6 +552,16 @@ int aco_batch_get_tau(aco_batch* b, int slot, float* tau_host) {
     return set_error(ACO_ERR_ARG, "invalid argument");
   const Slot& s = b->slots[slot];
   ACO_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  if (s.dev.tau_bf16) {  // bf16 storage: widened exactly to fp32
+    std::vector<uint16_t> h((size_t)s.p.n * s.p.n);
+    ACO_CUDA_TRY(cudaMemcpy2D(h.data(), sizeof(uint16_t) * s.p.n, s.dev.tau, sizeof(uint16_t) * s.dev.ld,
+                              sizeof(uint16_t) * s.p.n, s.p.n, cudaMemcpyDeviceToHost));
+    for (size_t q = 0; q < h.size(); ++q) {
+      const uint32_t bits = (uint32_t)h[q] << 16;
+      std::memcpy(tau_host + q, &bits, 4);
+    }
+    return ACO_OK;
+  }
   ACO_CUDA_TRY(cudaMemcpy2D(tau_host, sizeof(float) * s.p.n, s.dev.tau, sizeof(float) * s.dev.ld,
                             sizeof(float) * s.p.n, s.p.n, cudaMemcpyDeviceToHost));
   return ACO_OK;

@@ -13,7 +13,8 @@ struct InstDev {
   float rho, Q;
   uint2 key;                      // Philox key (seed low, high)
   const float* H;                 // eta^beta, n x ld
-  float* tau;                     // n x ld
+  float* tau;                     // n x ld, fp32 (tau_bf16: bf16 bit patterns, n x ld x 2 bytes)
+  int tau_bf16;                   // M_tau stored in bfloat16
   void* P;                        // M_p, n x ld at the batch precision
   const double* D;                // n x n
   int32_t* tours;                 // m x n

@@ -260,6 +260,7 @@ int instance_bind(const aco_params& p, unsigned char* ws, InstDev* d, cudaStream
   x.D = reinterpret_cast<double*>(ws + L.D);
   x.H = reinterpret_cast<float*>(ws + L.H);
   x.tau = reinterpret_cast<float*>(ws + L.tau);
+  x.tau_bf16 = p.tau_prec == ACO_BF16 ? 1 : 0;
   x.P = ws + L.P;
   x.tours = reinterpret_cast<int32_t*>(ws + L.tours);
   x.L = reinterpret_cast<double*>(ws + L.L);

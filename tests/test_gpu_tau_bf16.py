@@ -49,5 +49,33 @@ def test_tau_bf16_refusals():
         B.Solver(xy, m=10, tau_prec="fp16")
     bt = B.Batch(2, B.instance_bytes(60, 10) + (1 << 20))
     with pytest.raises(B.AcoError):
-        bt.add(xy, 10, tau_prec="bf16")
+        bt.add(xy, 10, tau_prec="fp16")
+    bt.close()
+
+
+def test_tau_bf16_in_batches_matches_standalone():
+    """Instances storing M_tau in bf16 and in fp32, side by side in one batch,
+    end exactly where standalone solvers (themselves pinned to the oracle
+    above) end."""
+    st = torch.cuda.Stream()
+    cases = [(90, 30, dict(rho=0.2, seed=1, tau_prec="bf16")),
+             (70, 25, dict(rho=0.3, seed=2)),
+             (110, 40, dict(rho=0.1, seed=3, tau_prec="bf16", roulette="adair", gamma_T=10))]
+    arena = sum(B.instance_bytes(n, m) for n, m, _ in cases) + (1 << 20)
+    bt = B.Batch(4, arena, stream=st)
+    slots = []
+    for q, (n, m, kw) in enumerate(cases):
+        xy = instances.uniform(n, 80 + q)
+        slots.append((bt.add(xy, m, iters=10, **kw), xy, m, kw))
+    bt.step(10)
+    for slot, xy, m, kw in slots:
+        s = B.Solver(xy, m=m, stream=st, **kw).iterate(10)
+        tau = bt.tau(slot)
+        assert np.array_equal(tau.view(np.uint32), s.tau().view(np.uint32))
+        if kw.get("tau_prec") == "bf16":
+            assert np.all((tau.view(np.uint32) & 0xFFFF) == 0)
+        tour, L = s.best()
+        bt_tour, bt_L = bt.best(slot)
+        assert bt_L == L and np.array_equal(bt_tour, tour)
+        s.close()
     bt.close()
