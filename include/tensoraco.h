@@ -231,10 +231,12 @@ int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int
 int aco_batch_destroy(aco_batch* b);
 
 /* Admit an instance: coords_host n x 2 fp32, p as for aco_create (p->prec
- * must equal the batch's).  It runs iters_budget iterations (0: until
- * removed), then stops advancing and keeps its results.  *slot receives its
- * slot id.  ACO_ERR_OOM (nothing changed) when no slot is free or its
- * workspace (aco_batch_instance_bytes) does not fit in the arena now. */
+ * must equal the batch's; p->tau_prec may differ between instances;
+ * p->roulette = ACO_RW is refused with ACO_ERR_UNSUPPORTED).  It runs
+ * iters_budget iterations (0: until removed), then stops advancing and
+ * keeps its results.  *slot receives its slot id.  ACO_ERR_OOM (nothing
+ * changed) when no slot is free or its workspace (aco_batch_instance_bytes)
+ * does not fit in the arena now. */
 int aco_batch_add(aco_batch* b, const float* coords_host, const aco_params* p, int iters_budget,
                   int* slot);
 /* Release a slot and its workspace. */
@@ -242,6 +244,7 @@ int aco_batch_remove(aco_batch* b, int slot);
 /* Run k iterations of every active (unfinished) instance. */
 int aco_batch_step(aco_batch* b, int k);
 int aco_batch_best(aco_batch* b, int slot, int32_t* tour_host, double* len_host);
+/* M_tau of a slot as n x n fp32 (bf16 storage widened exactly). */
 int aco_batch_get_tau(aco_batch* b, int slot, float* tau_host);
 int aco_batch_status(aco_batch* b, int slot, uint32_t* iterations_done, int* finished);
 /* Active instances, free arena bytes and largest free block. */
