@@ -274,7 +274,13 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
         const uint4 x = xc;
         const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
         const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
-        if (unvisited) better(sc, j, bs[q], bj[q]);
+        {
+          // better(sc, j) against the round's start (-1, none), written out:
+          // every unvisited finite score is taken, a NaN never
+          const bool take = unvisited && sc > -1.0f;
+          bs[q] = take ? sc : -1.0f;
+          bj[q] = take ? j : 0x7FFFFFFF;
+        }
         const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs[q]));
         const int win = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs[q]) == lk ? (uint32_t)bj[q] : 0x7FFFFFFFu);
         if (lk > rest) next[q] = win;
