@@ -228,6 +228,31 @@ def oracle_sample(w, coords, seed, budget_s=10.0, min_ants=None):
                       f"{secs:.3f} s", "_secs": secs}
 
 
+def oracle_batch_sample(sizes, budget_s=10.0, stride=32, ants=128):
+    """The CPU oracle on a sample of the batch workload: the first `ants` ants'
+    tours (bf16 M_p at iteration 0) of every `stride`-th instance, on all host
+    cores, until the budget is spent."""
+    import oracle
+    threads = oracle.default_threads()
+    ant_steps, secs, ids = 0, 0.0, []
+    for i in range(0, len(sizes), stride):
+        n = int(sizes[i])
+        xy = instances.uniform(n, 1000 + i)
+        H = oracle.heuristic(oracle.distances(xy), 2)
+        P, _, _ = oracle.build_P(oracle.init_tau(n), H, 1, 1.0, oracle.BF16)
+        k = min(n, ants)
+        t0 = time.perf_counter()
+        oracle.construct(P, i, 0, 0, k, threads)
+        secs += time.perf_counter() - t0
+        ant_steps += k * (n - 1)
+        ids.append(i)
+        if secs >= budget_s:
+            break
+    return {"value": round(ant_steps / secs, 1), "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": f"the first {ants} ants' tours of iteration 0 (bf16 M_p) of instances {ids} "
+                      f"(one in {stride}; n = {[int(sizes[i]) for i in ids]}), {secs:.3f} s"}
+
+
 # ---------------------------------------------------------------- native leg
 def run_native(args, w, dist):
     import torch
@@ -380,7 +405,8 @@ def run_native(args, w, dist):
     if dist.rank == 0 and not args.no_roulette:
         out["roulette"] = run_roulette(B, torch, w, coords, seed)
     if dist.rank == 0 and not args.no_batched:
-        out["batched"] = run_batched(B, torch, peak, value / dist.world if w["prec"] == "fp32" else None)
+        out["batched"] = run_batched(B, torch, peak, value / dist.world if w["prec"] == "fp32" else None,
+                                     cpu=not args.no_cpu_baseline and dist.world == 1)
     if dist.rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, w, coords, seed)
     if dist.rank == 0 and not args.no_cpu_baseline and dist.world == 1:
@@ -419,7 +445,7 @@ def run_roulette(B, torch, w, coords, seed, steps=10):
     return out
 
 
-def run_batched(B, torch, peak, single_value, steps=5, warmup=2):
+def run_batched(B, torch, peak, single_value, steps=5, warmup=2, cpu=False):
     """Many instances in one batch: 256 uniform instances, n ~ U{100..2000},
     m = n, alpha 1, beta 2, rho 0.1, bf16 M_p; every iteration is one graph
     replay whose construction is one persistent launch over all ants.  The
@@ -446,7 +472,8 @@ def run_batched(B, torch, peak, single_value, steps=5, warmup=2):
     ant_steps = float(sum(n * (n - 1) for n in sizes))
     alg = float(sum(n * n * (n - 1) / 2 for n in sizes)) * 2
     value = ant_steps / (ms / 1e3)
-    return {"workload": "256 uniform instances, n ~ U{100..2000} (seed 7), coords seeds 1000+i, m = n, "
+    extra = {"cpu_baseline": oracle_batch_sample(sizes)} if cpu else {}
+    return {**extra, "workload": "256 uniform instances, n ~ U{100..2000} (seed 7), coords seeds 1000+i, m = n, "
                         "alpha 1, beta 2, rho 0.1, bf16 M_p, candidate lists",
             "steps": steps, "warmup": warmup, "ms_per_iter": round(ms, 3),
             "value": round(value, 1), "unit": METRIC,
