@@ -166,20 +166,17 @@ __device__ __forceinline__ ListRow load_list_row(const uint2* __restrict__ lists
 // score key <= the row's bound, so the step is decided once the best score
 // key exceeds both.  Returns the chosen column, or -1 when the list cannot
 // decide; bs/bj then hold the best unvisited listed candidate (bs < 0: none),
-// a threshold for the full scan.  SPEC: in the first round, also start
-// loading the lists of the first two unvisited entries -- one of them is the
-// next city about 9 steps in 10 -- into spec[0], spec[1] (row = -1 when
-// there is none).
-template <bool SPEC>
-__device__ __forceinline__ int list_rounds(const uint2* __restrict__ lists, const uint32_t* __restrict__ lkey,
-                                           const ListRow& L, ListRow* spec, const uint32_t* __restrict__ svis,
-                                           const PhiloxKeys& key, uint32_t it, int k, int t, float& bs, int& bj) {
+// a threshold for the full scan.  (The full-scan kernel's list path; the lean
+// kernel has its own rounds.)
+__device__ __forceinline__ int list_rounds(const uint2* __restrict__ lists, const ListRow& L,
+                                           const uint32_t* __restrict__ svis, const PhiloxKeys& key, uint32_t it,
+                                           int k, int t, float& bs, int& bj) {
   const int lane = threadIdx.x & 31;
   const uint2* __restrict__ lrow = lists + (size_t)L.row * kListMax;
   uint2 e = L.e, e_next = L.e_next;
   // Rounds are written branch-free up to the decision so that the compiler
-  // can interleave the Philox chain with the visited test and the speculative
-  // loads; a padded slot scores column 0 and is then ignored.
+  // can interleave the Philox chain with the visited test; a padded slot
+  // scores column 0 and is then ignored.
 #pragma unroll 1
   for (int r = 0; r < kListMax / 32; ++r) {
     const bool valid = e.y != kListPad;
@@ -187,16 +184,6 @@ __device__ __forceinline__ int list_rounds(const uint2* __restrict__ lists, cons
     const bool unvisited = valid && !((svis[j >> 5] >> (j & 31)) & 1u);
     const uint4 x = philox(make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k, it), key);
     const unsigned vm = __ballot_sync(ACO_FULL_MASK, valid);
-    if (SPEC && r == 0) {
-      const unsigned un = __ballot_sync(ACO_FULL_MASK, unvisited);
-      const unsigned un2 = un & (un - 1u);
-      const int sj = __shfl_sync(ACO_FULL_MASK, j, un ? __ffs(un) - 1 : 0);
-      const int sj2 = __shfl_sync(ACO_FULL_MASK, j, un2 ? __ffs(un2) - 1 : 0);
-      spec[0] = load_list_row(lists, lkey, sj);  // harmless when there is no candidate
-      spec[1] = load_list_row(lists, lkey, sj2);
-      if (!un) spec[0].row = -1;
-      if (!un2) spec[1].row = -1;
-    }
     // every entry after this round has a value <= this round's last one
     const bool more = (vm >> 31) != 0u && r + 1 < kListMax / 32;
     uint32_t rest = L.lb;
@@ -328,7 +315,7 @@ __device__ __forceinline__ void construct_ant(const void* __restrict__ Pv, int n
     //    column not scored yet
     if (use_list) {
       const ListRow L = load_list_row(lists, lkey, cur);
-      next = list_rounds<false>(lists, lkey, L, nullptr, svis, ks, it, k, t, bs, bj);
+      next = list_rounds(lists, L, svis, ks, it, k, t, bs, bj);
     }
 
     if (next < 0) {  // full scan (seeded with the list's best candidate, if any)
