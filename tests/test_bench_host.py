@@ -1,0 +1,43 @@
+"""Host-side plumbing of bench.py: the committed ncu traffic is used only for
+the kernel source it was taken on, and the CPU baselines return well-formed
+records."""
+import importlib.util
+import json
+import os
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_traffic_only_for_the_profiled_source(bench):
+    entries = json.load(open(os.path.join(ROOT, "profiles", "construct_dram_traffic.json")))
+    key, e = next(iter(entries.items()))
+    kernel, workload, prec = key.split(":")
+    assert bench.traffic_from_profile(kernel, e["kernel_hash"], workload, prec) == e["dram_bytes_per_launch"]
+    assert e["dram_bytes_per_launch"] == e["dram_bytes_read"] + e["dram_bytes_write"]
+    assert bench.traffic_from_profile(kernel, "0" * 16, workload, prec) is None       # another source
+    assert bench.traffic_from_profile(kernel, e["kernel_hash"], workload, "bf16") is None
+
+
+def test_kernel_source_hash_follows_the_files(bench):
+    h = bench.kernel_source_hash("construct_lean_kernel")
+    assert len(h) == 16 and h == bench.kernel_source_hash("construct_lean_kernel")
+    assert all(os.path.exists(os.path.join(ROOT, "paper_2404_04895_gb300", "csrc", f))
+               for f in bench.KERNEL_SOURCES["construct_lean_kernel"])
+
+
+def test_batch_cpu_baseline_record(bench):
+    from paper_2404_04895_gb300 import instances
+    sizes = [int(x) for x in instances.batch_sizes(256, 100, 2000, seed=7)]
+    r = bench.oracle_batch_sample(sizes, budget_s=0.5, stride=128, ants=2)
+    assert r["kind"] == "oracle" and r["unit"] == bench.METRIC and r["cores"] >= 1
+    assert r["value"] > 0 and "instances [0" in r["sample"]
