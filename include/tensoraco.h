@@ -231,8 +231,9 @@ int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int
 int aco_batch_destroy(aco_batch* b);
 
 /* Admit an instance: coords_host n x 2 fp32, p as for aco_create (p->prec
- * must equal the batch's; p->tau_prec may differ between instances;
- * p->roulette = ACO_RW is refused with ACO_ERR_UNSUPPORTED).  It runs
+ * must equal the batch's; p->tau_prec and p->roulette may differ between
+ * instances: roulette-wheel instances (Sec. 2.4, n <= 16384) are built by
+ * their own multi-instance kernel, one CTA per ant).  It runs
  * iters_budget iterations (0: until removed), then stops advancing and
  * keeps its results.  *slot receives its slot id.  ACO_ERR_OOM (nothing
  * changed) when no slot is free or its workspace (aco_batch_instance_bytes)

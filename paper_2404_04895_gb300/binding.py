@@ -476,20 +476,6 @@ class Batch:
         call("aco_batch_info", self._h, C.byref(a), C.byref(f), C.byref(l))
         return dict(active=a.value, free_bytes=f.value, largest_block=l.value)
 
-    def state(self):
-        """The solver's checkpoint as bytes (tau, best tour/length, iteration, parameters)."""
-        nbytes = sz(0)
-        call("aco_solver_state_bytes", self._h, C.byref(nbytes))
-        buf = np.empty(nbytes.value, dtype=np.uint8)
-        call("aco_solver_save", self._h, buf.ctypes.data, nbytes.value)
-        return buf.tobytes()
-
-    def restore(self, blob):
-        """Restore a checkpoint taken from a solver with the same coordinates and parameters."""
-        buf = np.frombuffer(blob, dtype=np.uint8).copy()
-        call("aco_solver_load", self._h, buf.ctypes.data, buf.size)
-        return self
-
     def set_shape(self, warps=0, chunks=0, mode=0):
         call("aco_batch_set_shape", self._h, warps, chunks, mode)
 

@@ -205,7 +205,12 @@ struct aco_batch {
   int* d_counter = nullptr;
   int32_t* d_err = nullptr;
   std::vector<int> active;      // slot ids, n descending
-  int total_rows = 0, total_ants = 0, min_n = 0, max_n = 0;
+  int* d_rw_idx = nullptr;      // roulette-wheel instances: index into d_insts
+  int* d_rw_off = nullptr;      // their ants' exclusive prefix sums
+  int total_rows = 0, total_ants = 0;
+  int min_n = 0, max_n = 0;     // over the IR / AdaIR instances
+  int rw_count = 0, rw_ants = 0, rw_max_n = 0;
+  bool any_ir = false;          // some active instance constructs by IR / AdaIR
   size_t dep_smem = 0;          // deposit shared memory of the largest instance
   ConstructShape shape{0, 0, 0};  // forced shape for every class ({0,0,0}: per class)
   struct Class {
@@ -213,7 +218,7 @@ struct aco_batch {
     ConstructShape s;
   };
   std::vector<Class> classes;     // contiguous ranges of `active` sharing a shape
-  bool lean = false;              // all active instances use candidate lists: lean kernel
+  bool lean = false;              // all IR / AdaIR instances use candidate lists: lean kernel
   bool tables_ok = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -257,34 +262,75 @@ static int batch_refresh(aco_batch* b) {
   const int cnt = (int)b->active.size();
   std::vector<InstDev> insts(cnt);
   std::vector<int> row_off(cnt + 1, 0), ant_off(cnt + 1, 0);
+  std::vector<int> rw_idx, rw_off(1, 0);  // roulette-wheel instances: table index, ant prefix sums
   b->max_n = 0;
-  b->min_n = cnt > 0 ? b->slots[b->active[0]].p.n : 0;
+  b->min_n = 0;
+  b->rw_max_n = 0;
   b->dep_smem = 0;
   for (int q = 0; q < cnt; ++q) {
     const Slot& s = b->slots[b->active[q]];
     insts[q] = s.dev;
     row_off[q + 1] = row_off[q] + s.p.n;
     ant_off[q + 1] = ant_off[q] + s.p.m;
-    b->max_n = std::max(b->max_n, s.p.n);
-    b->min_n = std::min(b->min_n, s.p.n);
+    if (s.dev.rw) {
+      rw_idx.push_back(q);
+      rw_off.push_back(rw_off.back() + s.p.m);
+      b->rw_max_n = std::max(b->rw_max_n, s.p.n);
+    } else {
+      b->min_n = b->max_n == 0 ? s.p.n : std::min(b->min_n, s.p.n);
+      b->max_n = std::max(b->max_n, s.p.n);
+    }
     b->dep_smem = std::max(b->dep_smem, deposit_smem_bytes(s.p.n, deposit_cap(s.p.n, s.p.m)));
   }
   b->total_rows = row_off[cnt];
   b->total_ants = ant_off[cnt];
+  b->rw_count = (int)rw_idx.size();
+  b->rw_ants = rw_off.back();
   if (cnt) {
     ACO_CUDA_TRY(cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(InstDev) * cnt, cudaMemcpyHostToDevice, b->stream));
     ACO_CUDA_TRY(cudaMemcpyAsync(b->d_row_off, row_off.data(), sizeof(int) * (cnt + 1), cudaMemcpyHostToDevice, b->stream));
     ACO_CUDA_TRY(cudaMemcpyAsync(b->d_ant_off, ant_off.data(), sizeof(int) * (cnt + 1), cudaMemcpyHostToDevice, b->stream));
+    if (b->rw_count) {
+      ACO_CUDA_TRY(cudaMemcpyAsync(b->d_rw_idx, rw_idx.data(), sizeof(int) * b->rw_count, cudaMemcpyHostToDevice,
+                                   b->stream));
+      ACO_CUDA_TRY(cudaMemcpyAsync(b->d_rw_off, rw_off.data(), sizeof(int) * (b->rw_count + 1),
+                                   cudaMemcpyHostToDevice, b->stream));
+    }
     ACO_CUDA_TRY(cudaStreamSynchronize(b->stream));  // pageable sources
   }
-  // lean kernel when every active instance has candidate lists (and no shape is forced);
-  // else size classes: consecutive instances (n descending) sharing a shape
+  // IR / AdaIR instances: the lean kernel when all of them have candidate
+  // lists (and no shape is forced); else size classes: consecutive instances
+  // (n descending) sharing a shape.  Roulette-wheel instances have their own
+  // kernel; the IR kernels skip them, so they join whichever class is next to
+  // them (leading ones the first class).
   const int eb = b->prec == ACO_FP32 ? 4 : 2;
-  b->lean = cnt > 0 && b->shape.warps == 0 && b->max_n <= kLeanMaxN;
-  for (int q = 0; q < cnt; ++q) b->lean = b->lean && b->slots[b->active[q]].p.cand_lists;
-  b->classes.clear();
+  b->any_ir = b->rw_count < cnt;
+  b->lean = b->any_ir && b->shape.warps == 0 && b->max_n <= kLeanMaxN;
   for (int q = 0; q < cnt; ++q) {
     const Slot& sl = b->slots[b->active[q]];
+    b->lean = b->lean && (sl.dev.rw || sl.p.cand_lists);
+  }
+  b->classes.clear();
+  int lead = 0, lead_total = 0;  // roulette-wheel instances before the first class
+  for (int q = 0; q < cnt; ++q) {
+    const Slot& sl = b->slots[b->active[q]];
+    if (sl.dev.rw) {
+      if (b->classes.empty()) {
+        lead += 1;
+        lead_total += sl.p.m;
+      } else {
+        b->classes.back().count += 1;
+        b->classes.back().total += sl.p.m;
+      }
+      continue;
+    }
+    if (b->classes.empty() && lead) {  // the first IR / AdaIR instance opens a class holding the leading ones
+      ConstructShape s = b->shape;
+      if (s.warps == 0 || batch_shape_columns(s, eb) < sl.p.n) s = batch_default_shape(sl.p.n, eb);
+      if (s.warps == 0) return set_error(ACO_ERR_UNSUPPORTED, "no batch construct shape covers n=%d", sl.p.n);
+      b->classes.push_back({0, lead + 1, lead_total + sl.p.m, s});
+      continue;
+    }
     ConstructShape s = b->shape;
     if (s.warps == 0 || batch_shape_columns(s, eb) < sl.p.n) s = batch_default_shape(sl.p.n, eb);
     if (s.warps == 0) return set_error(ACO_ERR_UNSUPPORTED, "no batch construct shape covers n=%d", sl.p.n);
@@ -335,12 +381,17 @@ static int batch_enqueue(aco_batch* b) {
   }
   ACO_CHECK_LAUNCH("batch_build_lists_kernel");
   ACO_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int) * std::max<size_t>(1, b->classes.size()), st));
-  if (b->lean) {  // one persistent lean launch over every ant of every instance
+  if (b->rw_count) {  // one CTA per roulette-wheel ant
+    const int rc = launch_batch_construct_rw(b->d_insts, b->d_rw_idx, b->d_rw_off, b->rw_count, b->rw_ants,
+                                             b->d_err, b->prec, b->rw_max_n, st);
+    if (rc) return rc;
+  }
+  if (b->lean) {  // one persistent lean launch over every ant of every IR / AdaIR instance
     const int rc = launch_batch_construct_lean(b->d_insts, b->d_ant_off, cnt, b->total_ants, b->d_counter,
                                                b->d_err, b->prec, b->min_n, b->max_n, b->num_sms, st);
     if (rc) return rc;
   }
-  for (size_t ci = 0; ci < (b->lean ? 0 : b->classes.size()); ++ci) {
+  for (size_t ci = 0; ci < (b->lean || !b->any_ir ? 0 : b->classes.size()); ++ci) {
     const auto& c = b->classes[ci];
     const ConstructShape s = c.s;
     const InstDev* ins = b->d_insts + c.first;
@@ -418,6 +469,8 @@ int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int
     cudaFree(b->d_insts);
     cudaFree(b->d_row_off);
     cudaFree(b->d_ant_off);
+    cudaFree(b->d_rw_idx);
+    cudaFree(b->d_rw_off);
     cudaFree(b->d_counter);
     cudaFree(b->d_err);
     delete b;
@@ -435,6 +488,8 @@ int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int
   if (cudaMalloc(&b->d_insts, sizeof(InstDev) * max_instances) != cudaSuccess ||
       cudaMalloc(&b->d_row_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
       cudaMalloc(&b->d_ant_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
+      cudaMalloc(&b->d_rw_idx, sizeof(int) * max_instances) != cudaSuccess ||
+      cudaMalloc(&b->d_rw_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
       cudaMalloc(&b->d_counter, sizeof(int) * kMaxClasses) != cudaSuccess ||
       cudaMalloc(&b->d_err, sizeof(int32_t)) != cudaSuccess)
     return fail(cuda_error(cudaGetLastError(), "cudaMalloc(batch tables)"));
@@ -451,6 +506,8 @@ int aco_batch_destroy(aco_batch* b) {
   cudaFree(b->d_insts);
   cudaFree(b->d_row_off);
   cudaFree(b->d_ant_off);
+  cudaFree(b->d_rw_idx);
+  cudaFree(b->d_rw_off);
   cudaFree(b->d_counter);
   cudaFree(b->d_err);
   delete b;
@@ -462,7 +519,8 @@ int aco_batch_add(aco_batch* b, const float* coords_host, const aco_params* p, i
   if (!b || !coords_host || !p || !slot) return set_error(ACO_ERR_ARG, "NULL argument");
   if (p->prec != b->prec) return set_error(ACO_ERR_ARG, "instance precision %d differs from the batch's %d", p->prec, b->prec);
   if (iters_budget < 0) return set_error(ACO_ERR_ARG, "iters_budget must be >= 0");
-  if (p->roulette == ACO_RW) return set_error(ACO_ERR_UNSUPPORTED, "batches run IR / AdaIR instances only");
+  if (p->roulette == ACO_RW && p->n > kRwMaxN)  // before the arena: a size error, not a full arena
+    return set_error(ACO_ERR_UNSUPPORTED, "roulette-wheel construction serves n <= %d", kRwMaxN);
   int q = 0;
   while (q < (int)b->slots.size() && b->slots[q].used) ++q;
   if (q == (int)b->slots.size()) return set_error(ACO_ERR_OOM, "all %d batch slots are in use", q);

@@ -9,6 +9,7 @@ namespace aco {
 struct InstDev {
   int n, m, ld, alpha;
   int adair, n_sched;
+  int rw;                         // roulette-wheel construction (Sec. 2.4) instead of IR / AdaIR
   int topk;                       // paths that deposit (0: all)
   float rho, Q;
   uint2 key;                      // Philox key (seed low, high)
@@ -26,7 +27,7 @@ struct InstDev {
   double* best_len;               // 1
   uint32_t* it;                   // iterations completed (device counter)
   const float* sched;             // AdaIR 1/gamma per iteration (n_sched entries)
-  uint2* lists;                   // candidate lists, n x kListMax (nullptr: full scan only)
+  uint2* lists;                   // candidate lists, n x kListMax (nullptr: full scan only, or rw)
   int* lcnt;                      // n
   uint32_t* lkey;                 // n
 };

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "construct.cuh"
 #include "internal.h"
@@ -30,7 +31,6 @@ namespace aco {
 
 namespace {
 
-constexpr int kRwMaxN = 16384;
 constexpr int kRwThreads = 256;
 constexpr uint32_t kRwSpin = 1u << 20;  // bound on one mbarrier wait (polls)
 
@@ -124,19 +124,14 @@ __device__ __forceinline__ uint64_t shfl_up_u64(uint64_t x, int off) {
   return ((uint64_t)hi << 32) | lo;
 }
 
+// The tour of ant k (one CTA of kRwThreads threads; `rsm` holds
+// rw_smem_bytes(n) bytes of dynamic shared memory).
 template <int PREC>
-__global__ void __launch_bounds__(kRwThreads) construct_rw_kernel(const void* __restrict__ Pv, int n, int ld, int m,
-                                                                  uint2 key, uint32_t it_arg,
-                                                                  const uint32_t* __restrict__ it_dev,
-                                                                  int32_t* __restrict__ tours,
-                                                                  int32_t* __restrict__ err) {
-  extern __shared__ __align__(16) uint4 rsm[];
-  const int k = blockIdx.x;
-  if (k >= m) return;
+__device__ __forceinline__ void rw_ant(const void* __restrict__ Pv, int n, int ld, uint2 key, uint32_t it, int k,
+                                       int32_t* __restrict__ tour, int32_t* __restrict__ err, uint4* rsm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kRwThreads / 32;
   constexpr int EB = PREC == ACO_FP32 ? 4 : 2;
-  const uint32_t it = it_dev ? *it_dev : it_arg;
   char* sbase = reinterpret_cast<char*>(rsm);
   const uint32_t row_bytes = (uint32_t)rw_row_bytes(n, EB);  // <= ld * EB: a row's padded span
   volatile uint8_t* flags = reinterpret_cast<uint8_t*>(sbase + row_bytes);
@@ -149,7 +144,6 @@ __global__ void __launch_bounds__(kRwThreads) construct_rw_kernel(const void* __
   const uint32_t sbar = smem_addr(bar), srow = smem_addr(sbase);
   const int B = rw_block(n);
   const int j0 = min(n, tid * B), j1 = min(n, j0 + B);
-  int32_t* tour = tours + (size_t)k * n;
   const char* __restrict__ P = static_cast<const char*>(Pv);
   const size_t row_stride = (size_t)ld * EB;
 
@@ -263,6 +257,36 @@ __global__ void __launch_bounds__(kRwThreads) construct_rw_kernel(const void* __
   }
 }
 
+template <int PREC>
+__global__ void __launch_bounds__(kRwThreads) construct_rw_kernel(const void* __restrict__ Pv, int n, int ld, int m,
+                                                                  uint2 key, uint32_t it_arg,
+                                                                  const uint32_t* __restrict__ it_dev,
+                                                                  int32_t* __restrict__ tours,
+                                                                  int32_t* __restrict__ err) {
+  extern __shared__ __align__(16) uint4 rsm[];
+  const int k = blockIdx.x;
+  if (k >= m) return;
+  const uint32_t it = it_dev ? *it_dev : it_arg;
+  rw_ant<PREC>(Pv, n, ld, key, it, k, tours + (size_t)k * n, err, rsm);
+}
+
+// Multi-instance form: one CTA per ant of the batch's roulette-wheel
+// instances.  rw_idx[j] is the table index of the j-th such instance and
+// rw_off the exclusive prefix sums of their ant counts (rw_off[count] =
+// the grid size).
+template <int PREC>
+__global__ void __launch_bounds__(kRwThreads) batch_construct_rw_kernel(const InstDev* __restrict__ insts,
+                                                                        const int* __restrict__ rw_idx,
+                                                                        const int* __restrict__ rw_off, int count,
+                                                                        int32_t* __restrict__ err) {
+  extern __shared__ __align__(16) uint4 rsm[];
+  const int j = find_instance(rw_off, count, (int)blockIdx.x);
+  const InstDev& I = insts[__ldg(rw_idx + j)];
+  const int k = (int)blockIdx.x - __ldg(rw_off + j);
+  if (!I.rw || k >= I.m) return;  // cannot happen for consistent tables
+  rw_ant<PREC>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err, rsm);
+}
+
 }  // namespace
 
 int launch_construct_rw(const void* P, int prec, int n, int ld, int m, uint2 key, uint32_t it,
@@ -287,14 +311,38 @@ int launch_construct_rw(const void* P, int prec, int n, int ld, int m, uint2 key
   return e == cudaSuccess ? ACO_OK : cuda_error(e, "construct_rw_kernel launch");
 }
 
+int launch_batch_construct_rw(const InstDev* insts, const int* rw_idx, const int* rw_off, int count, int total,
+                              int32_t* err, int prec, int max_n, cudaStream_t st) {
+  if (count <= 0 || total <= 0) return ACO_OK;
+  if (max_n > kRwMaxN) return set_error(ACO_ERR_UNSUPPORTED, "roulette-wheel construction serves n <= %d", kRwMaxN);
+  const size_t smem = rw_smem_bytes(max_n, prec == ACO_FP32 ? 4 : 2);
+  switch (prec) {
+    case ACO_FP32:
+      batch_construct_rw_kernel<ACO_FP32><<<total, kRwThreads, smem, st>>>(insts, rw_idx, rw_off, count, err);
+      break;
+    case ACO_BF16:
+      batch_construct_rw_kernel<ACO_BF16><<<total, kRwThreads, smem, st>>>(insts, rw_idx, rw_off, count, err);
+      break;
+    case ACO_FP16:
+      batch_construct_rw_kernel<ACO_FP16><<<total, kRwThreads, smem, st>>>(insts, rw_idx, rw_off, count, err);
+      break;
+    default:
+      return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ACO_OK : cuda_error(e, "batch_construct_rw_kernel launch");
+}
+
 int prepare_construct_rw() {
   const int most = (int)rw_smem_bytes(kRwMaxN, 4);
-  cudaError_t e = cudaFuncSetAttribute(construct_rw_kernel<ACO_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(construct_rw_kernel<ACO_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(construct_rw_kernel<ACO_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-  return e == cudaSuccess ? ACO_OK : cuda_error(e, "cudaFuncSetAttribute(rw)");
+  const void* fns[] = {(const void*)construct_rw_kernel<ACO_FP32>,       (const void*)construct_rw_kernel<ACO_BF16>,
+                       (const void*)construct_rw_kernel<ACO_FP16>,       (const void*)batch_construct_rw_kernel<ACO_FP32>,
+                       (const void*)batch_construct_rw_kernel<ACO_BF16>, (const void*)batch_construct_rw_kernel<ACO_FP16>};
+  for (const void* f : fns) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(rw)");
+  }
+  return ACO_OK;
 }
 
 }  // namespace aco

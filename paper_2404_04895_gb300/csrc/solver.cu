@@ -178,8 +178,8 @@ static int validate(const aco_params* p) {
   if (p->prec < ACO_FP32 || p->prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", p->prec);
   if (p->roulette != ACO_IR && p->roulette != ACO_ADAIR && p->roulette != ACO_RW)
     return set_error(ACO_ERR_ARG, "unknown roulette %d", p->roulette);
-  if (p->roulette == ACO_RW && p->n > 16384)
-    return set_error(ACO_ERR_UNSUPPORTED, "roulette-wheel construction serves n <= 16384");
+  if (p->roulette == ACO_RW && p->n > kRwMaxN)
+    return set_error(ACO_ERR_UNSUPPORTED, "roulette-wheel construction serves n <= %d", kRwMaxN);
   if (p->deposit != ACO_DEPOSIT_DET && p->deposit != ACO_DEPOSIT_ATOMIC)
     return set_error(ACO_ERR_ARG, "unknown deposit mode %d", p->deposit);
   if (p->roulette == ACO_ADAIR) {
@@ -251,6 +251,7 @@ int instance_bind(const aco_params& p, unsigned char* ws, InstDev* d, cudaStream
   x.ld = ld;
   x.alpha = p.alpha;
   x.adair = p.roulette == ACO_ADAIR;
+  x.rw = p.roulette == ACO_RW;
   x.n_sched = x.adair ? std::min(p.gamma_T + 1, kSchedCap) : 1;
   x.rho = p.rho;
   x.Q = p.Q;
@@ -271,7 +272,7 @@ int instance_bind(const aco_params& p, unsigned char* ws, InstDev* d, cudaStream
   x.best_len = reinterpret_cast<double*>(ws + L.best_len);
   x.it = reinterpret_cast<uint32_t*>(ws + L.it);
   x.sched = reinterpret_cast<float*>(ws + L.sched);
-  x.lists = p.cand_lists ? reinterpret_cast<uint2*>(ws + L.lists) : nullptr;
+  x.lists = p.cand_lists && !x.rw ? reinterpret_cast<uint2*>(ws + L.lists) : nullptr;
   x.lcnt = reinterpret_cast<int*>(ws + L.lcnt);
   x.lkey = reinterpret_cast<uint32_t*>(ws + L.lkey);
   ACO_CUDA_TRY(cudaMemcpyAsync(coords, coords_host, sizeof(float) * 2 * p.n, cudaMemcpyHostToDevice, st));

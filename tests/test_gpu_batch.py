@@ -85,3 +85,38 @@ def test_batch_memory_gated_admission():
     bt.step(2)
     assert bt.status(s2) == (2, True) and bt.status(s3) == (2, True)
     bt.close()
+
+
+# (n, m, roulette): roulette-wheel instances lead, sit inside and trail the
+# batch's n-descending order
+MIXED = [(300, 20, "rw"), (257, 30, "ir"), (130, 40, "rw"), (100, 25, "adair"), (64, 33, "ir"), (40, 16, "rw")]
+
+
+@pytest.mark.parametrize("case", ["lists", "classes", "rw_only"])
+def test_batch_mixes_roulette_wheel_instances(orc, case):
+    """Roulette-wheel instances (Sec. 2.4; their own multi-instance kernel,
+    one CTA per ant) beside IR and AdaIR ones: on the candidate-list path, on
+    size classes (IR instances without lists) and alone, every instance ends
+    with a standalone solver's results, and a roulette-wheel instance with the
+    oracle's."""
+    sizes = [x for x in MIXED if case != "rw_only" or x[2] == "rw"]
+    arena = sum(B.instance_bytes(n, m) for n, m, _ in sizes) + (1 << 20)
+    bt = B.Batch(8, arena, stream=torch.cuda.Stream())
+    slots = []
+    for q, (n, m, rou) in enumerate(sizes):
+        xy = instances.uniform(n, 900 + q)
+        kw = dict(rho=0.25, seed=20 + q, roulette=rou, gamma_T=9, cand_lists=case != "classes")
+        slots.append((bt.add(xy, m, iters=9, **kw), xy, m, kw))
+    bt.step(11)
+    for slot, xy, m, kw in slots:
+        assert bt.status(slot) == (9, True)
+        (tour, L), tau = _alone(xy, m, 9, "fp32", **kw)
+        bt_tour, bt_L = bt.best(slot)
+        assert bt_L == L and np.array_equal(bt_tour, tour), kw
+        assert np.array_equal(bt.tau(slot).view(np.uint32), tau.view(np.uint32)), kw
+    slot, xy, m, kw = next(s for s in slots if s[3]["roulette"] == "rw" and s[2] == 40)
+    ref = orc.State(xy, m=m, rho=kw["rho"], seed=kw["seed"], rw=True).run(9)
+    tour, L = bt.best(slot)
+    assert L == ref.best_len[0] and np.array_equal(tour, ref.best_tour)
+    assert np.array_equal(bt.tau(slot), ref.tau)
+    bt.close()

@@ -57,6 +57,7 @@ def test_rw_limits():
     with pytest.raises(RuntimeError):
         B.Solver(xy, m=4, roulette="rw", workspace="library")
     bt = B.Batch(2, B.instance_bytes(60, 10) + (1 << 20))
-    with pytest.raises(RuntimeError):
-        bt.add(instances.uniform(60, 4), 10, roulette="rw")
+    with pytest.raises(RuntimeError):                      # a size error, before the arena
+        bt.add(xy, 4, roulette="rw")
+    assert bt.add(instances.uniform(60, 4), 10, roulette="rw") is not None
     bt.close()
