@@ -205,15 +205,17 @@ struct aco_batch {
   int* d_counter = nullptr;
   int32_t* d_err = nullptr;
   std::vector<int> active;      // slot ids, n descending
-  int* d_rw_idx = nullptr;      // roulette-wheel instances: index into d_insts
-  int* d_rw_off = nullptr;      // their ants' exclusive prefix sums
+  InstDev* d_ir_insts = nullptr;  // the IR / AdaIR instances of the active set
+  int* d_ir_off = nullptr;        // their ants' exclusive prefix sums
+  InstDev* d_rw_insts = nullptr;  // the roulette-wheel instances
+  int* d_rw_off = nullptr;
+  std::vector<int> ir;            // positions in `active` of the IR / AdaIR instances
   int total_rows = 0, total_ants = 0;
-  int min_n = 0, max_n = 0;     // over the IR / AdaIR instances
+  int min_n = 0, max_n = 0, ir_ants = 0;  // over the IR / AdaIR instances
   int rw_count = 0, rw_ants = 0, rw_max_n = 0;
-  bool any_ir = false;          // some active instance constructs by IR / AdaIR
   size_t dep_smem = 0;          // deposit shared memory of the largest instance
   ConstructShape shape{0, 0, 0};  // forced shape for every class ({0,0,0}: per class)
-  struct Class {
+  struct Class {  // first, count: a range of the IR / AdaIR table
     int first, count, total;
     ConstructShape s;
   };
@@ -260,9 +262,11 @@ static int batch_refresh(aco_batch* b) {
   std::stable_sort(b->active.begin(), b->active.end(),
                    [&](int x, int y) { return b->slots[x].p.n > b->slots[y].p.n; });
   const int cnt = (int)b->active.size();
-  std::vector<InstDev> insts(cnt);
-  std::vector<int> row_off(cnt + 1, 0), ant_off(cnt + 1, 0);
-  std::vector<int> rw_idx, rw_off(1, 0);  // roulette-wheel instances: table index, ant prefix sums
+  // every instance (build_P, lists, lengths, best, deposit); the IR / AdaIR
+  // ones (their construction kernels); the roulette-wheel ones (theirs)
+  std::vector<InstDev> insts(cnt), ir_insts, rw_insts;
+  std::vector<int> row_off(cnt + 1, 0), ant_off(cnt + 1, 0), ir_off(1, 0), rw_off(1, 0);
+  b->ir.clear();
   b->max_n = 0;
   b->min_n = 0;
   b->rw_max_n = 0;
@@ -273,10 +277,13 @@ static int batch_refresh(aco_batch* b) {
     row_off[q + 1] = row_off[q] + s.p.n;
     ant_off[q + 1] = ant_off[q] + s.p.m;
     if (s.dev.rw) {
-      rw_idx.push_back(q);
+      rw_insts.push_back(s.dev);
       rw_off.push_back(rw_off.back() + s.p.m);
       b->rw_max_n = std::max(b->rw_max_n, s.p.n);
     } else {
+      b->ir.push_back(q);
+      ir_insts.push_back(s.dev);
+      ir_off.push_back(ir_off.back() + s.p.m);
       b->min_n = b->max_n == 0 ? s.p.n : std::min(b->min_n, s.p.n);
       b->max_n = std::max(b->max_n, s.p.n);
     }
@@ -284,53 +291,32 @@ static int batch_refresh(aco_batch* b) {
   }
   b->total_rows = row_off[cnt];
   b->total_ants = ant_off[cnt];
-  b->rw_count = (int)rw_idx.size();
+  b->ir_ants = ir_off.back();
+  b->rw_count = (int)rw_insts.size();
   b->rw_ants = rw_off.back();
+  const int ir_cnt = (int)b->ir.size();
+  auto put = [&](void* dst, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, b->stream) : cudaSuccess;
+  };
   if (cnt) {
-    ACO_CUDA_TRY(cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(InstDev) * cnt, cudaMemcpyHostToDevice, b->stream));
-    ACO_CUDA_TRY(cudaMemcpyAsync(b->d_row_off, row_off.data(), sizeof(int) * (cnt + 1), cudaMemcpyHostToDevice, b->stream));
-    ACO_CUDA_TRY(cudaMemcpyAsync(b->d_ant_off, ant_off.data(), sizeof(int) * (cnt + 1), cudaMemcpyHostToDevice, b->stream));
-    if (b->rw_count) {
-      ACO_CUDA_TRY(cudaMemcpyAsync(b->d_rw_idx, rw_idx.data(), sizeof(int) * b->rw_count, cudaMemcpyHostToDevice,
-                                   b->stream));
-      ACO_CUDA_TRY(cudaMemcpyAsync(b->d_rw_off, rw_off.data(), sizeof(int) * (b->rw_count + 1),
-                                   cudaMemcpyHostToDevice, b->stream));
-    }
+    ACO_CUDA_TRY(put(b->d_insts, insts.data(), sizeof(InstDev) * cnt));
+    ACO_CUDA_TRY(put(b->d_row_off, row_off.data(), sizeof(int) * (cnt + 1)));
+    ACO_CUDA_TRY(put(b->d_ant_off, ant_off.data(), sizeof(int) * (cnt + 1)));
+    ACO_CUDA_TRY(put(b->d_ir_insts, ir_insts.data(), sizeof(InstDev) * ir_cnt));
+    ACO_CUDA_TRY(put(b->d_ir_off, ir_off.data(), sizeof(int) * (ir_cnt + 1)));
+    ACO_CUDA_TRY(put(b->d_rw_insts, rw_insts.data(), sizeof(InstDev) * b->rw_count));
+    ACO_CUDA_TRY(put(b->d_rw_off, rw_off.data(), sizeof(int) * (b->rw_count + 1)));
     ACO_CUDA_TRY(cudaStreamSynchronize(b->stream));  // pageable sources
   }
   // IR / AdaIR instances: the lean kernel when all of them have candidate
   // lists (and no shape is forced); else size classes: consecutive instances
-  // (n descending) sharing a shape.  Roulette-wheel instances have their own
-  // kernel; the IR kernels skip them, so they join whichever class is next to
-  // them (leading ones the first class).
+  // (n descending) sharing a shape.  Indices below are into their table.
   const int eb = b->prec == ACO_FP32 ? 4 : 2;
-  b->any_ir = b->rw_count < cnt;
-  b->lean = b->any_ir && b->shape.warps == 0 && b->max_n <= kLeanMaxN;
-  for (int q = 0; q < cnt; ++q) {
-    const Slot& sl = b->slots[b->active[q]];
-    b->lean = b->lean && (sl.dev.rw || sl.p.cand_lists);
-  }
+  b->lean = ir_cnt > 0 && b->shape.warps == 0 && b->max_n <= kLeanMaxN;
+  for (int q = 0; q < ir_cnt; ++q) b->lean = b->lean && b->slots[b->active[b->ir[q]]].p.cand_lists;
   b->classes.clear();
-  int lead = 0, lead_total = 0;  // roulette-wheel instances before the first class
-  for (int q = 0; q < cnt; ++q) {
-    const Slot& sl = b->slots[b->active[q]];
-    if (sl.dev.rw) {
-      if (b->classes.empty()) {
-        lead += 1;
-        lead_total += sl.p.m;
-      } else {
-        b->classes.back().count += 1;
-        b->classes.back().total += sl.p.m;
-      }
-      continue;
-    }
-    if (b->classes.empty() && lead) {  // the first IR / AdaIR instance opens a class holding the leading ones
-      ConstructShape s = b->shape;
-      if (s.warps == 0 || batch_shape_columns(s, eb) < sl.p.n) s = batch_default_shape(sl.p.n, eb);
-      if (s.warps == 0) return set_error(ACO_ERR_UNSUPPORTED, "no batch construct shape covers n=%d", sl.p.n);
-      b->classes.push_back({0, lead + 1, lead_total + sl.p.m, s});
-      continue;
-    }
+  for (int q = 0; q < ir_cnt; ++q) {
+    const Slot& sl = b->slots[b->active[b->ir[q]]];
     ConstructShape s = b->shape;
     if (s.warps == 0 || batch_shape_columns(s, eb) < sl.p.n) s = batch_default_shape(sl.p.n, eb);
     if (s.warps == 0) return set_error(ACO_ERR_UNSUPPORTED, "no batch construct shape covers n=%d", sl.p.n);
@@ -382,22 +368,23 @@ static int batch_enqueue(aco_batch* b) {
   ACO_CHECK_LAUNCH("batch_build_lists_kernel");
   ACO_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int) * std::max<size_t>(1, b->classes.size()), st));
   if (b->rw_count) {  // one CTA per roulette-wheel ant
-    const int rc = launch_batch_construct_rw(b->d_insts, b->d_rw_idx, b->d_rw_off, b->rw_count, b->rw_ants,
-                                             b->d_err, b->prec, b->rw_max_n, st);
+    const int rc = launch_batch_construct_rw(b->d_rw_insts, b->d_rw_off, b->rw_count, b->rw_ants, b->d_err,
+                                             b->prec, b->rw_max_n, st);
     if (rc) return rc;
   }
+  const int ir_cnt = (int)b->ir.size();
   if (b->lean) {  // one persistent lean launch over every ant of every IR / AdaIR instance
-    const int rc = launch_batch_construct_lean(b->d_insts, b->d_ant_off, cnt, b->total_ants, b->d_counter,
+    const int rc = launch_batch_construct_lean(b->d_ir_insts, b->d_ir_off, ir_cnt, b->ir_ants, b->d_counter,
                                                b->d_err, b->prec, b->min_n, b->max_n, b->num_sms, st);
     if (rc) return rc;
   }
-  for (size_t ci = 0; ci < (b->lean || !b->any_ir ? 0 : b->classes.size()); ++ci) {
+  for (size_t ci = 0; ci < (b->lean ? 0 : b->classes.size()); ++ci) {
     const auto& c = b->classes[ci];
     const ConstructShape s = c.s;
-    const InstDev* ins = b->d_insts + c.first;
-    const int* off = b->d_ant_off + c.first;
+    const InstDev* ins = b->d_ir_insts + c.first;
+    const int* off = b->d_ir_off + c.first;
     int* ctr = b->d_counter + ci;
-    const int bitmap = ((b->slots[b->active[c.first]].p.n + 127) / 128) * 16;  // largest n of the class
+    const int bitmap = ((b->slots[b->active[b->ir[c.first]]].p.n + 127) / 128) * 16;  // largest n of the class
     int rc;
     if (b->prec == ACO_FP32)
       rc = launch_batch_construct_f32(ins, off, c.count, c.total, ctr, b->d_err, s.warps, s.chunks, s.mode,
@@ -469,7 +456,9 @@ int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int
     cudaFree(b->d_insts);
     cudaFree(b->d_row_off);
     cudaFree(b->d_ant_off);
-    cudaFree(b->d_rw_idx);
+    cudaFree(b->d_ir_insts);
+    cudaFree(b->d_ir_off);
+    cudaFree(b->d_rw_insts);
     cudaFree(b->d_rw_off);
     cudaFree(b->d_counter);
     cudaFree(b->d_err);
@@ -488,7 +477,9 @@ int aco_batch_create(aco_batch** out, int max_instances, size_t arena_bytes, int
   if (cudaMalloc(&b->d_insts, sizeof(InstDev) * max_instances) != cudaSuccess ||
       cudaMalloc(&b->d_row_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
       cudaMalloc(&b->d_ant_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
-      cudaMalloc(&b->d_rw_idx, sizeof(int) * max_instances) != cudaSuccess ||
+      cudaMalloc(&b->d_ir_insts, sizeof(InstDev) * max_instances) != cudaSuccess ||
+      cudaMalloc(&b->d_ir_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
+      cudaMalloc(&b->d_rw_insts, sizeof(InstDev) * max_instances) != cudaSuccess ||
       cudaMalloc(&b->d_rw_off, sizeof(int) * (max_instances + 1)) != cudaSuccess ||
       cudaMalloc(&b->d_counter, sizeof(int) * kMaxClasses) != cudaSuccess ||
       cudaMalloc(&b->d_err, sizeof(int32_t)) != cudaSuccess)
@@ -506,7 +497,9 @@ int aco_batch_destroy(aco_batch* b) {
   cudaFree(b->d_insts);
   cudaFree(b->d_row_off);
   cudaFree(b->d_ant_off);
-  cudaFree(b->d_rw_idx);
+  cudaFree(b->d_ir_insts);
+  cudaFree(b->d_ir_off);
+  cudaFree(b->d_rw_insts);
   cudaFree(b->d_rw_off);
   cudaFree(b->d_counter);
   cudaFree(b->d_err);

@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(32 * W) construct_kernel(
 // Multi-instance construction: a persistent grid pulls work items (instance,
 // ant) from a global counter; items are ordered by instance, instances by
 // decreasing n, so the longest walks start first.  One launch covers every
-// IR / AdaIR ant of a batch (roulette-wheel instances are skipped).
+// ant of every active instance of a batch.
 // insts/ant_off point at the first instance of a size class of `count`
 // instances; its items are ant_off[0] .. ant_off[0] + total - 1.
 template <int PREC, int W, int KC, int MODE>
@@ -484,7 +484,6 @@ __global__ void __launch_bounds__(32 * W) batch_construct_kernel(
     if (item >= total) break;
     const int i = find_instance(ant_off, count, base + item);
     const InstDev& I = insts[i];
-    if (I.rw) continue;  // built by the roulette-wheel kernel
     const int k = base + item - __ldg(ant_off + i);
     construct_ant<PREC, W, KC, MODE>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err,
                                      red_s, red_j, srow, I.lists, I.lcnt, I.lkey, svis);

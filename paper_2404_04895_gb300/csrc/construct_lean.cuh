@@ -357,8 +357,7 @@ __global__ void __launch_bounds__(32) construct_lean_kernel(
 }
 
 // Multi-instance form: persistent warps pull (instance, ant) items; every
-// IR / AdaIR instance has candidate lists (roulette-wheel instances are
-// skipped).  FULL0: every IR / AdaIR instance has n >= 32.
+// instance has candidate lists.  FULL0: every instance has n >= 32.
 template <int PREC, bool FULL0>
 __global__ void __launch_bounds__(32) batch_construct_lean_kernel(
     const InstDev* __restrict__ insts, const int* __restrict__ ant_off, int count, int total,
@@ -375,7 +374,6 @@ __global__ void __launch_bounds__(32) batch_construct_lean_kernel(
     if (item >= total) break;
     const int i = find_instance(ant_off, count, base + item);
     const InstDev& I = insts[i];
-    if (I.rw) continue;  // built by the roulette-wheel kernel
     int k[1] = {base + item - __ldg(ant_off + i)};
     int32_t* tour[1] = {I.tours + (size_t)k[0] * I.n};
     uint32_t* sv[1] = {svis};

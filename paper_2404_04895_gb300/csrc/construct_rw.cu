@@ -270,19 +270,17 @@ __global__ void __launch_bounds__(kRwThreads) construct_rw_kernel(const void* __
   rw_ant<PREC>(Pv, n, ld, key, it, k, tours + (size_t)k * n, err, rsm);
 }
 
-// Multi-instance form: one CTA per ant of the batch's roulette-wheel
-// instances.  rw_idx[j] is the table index of the j-th such instance and
-// rw_off the exclusive prefix sums of their ant counts (rw_off[count] =
-// the grid size).
+// Multi-instance form: one CTA per ant of the `count` roulette-wheel
+// instances in `insts`; ant_off holds the exclusive prefix sums of their ant
+// counts (ant_off[count] = the grid size).
 template <int PREC>
 __global__ void __launch_bounds__(kRwThreads) batch_construct_rw_kernel(const InstDev* __restrict__ insts,
-                                                                        const int* __restrict__ rw_idx,
-                                                                        const int* __restrict__ rw_off, int count,
+                                                                        const int* __restrict__ ant_off, int count,
                                                                         int32_t* __restrict__ err) {
   extern __shared__ __align__(16) uint4 rsm[];
-  const int j = find_instance(rw_off, count, (int)blockIdx.x);
-  const InstDev& I = insts[__ldg(rw_idx + j)];
-  const int k = (int)blockIdx.x - __ldg(rw_off + j);
+  const int i = find_instance(ant_off, count, (int)blockIdx.x);
+  const InstDev& I = insts[i];
+  const int k = (int)blockIdx.x - __ldg(ant_off + i);
   if (!I.rw || k >= I.m) return;  // cannot happen for consistent tables
   rw_ant<PREC>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err, rsm);
 }
@@ -311,20 +309,20 @@ int launch_construct_rw(const void* P, int prec, int n, int ld, int m, uint2 key
   return e == cudaSuccess ? ACO_OK : cuda_error(e, "construct_rw_kernel launch");
 }
 
-int launch_batch_construct_rw(const InstDev* insts, const int* rw_idx, const int* rw_off, int count, int total,
-                              int32_t* err, int prec, int max_n, cudaStream_t st) {
+int launch_batch_construct_rw(const InstDev* insts, const int* ant_off, int count, int total, int32_t* err,
+                              int prec, int max_n, cudaStream_t st) {
   if (count <= 0 || total <= 0) return ACO_OK;
   if (max_n > kRwMaxN) return set_error(ACO_ERR_UNSUPPORTED, "roulette-wheel construction serves n <= %d", kRwMaxN);
   const size_t smem = rw_smem_bytes(max_n, prec == ACO_FP32 ? 4 : 2);
   switch (prec) {
     case ACO_FP32:
-      batch_construct_rw_kernel<ACO_FP32><<<total, kRwThreads, smem, st>>>(insts, rw_idx, rw_off, count, err);
+      batch_construct_rw_kernel<ACO_FP32><<<total, kRwThreads, smem, st>>>(insts, ant_off, count, err);
       break;
     case ACO_BF16:
-      batch_construct_rw_kernel<ACO_BF16><<<total, kRwThreads, smem, st>>>(insts, rw_idx, rw_off, count, err);
+      batch_construct_rw_kernel<ACO_BF16><<<total, kRwThreads, smem, st>>>(insts, ant_off, count, err);
       break;
     case ACO_FP16:
-      batch_construct_rw_kernel<ACO_FP16><<<total, kRwThreads, smem, st>>>(insts, rw_idx, rw_off, count, err);
+      batch_construct_rw_kernel<ACO_FP16><<<total, kRwThreads, smem, st>>>(insts, ant_off, count, err);
       break;
     default:
       return set_error(ACO_ERR_ARG, "unknown precision %d", prec);

@@ -82,11 +82,10 @@ int prepare_construct_lean();
 // Roulette-wheel construction (Sec. 2.4 baseline), n <= 16384, one 256-thread CTA per ant.
 int launch_construct_rw(const void* P, int prec, int n, int ld, int m, uint2 key, uint32_t it,
                         const uint32_t* it_dev, int32_t* tours, int32_t* err, cudaStream_t st);
-// Every ant of a batch's roulette-wheel instances: rw_idx[j] indexes insts,
-// rw_off holds the exclusive prefix sums of their ant counts (total ants),
-// max_n their largest n.
-int launch_batch_construct_rw(const InstDev* insts, const int* rw_idx, const int* rw_off, int count, int total,
-                              int32_t* err, int prec, int max_n, cudaStream_t st);
+// Every ant of `count` roulette-wheel instances (insts; ant_off: exclusive
+// prefix sums of their ant counts, `total` ants; max_n: their largest n).
+int launch_batch_construct_rw(const InstDev* insts, const int* ant_off, int count, int total, int32_t* err,
+                              int prec, int max_n, cudaStream_t st);
 int prepare_construct_rw();
 constexpr int kModeLean = 2;
 constexpr int kLeanMaxN = 16384;
