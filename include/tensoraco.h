@@ -76,8 +76,8 @@ int aco_init(const float* coords_host, int n, int m, float alpha, float beta, fl
  * q_j = floor(p_j 2^(40-e)), S the sum of the unvisited q, a 64-bit uniform u
  * from Philox counter (2^30, t, k, it) (words 0, 1) and v = floor(u S / 2^64),
  * the next city is the first unvisited j whose running sum of q exceeds v
- * (S = 0: the lowest unvisited j); n <= 16384, no candidate lists, not in
- * batches.  ACO_IR ignores the gammas.  ACO_ADAIR
+ * (S = 0: the lowest unvisited j); n <= 16384, no candidate lists.  ACO_IR
+ * ignores the gammas.  ACO_ADAIR
  * anneals gamma from gamma_max to gamma_min over T iterations by a cosine
  * schedule (gamma_t = gmin + (gmax-gmin)/2 (1 + cos(pi t / T)), gmin after T)
  * and selects argmax(r^gamma p) in the equivalent form argmax(r p^(1/gamma)).
@@ -86,7 +86,8 @@ int aco_set_variant(int roulette, float gamma_max, float gamma_min, int T);
 
 /* Storage precision of M_p: ACO_FP32, ACO_BF16 (RNE), ACO_FP16 (RNE after a
  * per-row power-of-two scale 2^-e_i placing the row maximum in [2^14, 2^15)).
- * Scores are always fp32, tau always fp32.  Takes effect at the next iteration. */
+ * Scores are always fp32; tau is stored as aco_set_tau_precision selects.
+ * Takes effect at the next iteration. */
 int aco_set_precision(int prec);
 
 /* Storage precision of M_tau: ACO_FP32 (default) or ACO_BF16.  With BF16 the
@@ -154,7 +155,7 @@ typedef struct {
   int topk;                 /* paths that deposit (Sec. 2.3): 0 = all (Ant System), else the
                                topk shortest (ties: lower ant index); >= m means all */
   int tau_prec;             /* storage of M_tau: ACO_FP32 (default) or ACO_BF16 (deterministic
-                               deposit only; not in batches) */
+                               deposit only) */
 } aco_params;
 
 /* Fill *p with defaults: alpha 1, beta 2, rho 0.5, Q 1, tau0 1, seed 0, FP32,
@@ -174,8 +175,9 @@ int aco_solver_get_tau(aco_solver* s, float* tau_host);
 int aco_solver_get_tours(aco_solver* s, int32_t* tours_host);
 int aco_solver_get_lengths(aco_solver* s, double* lengths_host);
 /* Device pointers into the solver's state (borrowed, valid until destroy):
- * tau (fp32, leading dimension *ld), tours (int32 m x n), lengths (fp64 m),
- * best tour (int32 n), best length (fp64 1). */
+ * tau (leading dimension *ld; fp32, or bf16 bit patterns when the solver
+ * stores M_tau in bf16), tours (int32 m x n), lengths (fp64 m), best tour
+ * (int32 n), best length (fp64 1). */
 int aco_solver_device_state(aco_solver* s, float** tau, int* ld, int32_t** tours,
                             double** lengths, int32_t** best_tour, double** best_len);
 /* Iterations completed so far. */
@@ -210,12 +212,13 @@ int aco_solver_set_shape(aco_solver* s, int warps, int chunks, int mode);
 
 /* ======================================================================
  * Batches: many independent instances advanced together.  One iteration of
- * a batch is five multi-instance launches over all active instances -- one
- * CTA per (instance, row) for M_p and the deposit, one persistent launch for
- * the construction of every ant of every instance (work items handed out
- * by a global counter, largest n first), one warp per (instance, ant) for
- * the lengths, one CTA per instance for the best -- replayed as a CUDA graph
- * while the active set is unchanged.  Each instance keeps its whole state
+ * a batch is a few multi-instance launches over all active instances -- one
+ * CTA per (instance, row) for M_p, the candidate lists and the deposit, one
+ * persistent launch for the construction of every ant of every IR / AdaIR
+ * instance (work items handed out by a global counter, largest n first), one
+ * CTA per ant of the roulette-wheel instances, one warp per (instance, ant)
+ * for the lengths, one CTA per instance for the best -- replayed as a CUDA
+ * graph while the active set is unchanged.  Each instance keeps its whole state
  * (tau, M_p, tours, best) resident in a workspace carved from the batch's
  * device arena by a first-fit allocator; results are bit-identical to those
  * of a single solver with the same parameters.
