@@ -108,9 +108,10 @@ class Server:
                 active[slot] = r
             if not active:
                 if pending:
-                    if not realtime:
-                        raise RuntimeError(f"request {pending[0].rid} (n={pending[0].n}) does not fit an empty batch")
-                    self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
+                    head = pending[0]
+                    if not realtime or head.arrival <= now:  # it was offered to an empty batch
+                        raise RuntimeError(f"request {head.rid} (n={head.n}) does not fit an empty batch")
+                    self.sleep(max(0.0, head.arrival - (self.clock() - t0)))
                 continue
             self.batch.step(1)
             steps += 1

@@ -117,3 +117,14 @@ def test_cancellation_frees_slots_and_returns_no_result():
     assert reqs[0].finished is None and reqs[0].tour is None
     assert fb.used == 0 and not fb.slots           # every slot and byte returned
     assert ("add", 2) not in fb.log and ("add", 3) not in fb.log
+
+
+def test_request_too_large_for_an_empty_batch_is_an_error():
+    """A request that does not fit even an empty batch stops the server with
+    an error, in real time as well (it would otherwise be offered forever)."""
+    import pytest
+    for realtime in (True, False):
+        clock = FakeClock()
+        srv = serve.Server(FakeBatch(capacity=50), clock=clock, sleep=clock.sleep)
+        with pytest.raises(RuntimeError, match="does not fit an empty batch"):
+            srv.run([_req(0, 0.0, 20, 1), _req(1, 0.5, 80, 1)], realtime=realtime)
