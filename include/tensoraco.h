@@ -14,7 +14,11 @@
  *     and never aborts; aco_last_error() returns a text for the last error of
  *     the calling thread.
  *   - Sizes are element counts.  n = cities (3 <= n <= ACO_MAX_N),
- *     m = ants (1 <= m <= ACO_MAX_M).
+ *     m = ants (1 <= m <= ACO_MAX_M).  The construction kernels serve
+ *     n <= ACO_MAX_N_FP32 with fp32 M_p (ACO_MAX_N_FP32_BATCH in batches),
+ *     n <= ACO_MAX_N with bf16 / fp16 M_p, and n <= ACO_MAX_N_RW for the
+ *     roulette wheel; solvers and batch instances beyond these are refused
+ *     with ACO_ERR_UNSUPPORTED when they are created.
  *   - Arguments named *_host are host pointers, *_dev device pointers.
  *   - Matrices are row-major.  n x n fp32/bf16/fp16 matrices on the device
  *     have a leading dimension `ld` (elements): ld >= n, ld % 8 == 0, base
@@ -49,6 +53,9 @@ extern "C" {
 #define ACO_ERR_TIMEOUT (-6)     /* a bounded device-side wait ran out */
 
 #define ACO_MAX_N 65536
+#define ACO_MAX_N_FP32 49152       /* fp32 M_p: a row staged in at most 192 KB of shared memory */
+#define ACO_MAX_N_FP32_BATCH 32768 /* fp32 M_p inside batches */
+#define ACO_MAX_N_RW 16384         /* roulette-wheel construction */
 #define ACO_MAX_M 1048576
 
 enum { ACO_FP32 = 0, ACO_BF16 = 1, ACO_FP16 = 2 };           /* storage of M_p */

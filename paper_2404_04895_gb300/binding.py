@@ -12,6 +12,7 @@ FP32, BF16, FP16 = 0, 1, 2
 IR, ADAIR, RW = 0, 1, 2
 DEPOSIT_DET, DEPOSIT_ATOMIC = 0, 1
 MAX_N = 65536
+MAX_N_FP32, MAX_N_FP32_BATCH, MAX_N_RW = 49152, 32768, 16384   # construction limits of tensoraco.h
 
 PREC = {"fp32": FP32, "bf16": BF16, "fp16": FP16}
 ROULETTE = {"ir": IR, "adair": ADAIR, "rw": RW}

@@ -512,8 +512,12 @@ int aco_batch_add(aco_batch* b, const float* coords_host, const aco_params* p, i
   if (!b || !coords_host || !p || !slot) return set_error(ACO_ERR_ARG, "NULL argument");
   if (p->prec != b->prec) return set_error(ACO_ERR_ARG, "instance precision %d differs from the batch's %d", p->prec, b->prec);
   if (iters_budget < 0) return set_error(ACO_ERR_ARG, "iters_budget must be >= 0");
-  if (p->roulette == ACO_RW && p->n > kRwMaxN)  // before the arena: a size error, not a full arena
+  // size errors before the arena: an instance no kernel serves is refused, not queued
+  if (p->roulette == ACO_RW && p->n > kRwMaxN)
     return set_error(ACO_ERR_UNSUPPORTED, "roulette-wheel construction serves n <= %d", kRwMaxN);
+  if (p->roulette != ACO_RW && p->prec == ACO_FP32 && p->n > ACO_MAX_N_FP32_BATCH)
+    return set_error(ACO_ERR_UNSUPPORTED, "batched construction with fp32 M_p serves n <= %d",
+                     ACO_MAX_N_FP32_BATCH);
   int q = 0;
   while (q < (int)b->slots.size() && b->slots[q].used) ++q;
   if (q == (int)b->slots.size()) return set_error(ACO_ERR_OOM, "all %d batch slots are in use", q);

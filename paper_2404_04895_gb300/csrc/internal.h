@@ -89,7 +89,7 @@ int launch_batch_construct_rw(const InstDev* insts, const int* ant_off, int coun
 int prepare_construct_rw();
 constexpr int kModeLean = 2;
 constexpr int kLeanMaxN = 16384;
-constexpr int kRwMaxN = 16384;
+constexpr int kRwMaxN = ACO_MAX_N_RW;
 
 int prepare_construct_f32();
 int prepare_construct_bf16();

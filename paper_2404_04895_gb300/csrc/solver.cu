@@ -47,6 +47,19 @@ static const ConstructShape kShapes2[] = {
 #undef X
 };
 
+// The size limits of tensoraco.h are those of the compiled shapes: the
+// widest covers 32 * warps * chunks * (16 / element bytes) columns.
+#define ACO_WIDEST(W, KC, MODE) most = most > 32 * (W) * (KC) * V ? most : 32 * (W) * (KC) * V;
+constexpr int widest_4b() { constexpr int V = 4; int most = 0; ACO_SHAPES_4B(ACO_WIDEST) return most; }
+constexpr int widest_2b() { constexpr int V = 8; int most = 0; ACO_SHAPES_2B(ACO_WIDEST) return most; }
+constexpr int widest_batch_4b() { constexpr int V = 4; int most = 0; ACO_BATCH_SHAPES_4B(ACO_WIDEST) return most; }
+constexpr int widest_batch_2b() { constexpr int V = 8; int most = 0; ACO_BATCH_SHAPES_2B(ACO_WIDEST) return most; }
+#undef ACO_WIDEST
+static_assert(widest_4b() == ACO_MAX_N_FP32, "ACO_MAX_N_FP32 is the widest fp32 shape");
+static_assert(widest_batch_4b() == ACO_MAX_N_FP32_BATCH, "ACO_MAX_N_FP32_BATCH is the widest fp32 batch shape");
+static_assert(widest_2b() >= ACO_MAX_N && widest_batch_2b() >= ACO_MAX_N, "16-bit shapes cover ACO_MAX_N");
+static_assert(kRwMaxN == ACO_MAX_N_RW && kLeanMaxN <= ACO_MAX_N_FP32_BATCH, "size limits");
+
 static const ConstructShape kBatchShapes4[] = {
 #define X(W, KC, MODE) {W, KC, MODE},
     ACO_BATCH_SHAPES_4B(X)
@@ -180,6 +193,8 @@ static int validate(const aco_params* p) {
     return set_error(ACO_ERR_ARG, "unknown roulette %d", p->roulette);
   if (p->roulette == ACO_RW && p->n > kRwMaxN)
     return set_error(ACO_ERR_UNSUPPORTED, "roulette-wheel construction serves n <= %d", kRwMaxN);
+  if (p->roulette != ACO_RW && p->prec == ACO_FP32 && p->n > ACO_MAX_N_FP32)
+    return set_error(ACO_ERR_UNSUPPORTED, "construction with fp32 M_p serves n <= %d", ACO_MAX_N_FP32);
   if (p->deposit != ACO_DEPOSIT_DET && p->deposit != ACO_DEPOSIT_ATOMIC)
     return set_error(ACO_ERR_ARG, "unknown deposit mode %d", p->deposit);
   if (p->roulette == ACO_ADAIR) {
@@ -935,6 +950,12 @@ int aco_set_variant(int roulette, float gamma_max, float gamma_min, int T) {
 
 int aco_set_precision(int prec) {
   if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  if (g_solver) {
+    aco_params p = g_solver->p;
+    p.prec = prec;
+    const int rc = validate(&p);
+    if (rc) return rc;
+  }
   g_pending.prec = prec;
   if (g_solver) {
     g_solver->p.prec = prec;

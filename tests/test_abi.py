@@ -79,3 +79,25 @@ def test_list_sizes_match_header_and_are_enforced():
         B._check_lists(n, np.zeros((n, B.LIST_MAX // 2, 2), np.int32), ok[1], ok[2])
     with pytest.raises(ValueError):
         B._check_lists(n, ok[0], np.zeros(n - 1, np.int32), ok[2])
+
+
+def test_sizes_no_kernel_serves_are_refused_at_creation():
+    """Solvers beyond the construction kernels' limits (fp32 M_p above
+    ACO_MAX_N_FP32, the roulette wheel above ACO_MAX_N_RW) are refused by
+    aco_create before any device work; the binding's limits are the header's."""
+    import numpy as np
+    from paper_2404_04895_gb300 import binding as B
+    text = open(os.path.join(ROOT, "include", "tensoraco.h")).read()
+    for name, val in [("ACO_MAX_N", B.MAX_N), ("ACO_MAX_N_FP32", B.MAX_N_FP32),
+                      ("ACO_MAX_N_FP32_BATCH", B.MAX_N_FP32_BATCH), ("ACO_MAX_N_RW", B.MAX_N_RW)]:
+        assert int(re.search(rf"#define {name} (\d+)", text).group(1)) == val
+    L = B.lib()
+    for prec, n, rou, want in [(B.FP32, B.MAX_N_FP32 + 1, B.IR, B.ERR_UNSUPPORTED),
+                               (B.FP32, B.MAX_N_FP32 + 1, B.ADAIR, B.ERR_UNSUPPORTED),
+                               (B.BF16, B.MAX_N_RW + 1, B.RW, B.ERR_UNSUPPORTED),
+                               (B.BF16, B.MAX_N + 1, B.IR, B.ERR_ARG)]:
+        p = B.make_params(n, 1, prec=prec, roulette=rou)
+        xy = np.zeros((n, 2), np.float32)
+        h = ctypes.c_void_p()
+        assert L.aco_create(ctypes.byref(h), xy.ctypes.data, ctypes.byref(p), None, 0, None) == want
+        assert h.value is None
