@@ -198,6 +198,12 @@ class Dist:
             self.dist.destroy_process_group()
 
 
+def whole_job_value(units_per_rank_step, world, t_max_ms, steps):
+    """Units per second of the whole job: every rank's units of `steps`
+    steps over the slowest rank's timed region (ms)."""
+    return units_per_rank_step * world * steps / (t_max_ms / 1e3)
+
+
 # ---------------------------------------------------------------- CPU oracle leg
 def oracle_sample(w, coords, seed, budget_s=10.0, min_ants=None):
     """Construct tours with the CPU oracle for a sample of the workload's ants
@@ -312,7 +318,7 @@ def run_native(args, w, dist):
     t_max = dist.max(total_ms)
     ms_per_step = t_max / args.steps
     ant_steps = m * (n - 1)
-    value = ant_steps * dist.world / (ms_per_step / 1e3)
+    value = whole_job_value(ant_steps, dist.world, t_max, args.steps)
 
     def full_scan_roofline(construct_ms, shape):
         achieved = alg_bytes / (construct_ms / 1e3) / 1e9
