@@ -101,3 +101,43 @@ def test_sizes_no_kernel_serves_are_refused_at_creation():
         h = ctypes.c_void_p()
         assert L.aco_create(ctypes.byref(h), xy.ctypes.data, ctypes.byref(p), None, 0, None) == want
         assert h.value is None
+
+
+def test_create_refuses_each_invalid_parameter_before_device_work():
+    """aco_create checks every field of aco_params (and the coordinates)
+    against the header's ranges before it touches the device: each invalid
+    value returns its documented code with a message and no handle."""
+    import numpy as np
+    from paper_2404_04895_gb300 import binding as B
+    L = B.lib()
+    n = 10
+    cases = [("n", 2, B.ERR_ARG), ("n", B.MAX_N + 1, B.ERR_ARG), ("m", 0, B.ERR_ARG),
+             ("m", (1 << 20) + 1, B.ERR_ARG), ("alpha", 9, B.ERR_UNSUPPORTED), ("beta", -1, B.ERR_UNSUPPORTED),
+             ("rho", -0.1, B.ERR_ARG), ("rho", 1.5, B.ERR_ARG), ("rho", float("nan"), B.ERR_ARG),
+             ("Q", 0.0, B.ERR_ARG), ("Q", float("inf"), B.ERR_ARG), ("tau0", -1.0, B.ERR_ARG),
+             ("topk", -1, B.ERR_ARG), ("tau_prec", B.FP16, B.ERR_UNSUPPORTED), ("prec", 3, B.ERR_ARG),
+             ("roulette", 3, B.ERR_ARG), ("deposit", 2, B.ERR_ARG)]
+    xy = np.random.default_rng(0).random((B.MAX_N + 1, 2)).astype(np.float32)
+
+    def create(p):
+        h = ctypes.c_void_p()
+        rc = L.aco_create(ctypes.byref(h), xy.ctypes.data, ctypes.byref(p), None, 0, None)
+        assert h.value is None
+        return rc
+
+    for field, value, want in cases:
+        p = B.make_params(n, 5)
+        setattr(p, field, value)
+        assert create(p) == want, (field, value)
+        assert L.aco_last_error(), field
+    p = B.make_params(n, 5, tau_prec="bf16", deposit="atomic")   # bf16 tau needs the exact deposit
+    assert create(p) == B.ERR_UNSUPPORTED
+    for gmax, gmin, T in [(0.0, 0.5, 10), (1.5, 17.0, 10), (1.5, 0.5, 0)]:
+        p = B.make_params(n, 5, roulette="adair", gamma_max=gmax, gamma_min=gmin, gamma_T=T)
+        assert create(p) == B.ERR_ARG, (gmax, gmin, T)
+    bad = xy.copy()
+    bad[3, 1] = np.nan                                             # a coordinate that is not finite
+    h = ctypes.c_void_p()
+    assert L.aco_create(ctypes.byref(h), bad.ctypes.data, ctypes.byref(B.make_params(n, 5)), None, 0,
+                        None) == B.ERR_ARG
+    assert L.aco_create(ctypes.byref(h), None, ctypes.byref(B.make_params(n, 5)), None, 0, None) == B.ERR_ARG
