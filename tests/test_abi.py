@@ -141,3 +141,46 @@ def test_create_refuses_each_invalid_parameter_before_device_work():
     assert L.aco_create(ctypes.byref(h), bad.ctypes.data, ctypes.byref(B.make_params(n, 5)), None, 0,
                         None) == B.ERR_ARG
     assert L.aco_create(ctypes.byref(h), None, ctypes.byref(B.make_params(n, 5)), None, 0, None) == B.ERR_ARG
+
+
+def test_calls_refuse_null_buffers_and_handles_before_device_work():
+    """Every step-level call refuses a NULL device buffer, and the handle
+    calls a NULL handle, with ACO_ERR_ARG; the single-instance calls before
+    aco_init answer ACO_ERR_STATE.  Each case fails its checks before any
+    launch, so this runs on the CPU."""
+    from paper_2404_04895_gb300 import binding as B
+    L = B.lib()
+    N = None
+    ops = [
+        ("aco_op_heuristic", (N, 10, 2, N, N, 16, N)),
+        ("aco_op_fill", (N, 10, 16, 1.0, N)),
+        ("aco_op_build_P", (N, N, 10, 16, 1, 1.0, B.FP32, N, N)),
+        ("aco_op_construct", (N, B.FP32, 10, 16, 4, 0, 0, N, N, N)),
+        ("aco_op_construct_rw", (N, B.FP32, 10, 16, 4, 0, 0, N, N, N)),
+        ("aco_op_construct_shape", (N, B.FP32, 10, 16, 4, 0, 0, N, N, 1, 1, 1, N)),
+        ("aco_op_build_lists", (N, B.FP32, 10, 16, N, N, N, N)),
+        ("aco_op_construct_ex", (N, B.FP32, 10, 16, 4, 0, 0, N, N, N, N, N, 0, 0, 0, N)),
+        ("aco_op_tour_length", (N, 10, N, 4, 1.0, N, N, N, N)),
+        ("aco_op_best", (N, N, 10, 4, N, N, N)),
+        ("aco_op_deposit", (N, 10, 16, N, N, 4, 0.5, N, N)),
+        ("aco_op_deposit_atomic", (N, 10, 16, N, N, 4, 0.5, N)),
+        ("aco_op_deposit_tours_noalloc", (N, 10, 16, N, N, 4, 0.5, 1.0, N, N)),
+        ("aco_op_select_topk", (N, 4, 2, N, N)),
+        ("aco_op_selection_counts", (N, N, 10, 100, 0, 0, N, N)),
+        ("aco_op_philox", (N, 0, N, 4, N)),
+        ("aco_op_pow_own", (N, 0.5, N, 4, N)),
+        ("aco_solver_iterate", (N, 1)),
+        ("aco_solver_best", (N, N, N)),
+        ("aco_solver_get_tau", (N, N)),
+        ("aco_solver_set_shape", (N, 1, 1, 1)),
+        ("aco_batch_add", (N, N, N, 1, N)),
+        ("aco_batch_step", (N, 1)),
+        ("aco_batch_best", (N, 0, N, N)),
+        ("aco_batch_remove", (N, 0)),
+    ]
+    for name, args in ops:
+        assert getattr(L, name)(*args) == B.ERR_ARG, name
+        assert L.aco_last_error(), name
+    assert L.aco_destroy(None) == B.OK            # destroying nothing is allowed
+    assert L.aco_iterate(1) == B.ERR_STATE
+    assert L.aco_best(N, N) == B.ERR_STATE
