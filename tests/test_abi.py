@@ -81,7 +81,7 @@ def test_list_sizes_match_header_and_are_enforced():
         B._check_lists(n, ok[0], np.zeros(n - 1, np.int32), ok[2])
 
 
-def test_sizes_no_kernel_serves_are_refused_at_creation():
+def test_sizes_no_kernel_serves_are_refused_at_creation(lib):
     """Solvers beyond the construction kernels' limits (fp32 M_p above
     ACO_MAX_N_FP32, the roulette wheel above ACO_MAX_N_RW) are refused by
     aco_create before any device work; the binding's limits are the header's."""
@@ -103,7 +103,7 @@ def test_sizes_no_kernel_serves_are_refused_at_creation():
         assert h.value is None
 
 
-def test_create_refuses_each_invalid_parameter_before_device_work():
+def test_create_refuses_each_invalid_parameter_before_device_work(lib):
     """aco_create checks every field of aco_params (and the coordinates)
     against the header's ranges before it touches the device: each invalid
     value returns its documented code with a message and no handle."""
@@ -143,7 +143,7 @@ def test_create_refuses_each_invalid_parameter_before_device_work():
     assert L.aco_create(ctypes.byref(h), None, ctypes.byref(B.make_params(n, 5)), None, 0, None) == B.ERR_ARG
 
 
-def test_calls_refuse_null_buffers_and_handles_before_device_work():
+def test_calls_refuse_null_buffers_and_handles_before_device_work(lib):
     """Every step-level call refuses a NULL device buffer, and the handle
     calls a NULL handle, with ACO_ERR_ARG; the single-instance calls before
     aco_init answer ACO_ERR_STATE.  Each case fails its checks before any
