@@ -99,8 +99,8 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel, kernel_hash, workload_name, prec):
-    """dram bytes per launch of `kernel` from the committed ncu summary, if it
+def profile_counter(kernel, kernel_hash, workload_name, prec, field):
+    """One per-launch counter of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "construct_dram_traffic.json")
     if not os.path.exists(p):
@@ -109,7 +109,28 @@ def traffic_from_profile(kernel, kernel_hash, workload_name, prec):
     e = d.get(f"{kernel}:{workload_name}:{prec}")
     if not e or e.get("kernel_hash") != kernel_hash:
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get(field)
+
+
+def traffic_from_profile(kernel, kernel_hash, workload_name, prec):
+    """dram bytes per launch of `kernel` (ncu), for the current source only."""
+    return profile_counter(kernel, kernel_hash, workload_name, prec, "dram_bytes_per_launch")
+
+
+SCHEDULERS_PER_SM = 4   # warp schedulers of a Blackwell SM, one instruction issued per cycle each
+
+
+def issue_roofline(kernel, inst_per_launch, launch_ms, sms, sm_mhz):
+    """Instruction-issue roofline: warp instructions per launch (ncu) over the
+    launch time, against every scheduler issuing one per cycle at the SM
+    clock sampled during the timed region."""
+    peak = sms * SCHEDULERS_PER_SM * sm_mhz * 1e6 if sms and sm_mhz else None
+    achieved = inst_per_launch / (launch_ms / 1e3) if inst_per_launch and launch_ms > 0 else None
+    return {"bound": "issue", "kernel": kernel, "unit": "warp-instructions/s",
+            "achieved": achieved, "peak": peak,
+            "frac": round(achieved / peak, 4) if achieved and peak else None,
+            "inst_per_launch": inst_per_launch, "sms": sms, "schedulers_per_sm": SCHEDULERS_PER_SM,
+            "sm_mhz": sm_mhz, "avg_launch_ms": round(launch_ms, 4)}
 
 
 # ---------------------------------------------------------------- clocks
@@ -348,6 +369,21 @@ def run_native(args, w, dist):
     else:
         roofline = full_scan_roofline(construct_ms, tuned[0])
     kernel_ms = dict(zip(STEPS, [round(x / args.steps, 4) for x in kern]))
+    issue = None
+    if lists:
+        # the list kernel is bound by each ant's dependent step chain: its
+        # instruction issue rate is the figure that moves with its speed
+        try:
+            issue = issue_roofline("construct_lean_kernel",
+                                   profile_counter("construct_lean_kernel", kh, args.workload, w["prec"],
+                                                   "inst_executed_per_launch"),
+                                   construct_ms,
+                                   torch.cuda.get_device_properties(dist.local).multi_processor_count,
+                                   clocks.get("sm_mhz"))
+            issue["note"] = ("instructions of one captured launch (ncu, 3rd iteration); later iterations "
+                             "take fewer slow paths, so frac is an upper estimate")
+        except Exception as e:  # an auxiliary figure never costs the bench line
+            issue = {"bound": "issue", "error": repr(e)}
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": dist.world,
@@ -363,6 +399,7 @@ def run_native(args, w, dist):
                    "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU",
                    "iters_per_s": round(1e3 / ms_per_step, 2)},
         "roofline": roofline,
+        "issue_roofline": issue,
         "kernel_ms": kernel_ms,
         "gpu_launches": args.steps * (6 if lists else 5),
         "clocks": clocks,

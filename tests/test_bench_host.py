@@ -41,3 +41,20 @@ def test_batch_cpu_baseline_record(bench):
     r = bench.oracle_batch_sample(sizes, budget_s=0.5, stride=128, ants=2)
     assert r["kind"] == "oracle" and r["unit"] == bench.METRIC and r["cores"] >= 1
     assert r["value"] > 0 and "instances [0" in r["sample"]
+
+
+def test_issue_roofline(bench):
+    """Warp instructions per launch over the launch time, against 4 schedulers
+    per SM issuing one instruction per cycle; missing inputs give None, never
+    an exception."""
+    entries = json.load(open(os.path.join(ROOT, "profiles", "construct_dram_traffic.json")))
+    key, e = next(iter(entries.items()))
+    kernel, workload, prec = key.split(":")
+    inst = bench.profile_counter(kernel, e["kernel_hash"], workload, prec, "inst_executed_per_launch")
+    assert inst == e["inst_executed_per_launch"] > 0
+    r = bench.issue_roofline(kernel, 1.2e9, 2.0, 152, 2000.0)
+    assert r["achieved"] == 1.2e9 / 2.0e-3 and r["peak"] == 152 * 4 * 2000.0e6
+    assert r["frac"] == round(r["achieved"] / r["peak"], 4) and r["bound"] == "issue"
+    for args in [(None, 2.0, 152, 2000.0), (1e9, 2.0, 152, None), (1e9, 0.0, 152, 2000.0)]:
+        r = bench.issue_roofline(kernel, *args)
+        assert r["frac"] is None
