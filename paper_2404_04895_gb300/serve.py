@@ -130,6 +130,10 @@ class Server:
 
 
 def summarize(done, wall):
+    if not done:  # every request was cancelled
+        return {"requests": 0, "latency_p50_s": None, "latency_p99_s": None, "latency_mean_s": None,
+                "throughput_req_per_s": 0.0, "ant_steps_per_s": 0.0, "offered_req_per_s": float("nan"),
+                "offered_ant_steps_per_s": float("nan"), "offered_over_served": float("nan"), "wall_s": wall}
     lat = np.array([r.latency for r in done])
     ant_steps = float(sum(r.ant_steps for r in done))
     span = max(r.arrival for r in done) - min(r.arrival for r in done) if len(done) > 1 else 0.0

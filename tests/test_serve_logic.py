@@ -128,3 +128,15 @@ def test_request_too_large_for_an_empty_batch_is_an_error():
         srv = serve.Server(FakeBatch(capacity=50), clock=clock, sleep=clock.sleep)
         with pytest.raises(RuntimeError, match="does not fit an empty batch"):
             srv.run([_req(0, 0.0, 20, 1), _req(1, 0.5, 80, 1)], realtime=realtime)
+
+
+def test_all_cancelled_run_summarizes_to_zero_served():
+    clock = FakeClock()
+    srv = serve.Server(FakeBatch(capacity=100), clock=clock, sleep=clock.sleep)
+    reqs = [_req(0, 0.0, 20, 3), _req(1, 0.0, 20, 3)]
+    for r in reqs:
+        r.cancel_at = 0.0
+    done, wall, steps = srv.run(reqs, realtime=True)
+    assert done == [] and all(r.cancelled for r in reqs)
+    s = serve.summarize(done, wall)
+    assert s["requests"] == 0 and s["latency_p50_s"] is None and s["throughput_req_per_s"] == 0.0
