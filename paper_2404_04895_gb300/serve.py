@@ -23,6 +23,11 @@ import time
 import numpy as np
 
 from . import instances
+from .binding import ERR_ARG, ERR_UNSUPPORTED
+
+# library status codes that describe the request itself: such a request is
+# rejected, the others keep being served
+REQUEST_ERRORS = (ERR_ARG, ERR_UNSUPPORTED)
 
 
 @dataclasses.dataclass
@@ -36,6 +41,7 @@ class Request:
     params: dict = dataclasses.field(default_factory=dict)
     cancel_at: float = None  # seconds from the start of the trace; None: never
     cancelled: bool = False
+    rejected: str = None     # why the solver library refused the request (invalid or unsupported)
     admitted: float = None
     finished: float = None
     best_len: float = None
@@ -82,7 +88,9 @@ class Server:
         """Serve `requests`; returns (finished requests, wall seconds, batched
         steps).  A request whose cancel_at has passed is dropped from the
         queue, or, once admitted, removed between steps (its slot and memory
-        freed, no result); it is marked cancelled and not returned."""
+        freed, no result); it is marked cancelled and not returned.  A
+        request the library refuses (invalid or unsupported parameters or
+        size) is marked rejected with the reason and not returned."""
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         active = {}
         done = []
@@ -100,7 +108,14 @@ class Server:
             # admit arrived requests in order while they fit
             while pending and (pending[0].arrival <= now or not realtime):
                 r = pending[0]
-                slot = self.batch.add(r.coords, r.m, iters=r.iters, seed=r.seed, **r.params)
+                try:
+                    slot = self.batch.add(r.coords, r.m, iters=r.iters, seed=r.seed, **r.params)
+                except RuntimeError as e:
+                    if getattr(e, "code", None) not in REQUEST_ERRORS:
+                        raise
+                    r.rejected = str(e)
+                    pending.pop(0)
+                    continue
                 if slot is None:
                     break
                 pending.pop(0)
@@ -205,7 +220,8 @@ def main(argv=None):
     out = summarize(done, wall)
     out.update({"config": {"requests": args.requests, "rate": args.rate, "n": [args.nmin, args.nmax],
                            "m": "min(n, 1024)", "iters": args.iters, "P_dtype": args.prec,
-                           "arena_gb": args.arena_gb}, "batched_steps": steps})
+                           "arena_gb": args.arena_gb}, "batched_steps": steps,
+                "rejected": sum(1 for r in reqs if r.rejected)})
     print(json.dumps(out))
     return 0
 

@@ -140,3 +140,33 @@ def test_all_cancelled_run_summarizes_to_zero_served():
     assert done == [] and all(r.cancelled for r in reqs)
     s = serve.summarize(done, wall)
     assert s["requests"] == 0 and s["latency_p50_s"] is None and s["throughput_req_per_s"] == 0.0
+
+
+class RefusingBatch(FakeBatch):
+    """Refuses requests above `limit` cities the way the library does."""
+
+    def __init__(self, capacity, limit, code):
+        super().__init__(capacity)
+        self.limit, self.code = limit, code
+
+    def add(self, coords, m, iters, **kw):
+        if coords.shape[0] > self.limit:
+            from paper_2404_04895_gb300.binding import AcoError
+            raise AcoError(self.code, "construction serves n <= %d" % self.limit)
+        return super().add(coords, m, iters, **kw)
+
+
+def test_refused_request_is_rejected_and_the_rest_served():
+    from paper_2404_04895_gb300 import binding as B
+    import pytest
+    clock = FakeClock()
+    srv = serve.Server(RefusingBatch(capacity=100, limit=40, code=B.ERR_UNSUPPORTED), clock=clock,
+                       sleep=clock.sleep)
+    reqs = [_req(0, 0.0, 20, 2), _req(1, 0.0, 50, 2), _req(2, 0.1, 30, 1)]
+    done, wall, steps = srv.run(reqs, realtime=True)
+    assert sorted(r.rid for r in done) == [0, 2]
+    assert reqs[1].rejected and "n <= 40" in reqs[1].rejected and reqs[1].finished is None
+    # a failure of the device, not of the request, still stops the server
+    srv = serve.Server(RefusingBatch(capacity=100, limit=40, code=B.ERR_CUDA), clock=clock, sleep=clock.sleep)
+    with pytest.raises(B.AcoError):
+        srv.run([_req(0, 0.0, 50, 1)], realtime=False)
