@@ -89,7 +89,7 @@ def run(n_list=(100, 422), iters=(0, 1, 2, 5, 10, 20, 50, 100), gammas=(1.0, 1.5
         done = 0
         rng = np.random.default_rng(n)
         cities = rng.choice(n, size=rows, replace=False)
-        for it in iters:
+        for it in sorted(set(iters)):  # the solver only moves forward
             s.iterate(it - done)
             done = it
             P = _rows_p(B, torch, xy, s.tau(), beta=2)
