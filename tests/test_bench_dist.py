@@ -60,3 +60,22 @@ def test_whole_job_value_counts_every_rank_over_the_slowest():
     # 2 ranks, 4 steps of 1000 units each, the slowest rank took 13 ms in all
     assert bench.whole_job_value(1000, 2, 13.0, 4) == 2 * 4 * 1000 / 13.0e-3
     assert bench.whole_job_value(1000, 1, 13.0, 4) == 4 * 1000 / 13.0e-3
+
+
+def test_reference_arm_under_two_ranks_prints_once():
+    """`bench.py --impl reference --gpus 2` as torchrun starts it: rank 0
+    alone runs the oracle and prints the line; rank 1 exits 0 without work."""
+    port = _free_port()
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, RANK=str(r), WORLD_SIZE="2", LOCAL_RANK=str(r),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                                       "--gpus", "2", "--steps", "1", "--warmup", "1", "--workload", "n50_ir"],
+                                      env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=300) for p in procs]
+    for p, (o, e) in zip(procs, outs):
+        assert p.returncode == 0, e
+    lines0 = [x for x in outs[0][0].splitlines() if x.strip()]
+    assert len(lines0) == 1 and json.loads(lines0[0])["n_gpus"] == 2
+    assert outs[1][0].strip() == ""
