@@ -1,0 +1,37 @@
+// Host build of the library's exact deposit arithmetic (csrc/exact.cuh, the
+// integer code the deposit kernel runs) for the CPU tests: one touched
+// pheromone entry, tau' + the exact sum of its paths' weights (Sec. 2.3,
+// Eq. 3), formed the way the kernel forms it -- weights split into 24-bit
+// chunks in units of 2^E0 (E0 the smallest weight exponent), the chunks
+// summed per word in any order, then rounded once.
+#include <climits>
+
+#include "exact.cuh"
+
+extern "C" {
+
+// c: k >= 1 positive finite weights spanning at most kDepSpan binades.
+// Writes fp32 bits (bf16 = 0) or the bfloat16 pattern (bf16 = 1) to *out;
+// returns -1 if the weights are out of the fixed-point range.
+int hx_deposit_entry(float tp, const double* c, int k, int bf16, uint32_t* out) {
+  int e0 = INT_MAX, emax = INT_MIN;
+  for (int i = 0; i < k; ++i) {
+    const int e = aco::exponent_of(c[i]);
+    e0 = e < e0 ? e : e0;
+    emax = e > emax ? e : emax;
+  }
+  if (k < 1 || emax - e0 > aco::kDepSpan) return -1;
+  uint64_t w0 = 0, w1 = 0, w2 = 0;
+  for (int i = k - 1; i >= 0; --i) {  // any order: integer sums
+    uint32_t a, b, d;
+    aco::weight_chunks(c[i], e0, &a, &b, &d);
+    w0 += a;
+    w1 += b;
+    w2 += d;
+  }
+  *out = bf16 ? aco::round_sum_bf16(tp, w0, w1, w2, e0) : aco::bits_of(aco::round_sum_f32(tp, w0, w1, w2, e0));
+  return 0;
+}
+
+int hx_dep_span() { return aco::kDepSpan; }
+}
