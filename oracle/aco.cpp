@@ -280,26 +280,6 @@ void orc_selection_counts(const float* q, const uint8_t* visited, int n, uint64_
   }
 }
 
-// f(s) (Eq. 3): closed tour length, the sum over t = 0..n-1 of
-// d(p_t, p_{t+1 mod n}) in fp64, taken in blocks of 32 consecutive edges:
-// each block t = 32b .. 32b+31 summed in t order, then the block sums added
-// in block order.
-void orc_tour_lengths(const double* D, int n, const int32_t* tours, int m, double* L) {
-  for (int k = 0; k < m; ++k) {
-    const int32_t* p = tours + (size_t)k * n;
-    double total = 0.0;
-    for (int b = 0; 32 * b < n; ++b) {
-      double s = 0.0;
-      for (int t = 32 * b; t < n && t < 32 * b + 32; ++t) {
-        int32_t a = p[t], c = p[(t + 1) % n];
-        s = s + D[(size_t)a * n + c];
-      }
-      total = total + s;
-    }
-    L[k] = total;
-  }
-}
-
 // Exact summation after Shewchuk, "Adaptive Precision Floating-Point
 // Arithmetic" (1997): the running sum is kept as an expansion -- a list of
 // non-overlapping doubles of increasing magnitude whose real sum is exactly
@@ -435,6 +415,19 @@ static float exact_sum_bf16(const double* x, size_t count) {
 }
 
 float orc_exact_sum_bf16(const double* x, int64_t count) { return exact_sum_bf16(x, (size_t)count); }
+
+// f(s) (Eq. 3): the closed tour length, the sum over t = 0..n-1 of
+// d(p_t, p_{t+1 mod n}).  Eq. 3 writes f as a plain sum and fixes no order,
+// so none is imposed: the n fp64 edge lengths are summed exactly and the sum
+// is rounded once to fp64 (ties to even).
+void orc_tour_lengths(const double* D, int n, const int32_t* tours, int m, double* L) {
+  std::vector<double> edges((size_t)n);
+  for (int k = 0; k < m; ++k) {
+    const int32_t* p = tours + (size_t)k * n;
+    for (int t = 0; t < n; ++t) edges[t] = D[(size_t)p[t] * n + p[(t + 1) % n]];
+    L[k] = exact_sum(edges.data(), (size_t)n);
+  }
+}
 
 // Eq. 2: the path and its one-step cyclic shift side by side, row t = (p_t, p_{t-1}).
 void orc_index_matrix(const int32_t* tour, int n, int32_t* I) {

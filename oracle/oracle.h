@@ -39,8 +39,9 @@
  *     for each edge of its closed tour; the new tau_ij is tau'_ij plus the
  *     sum of those weights, taken exactly and rounded once to fp32 (the
  *     paper's sum over paths fixes no order, so none is imposed).
- *   - Tour length: fp64, edges in blocks of 32 consecutive ones, each block
- *     summed in tour order, the block sums added in block order.
+ *   - Tour length (Eq. 3): the n fp64 edge lengths of a tour summed exactly
+ *     and rounded once to fp64 (the paper's sum fixes no order, so none is
+ *     imposed).
  *
  * All matrices here are dense row-major n x n (no padding).
  */
@@ -121,6 +122,8 @@ void orc_selection_counts(const float* q, const uint8_t* visited, int n, uint64_
                           uint64_t seed, uint32_t salt, uint64_t* counts);
 
 /* ---- fitness f (Eq. 3) ---- */
+/* L[k] = the exact sum of tour k's n edge lengths D[p_t][p_{t+1 mod n}],
+ * rounded once to fp64 (ties to even) */
 void orc_tour_lengths(const double* D, int n, const int32_t* tours, int m, double* L);
 /* exact sum of count doubles rounded once to fp64 / to fp32 (ties to even) */
 double orc_exact_sum(const double* x, int64_t count);

@@ -1,7 +1,7 @@
 """Oracle pins for the order-free readings of two sums of the path:
 the deposit (Sec. 2.3, Eq. 3: the real sum of the paths' weights added to the
-evaporated pheromone, rounded once to fp32) and the fitness f (Eq. 3, fp64 in
-blocks of 32 edges).  Exact rational arithmetic (fractions.Fraction) and
+evaporated pheromone, rounded once to fp32) and the fitness f (Eq. 3: the
+exact sum of a tour's fp64 edge lengths rounded once).  Exact rational arithmetic (fractions.Fraction) and
 math.fsum are the independent references."""
 import math
 from fractions import Fraction
@@ -146,21 +146,78 @@ def test_tour_length_integer_grid_exact(orc):
         assert L[k] == float(exact)
 
 
-def test_tour_length_blocked_error_bound(orc):
-    """fp64 in blocks of 32 edges: within (32 + n/32) roundings of the exact
-    sum (fsum), on random planar tours of ragged lengths."""
+def _tour_edges(D, p):
+    n = len(p)
+    return [float(D[p[t], p[(t + 1) % n]]) for t in range(n)]
+
+
+def test_tour_length_is_the_correctly_rounded_sum(orc):
+    """Eq. 3 fixes no order: the oracle's f is the exact sum of the n fp64
+    edge lengths rounded once, i.e. math.fsum (correctly rounded), bit for
+    bit, on random planar tours of ragged lengths and on tours that revisit
+    short and long edges (clustered cities)."""
     rng = np.random.default_rng(15)
-    u = 2.0 ** -53
-    for n in (3, 31, 32, 33, 1000, 1025):
-        xy = rng.uniform(0, 1, size=(n, 2)).astype(np.float32)
-        D = orc.distances(xy)
-        tours = np.stack([rng.permutation(n) for _ in range(4)]).astype(np.int32)
+    for n in (3, 4, 31, 32, 33, 63, 1000, 1025):
+        for kind in ("uniform", "clustered"):
+            if kind == "uniform":
+                xy = rng.uniform(0, 1, size=(n, 2)).astype(np.float32)
+            else:
+                c = rng.uniform(0, 1, size=(max(1, n // 16), 2))
+                xy = (c[rng.integers(0, len(c), size=n)] + rng.normal(0, 1e-3, size=(n, 2))).astype(np.float32)
+            D = orc.distances(xy)
+            tours = np.stack([rng.permutation(n) for _ in range(4)]).astype(np.int32)
+            L = orc.tour_lengths(D, tours)
+            for k in range(4):
+                assert L[k] == math.fsum(_tour_edges(D, tours[k])), (n, kind, k)
+
+
+def test_tour_length_wide_range_matches_rational(orc):
+    """Edge lengths spanning the whole range distances of fp32 coordinates can
+    take ([2^-149, 2^130)) and zeros: the oracle equals the nearest double to
+    the exact rational sum (Python's float(Fraction) rounds correctly)."""
+    rng = np.random.default_rng(16)
+    for trial in range(300):
+        n = int(rng.integers(3, 40))
+        e = rng.uniform(-149, 129, size=(n, n))
+        if trial % 3 == 1:                       # a narrow band plus a few outliers
+            e = rng.uniform(-3, 1, size=(n, n))
+            e[rng.random((n, n)) < 0.05] = rng.uniform(-149, -60)
+        D = np.exp2(e) * rng.uniform(1, 2, size=(n, n))
+        D[rng.random((n, n)) < 0.1] = 0.0        # coincident cities
+        D = np.minimum(D, D.T)
+        np.fill_diagonal(D, 0.0)
+        tours = np.stack([rng.permutation(n) for _ in range(3)]).astype(np.int32)
         L = orc.tour_lengths(D, tours)
-        for k in range(4):
-            p = tours[k]
-            edges = [D[p[t], p[(t + 1) % n]] for t in range(n)]
-            exact = math.fsum(edges)
-            assert abs(L[k] - exact) <= (32 + n / 32 + 2) * u * exact
+        for k in range(3):
+            edges = _tour_edges(D, tours[k])
+            exact = sum((Fraction(v) for v in edges), Fraction(0))
+            assert L[k] == float(exact), (trial, k)
+            assert L[k] == math.fsum(edges)
+
+
+def test_tour_length_ties_and_lost_bits_golden(orc):
+    """Hand-worked sums where any fixed-order fp64 summation is wrong: a tie
+    settled by an edge far below it, and edges each below half an ulp of the
+    running sum that together move it (tests/golden/tour_length_exact.txt)."""
+    rows = [ln.split() for ln in open(golden_path("tour_length_exact.txt")) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) >= 7
+    differ = 0
+    for row in rows:
+        edges = [float.fromhex(v) for v in row[:-1]]
+        want = float.fromhex(row[-1])
+        n = len(edges)
+        # a cycle 0 -> 1 -> ... -> n-1 -> 0 whose t-th edge has length edges[t]
+        D = np.zeros((n, n))
+        for t in range(n):
+            a, b = t, (t + 1) % n
+            D[a, b] = D[b, a] = edges[t]
+        L = orc.tour_lengths(D, np.arange(n, dtype=np.int32)[None, :])
+        assert L[0] == want, row
+        naive = 0.0
+        for v in edges:
+            naive += v
+        differ += naive != want
+    assert differ >= 4   # a left-to-right sum would fail this pin
 
 
 def _rnbf16(x: Fraction) -> np.float32:
