@@ -212,6 +212,18 @@ int aco_solver_load(aco_solver* s, const void* host_buf, size_t bytes);
 int aco_solver_set_profiling(aco_solver* s, int on);
 int aco_solver_kernel_ms(aco_solver* s, float* ms6);
 
+/* Bound on each roulette-wheel step's wait for the copy of its row of M_p
+ * (ACO_RW solvers), in polls of the copy's mbarrier; the default,
+ * ACO_WAIT_POLLS_DEFAULT, is far above a normal copy's wait.  A wait that
+ * runs out makes that ant's CTA record it, let the copy land and stop; the
+ * next call that synchronises the solver returns ACO_ERR_TIMEOUT, once (the
+ * solver's error word is cleared when read).  That iteration's tours and the
+ * state it updated are not meaningful: restore a checkpoint.  polls = 0 makes
+ * every wait give up at once, which exercises this path.  Takes effect at
+ * the next iteration. */
+#define ACO_WAIT_POLLS_DEFAULT 1048576u
+int aco_solver_set_wait_polls(aco_solver* s, uint32_t polls);
+
 /* Choose the construct launch shape (warps, chunks, mode as for
  * aco_op_construct_shape) for this solver: warps = chunks = 0 restores the
  * default (autotuned if aco_autotune_construct ran for its n, m and precision). */
@@ -330,12 +342,14 @@ int aco_op_construct_ex(const void* P_dev, int prec, int n, int ld, int m, uint6
                         const int* lcnt_dev, const uint32_t* lkey_dev, int warps, int chunks,
                         int mode, void* stream);
 
-/* Eq. 3 and the index mapping of Eq. 2: L_k = sum_t D[p_t][p_{t+1 mod n}] in
- * fp64, in blocks of 32 consecutive edges (each summed in t order from 0, the
- * block sums then added in block order) (L_dev, m), c_k = fl64(Q / L_k)
- * (c_dev, m), and for every
- * city a the neighbours of a in tour k: nbr_dev[(a*m + k)*2 + {0,1}] =
- * (predecessor, successor) (nbr_dev: n*m*2 int32, nullable). */
+/* Eq. 3 and the index mapping of Eq. 2: L_k = sum_t D[p_t][p_{t+1 mod n}],
+ * the exact sum of the n fp64 edge lengths rounded once to fp64 (ties to
+ * even; Eq. 3 fixes no order, so the result depends on none) (L_dev, m),
+ * c_k = fl64(Q / L_k) (c_dev, m), and for every city a the neighbours of a in
+ * tour k: nbr_dev[(a*m + k)*2 + {0,1}] = (predecessor, successor) (nbr_dev:
+ * n*m*2 int32, nullable).  The exact sum holds edge lengths of 0 or in
+ * [2^-149, 2^130) -- every distance of fp32 coordinates; a tour with any
+ * other edge length gets L_k = c_k = NaN. */
 int aco_op_tour_length(const double* D_dev, int n, const int32_t* tours_dev, int m, float Q,
                        double* L_dev, double* c_dev, int32_t* nbr_dev, void* stream);
 
@@ -351,9 +365,9 @@ int aco_op_best(const double* L_dev, const int32_t* tours_dev, int n, int m,
  * ants is involved.  Input: nbr/c from aco_op_tour_length; every c_k must be
  * >= 0 or +inf (+inf makes the entries of that tour +inf) and the positive
  * finite ones must lie within a factor 2^19 of each other (true for the
- * tour lengths of one planar instance).  Otherwise the entries are only
- * evaporated and *err_dev (nullable, device int32) is set to 2.
- * tau_dev n x ld, 16-byte aligned, updated in place. */
+ * tour lengths of one planar instance).  Otherwise every entry some path
+ * uses becomes NaN, the others tau'_ab, and *err_dev (nullable, device
+ * int32) is set to 2.  tau_dev n x ld, 16-byte aligned, updated in place. */
 int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const double* c_dev,
                    int m, float rho, int32_t* err_dev, void* stream);
 
@@ -381,23 +395,29 @@ int aco_op_deposit_atomic(float* tau_dev, int n, int ld, const int32_t* tours_de
                           const double* c_dev, int m, float rho, void* stream);
 
 /* Allocation-free tour lengths + deterministic deposit.  The paper has no
- * counterpart: this serves callers that cannot allocate device memory where
- * they update the pheromone (inside CUDA stream capture, in loops that must
- * not block on the allocator, or under a framework-owned memory pool).
+ * counterpart.  It serves callers that cannot allocate device memory where
+ * they update the pheromone: embedders whose device memory all belongs to a
+ * framework pool or a budget fixed at start-up, and loops with a latency
+ * bound, where a cudaMalloc (which may synchronise the device and has no
+ * bounded running time) is not allowed.
  * Same results as aco_op_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c, nbr)
- * followed by aco_op_deposit(tau_dev, n, ld, nbr, c, m, rho, NULL), but the scratch
- * c (m fp64) and nbr (2*n*m int32) lives in a fixed device array inside the
- * library of ACO_NOALLOC_SCRATCH_BYTES (16 MiB; every GPU that loads the
- * library holds it until exit), so 8*m (rounded up to 256) + 8*n*m must fit:
- * larger n*m returns ACO_ERR_ARG.  Inputs/outputs as for the two calls above;
- * L_dev (m fp64) receives the lengths, tau_dev is updated in place.
- * Allocates nothing.  Its first call on a device looks up the array's device
- * address with cudaGetSymbolAddress; make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race. */
+ * followed by aco_op_deposit(tau_dev, n, ld, nbr, c, m, rho, err_dev), but the
+ * scratch c (m fp64) and nbr (2*n*m int32) lives in a fixed device array
+ * inside the library of ACO_NOALLOC_SCRATCH_BYTES (16 MiB; every GPU that
+ * loads the library holds it until exit), so 8*m (rounded up to 256) + 8*n*m
+ * must fit: larger n*m returns ACO_ERR_ARG before any device work.
+ * Inputs/outputs as for the two calls above; L_dev (m fp64) receives the
+ * lengths, tau_dev is updated in place, *err_dev (nullable, device int32) is
+ * set to 2 when the weights Q / L_k cannot be summed exactly (the touched
+ * entries are then NaN).  Allocates nothing.  Its first call on a device
+ * looks up the array's device address with cudaGetSymbolAddress; make that
+ * first call before any stream capture.  Every call clears the array's
+ * index mapping before use.  All calls share the array: calls that overlap
+ * on the GPU race. */
 #define ACO_NOALLOC_SCRATCH_BYTES (16u << 20)
 int aco_op_deposit_tours_noalloc(float* tau_dev, int n, int ld, const double* D_dev,
                                  const int32_t* tours_dev, int m, float rho, float Q,
-                                 double* L_dev, void* stream);
+                                 double* L_dev, int32_t* err_dev, void* stream);
 
 /* Autotuner: times every compiled construct shape that covers n on the
  * given M_p (reps launches each, after one warm-up) and registers the fastest
@@ -413,6 +433,29 @@ int aco_autotune_construct(const void* P_dev, int prec, int n, int ld, int m, ui
 int aco_op_philox(const uint32_t* ctr_dev, uint64_t seed, uint32_t* out_dev, int count,
                   void* stream);
 int aco_op_pow_own(const float* x_dev, float e, float* out_dev, int count, void* stream);
+
+/* Roofline ceilings of the construction step (measurement utilities; the
+ * paper has no counterpart).  Each launch is asynchronous on `stream`; time it
+ * with events and divide the work it states by the time.  sink_dev: one
+ * device u64 the kernels add a checksum to (keeps their work observable).
+ *   aco_ceiling_row_reads: `warps` warps (a multiple of 8) each read
+ *     rows_per_warp whole rows, chosen at random (salt varies the choice), of
+ *     a buffer of `bytes` bytes cut into rows of row_bytes (a multiple of 16)
+ *     with 16-byte coalesced loads -- the full-scan construction's reads of
+ *     M_p rows (Sec. 2.4).  Work: warps * rows_per_warp * row_bytes bytes.
+ *   aco_ceiling_philox: `threads` threads (a multiple of 256) each draw
+ *     blocks_per_thread Philox4x32-10 blocks and score their four words as
+ *     candidates (fl32(r * p), running argmax) -- a step's arithmetic per
+ *     candidate.  Work: 4 * threads * blocks_per_thread candidates.
+ *   aco_ceiling_chase: `chains` CTAs each follow `hops` dependent loads
+ *     j <- next_dev[j] (next_dev: a permutation of 0..slots-1, u32) from slot
+ *     977 * chain; cycles_dev[chain] (u64) receives clock cycles per load. */
+int aco_ceiling_row_reads(const void* buf_dev, size_t bytes, int row_bytes, int warps, int rows_per_warp,
+                          uint32_t salt, unsigned long long* sink_dev, void* stream);
+int aco_ceiling_philox(uint64_t seed, int threads, int blocks_per_thread, uint32_t salt,
+                       unsigned long long* sink_dev, void* stream);
+int aco_ceiling_chase(const uint32_t* next_dev, size_t slots, int chains, int hops,
+                      unsigned long long* cycles_dev, unsigned long long* sink_dev, void* stream);
 
 /* Cosine-annealed gamma of iteration it (host, fp64 rounded to fp32) and
  * fl32(1/gamma); the same values the solvers use. */

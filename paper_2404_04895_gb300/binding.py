@@ -13,6 +13,7 @@ IR, ADAIR, RW = 0, 1, 2
 DEPOSIT_DET, DEPOSIT_ATOMIC = 0, 1
 MAX_N = 65536
 MAX_N_FP32, MAX_N_FP32_BATCH, MAX_N_RW = 49152, 32768, 16384   # construction limits of tensoraco.h
+WAIT_POLLS_DEFAULT = 1048576
 
 PREC = {"fp32": FP32, "bf16": BF16, "fp16": FP16}
 ROULETTE = {"ir": IR, "adair": ADAIR, "rw": RW}
@@ -73,6 +74,10 @@ _SIGS = {
     "aco_solver_set_profiling": (i32, [v, i32]),
     "aco_solver_kernel_ms": (i32, [v, v]),
     "aco_solver_set_shape": (i32, [v, i32, i32, i32]),
+    "aco_solver_set_wait_polls": (i32, [v, u32]),
+    "aco_ceiling_row_reads": (i32, [v, sz, i32, i32, i32, u32, v, v]),
+    "aco_ceiling_philox": (i32, [u64, i32, i32, u32, v, v]),
+    "aco_ceiling_chase": (i32, [v, sz, i32, i32, v, v, v]),
     "aco_autotune_construct": (i32, [v, i32, i32, i32, i32, u64, v, i32, C.POINTER(i32),
                                      C.POINTER(i32), C.POINTER(i32), C.POINTER(f32), v]),
     "aco_batch_create": (i32, [C.POINTER(v), i32, sz, i32, v, v]),
@@ -98,7 +103,7 @@ _SIGS = {
     "aco_op_best": (i32, [v, v, i32, i32, v, v, v]),
     "aco_op_deposit": (i32, [v, i32, i32, v, v, i32, f32, v, v]),
     "aco_op_deposit_atomic": (i32, [v, i32, i32, v, v, i32, f32, v]),
-    "aco_op_deposit_tours_noalloc": (i32, [v, i32, i32, v, v, i32, f32, f32, v, v]),
+    "aco_op_deposit_tours_noalloc": (i32, [v, i32, i32, v, v, i32, f32, f32, v, v, v]),
     "aco_op_philox": (i32, [v, u64, v, i32, v]),
     "aco_op_pow_own": (i32, [v, f32, v, i32, v]),
     "aco_gamma": (f32, [i32, i32, f32, f32]),
@@ -233,12 +238,25 @@ def op_deposit_atomic(tau, n, ld, tours, c, m, rho, stream=None):
     call("aco_op_deposit_atomic", ptr(tau), n, ld, ptr(tours), ptr(c), m, rho, stream_ptr(stream))
 
 
-def op_deposit_tours_noalloc(tau, n, ld, D, tours, m, rho, Q, L, stream=None):
+def op_deposit_tours_noalloc(tau, n, ld, D, tours, m, rho, Q, L, err=None, stream=None):
     call("aco_op_deposit_tours_noalloc", ptr(tau), n, ld, ptr(D), ptr(tours), m, rho, Q, ptr(L),
-         stream_ptr(stream))
+         ptr(err), stream_ptr(stream))
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def ceiling_row_reads(buf, nbytes, row_bytes, warps, rows_per_warp, salt, sink, stream=None):
+    call("aco_ceiling_row_reads", ptr(buf), nbytes, row_bytes, warps, rows_per_warp, salt, ptr(sink),
+         stream_ptr(stream))
+
+
+def ceiling_philox(seed, threads, blocks_per_thread, salt, sink, stream=None):
+    call("aco_ceiling_philox", seed, threads, blocks_per_thread, salt, ptr(sink), stream_ptr(stream))
+
+
+def ceiling_chase(nxt, slots, chains, hops, cycles, sink, stream=None):
+    call("aco_ceiling_chase", ptr(nxt), slots, chains, hops, ptr(cycles), ptr(sink), stream_ptr(stream))
 
 
 def op_philox(ctr, seed, out, count, stream=None):
@@ -377,6 +395,10 @@ class Solver:
 
     def set_shape(self, warps=0, chunks=0, mode=0):
         call("aco_solver_set_shape", self._h, warps, chunks, mode)
+
+    def set_wait_polls(self, polls=None):
+        """Bound on the roulette-wheel kernel's row-copy waits (None: default)."""
+        call("aco_solver_set_wait_polls", self._h, WAIT_POLLS_DEFAULT if polls is None else polls)
         return self
 
     def close(self):

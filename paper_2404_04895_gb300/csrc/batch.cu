@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) batch_tour_length_kernel(const InstDev* _
   const int i = find_instance(ant_off, count, item);
   const InstDev& I = insts[i];
   const int k = item - __ldg(ant_off + i);
-  tour_length_ant(I.D, I.n, I.tours + (size_t)k * I.n, I.m, k, I.Q, I.L, I.c, I.nbr);
+  tour_length_exact<1>(I.D, I.n, I.tours + (size_t)k * I.n, I.m, k, I.Q, I.L, I.c, I.nbr, 0, nullptr);
 }
 
 __global__ void __launch_bounds__(256) batch_best_kernel(const InstDev* __restrict__ insts,
@@ -596,7 +596,7 @@ int aco_batch_best(aco_batch* b, int slot, int32_t* tour_host, double* len_host)
   ACO_CUDA_TRY(cudaStreamSynchronize(b->stream));
   int32_t err = 0;
   ACO_CUDA_TRY(cudaMemcpy(&err, b->d_err, 4, cudaMemcpyDeviceToHost));
-  if (err) return set_error(ACO_ERR_CUDA, "a kernel-side check failed (code %d)", err);
+  if (err) return kernel_check_error(err);
   ACO_CUDA_TRY(cudaMemcpy(len_host, s.dev.best_len, 8, cudaMemcpyDeviceToHost));
   ACO_CUDA_TRY(cudaMemcpy(tour_host, s.dev.best_tour, sizeof(int32_t) * s.p.n, cudaMemcpyDeviceToHost));
   return ACO_OK;

@@ -17,6 +17,7 @@ namespace aco {
 // kernel-side check codes written to an instance's error word
 constexpr int kErrConstruct = 1;     // an ant found no unvisited city
 constexpr int kErrDepositRange = 2;  // deposit weights negative, NaN or spanning > 2^19
+constexpr int kErrTimeout = 3;       // a bounded device-side wait ran out (reported as ACO_ERR_TIMEOUT)
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of

@@ -32,7 +32,7 @@ namespace aco {
 namespace {
 
 constexpr int kRwThreads = 256;
-constexpr uint32_t kRwSpin = 1u << 20;  // bound on one mbarrier wait (polls)
+constexpr uint32_t kRwSpin = kRwWaitPolls;  // bound on the wait that drains a copy after a give-up
 
 __host__ __device__ inline int rw_block(int n) {
   const int q = (n + kRwThreads - 1) / kRwThreads;  // columns per thread, at least
@@ -68,9 +68,9 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 }
 
 // Waits until the mbarrier's phase `parity` has completed, for at most
-// kRwSpin polls; false if it has not.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kRwSpin; ++i) {
+// `polls` polls; false if it has not.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t polls) {
+  for (uint32_t i = 0; i < polls; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -125,10 +125,13 @@ __device__ __forceinline__ uint64_t shfl_up_u64(uint64_t x, int off) {
 }
 
 // The tour of ant k (one CTA of kRwThreads threads; `rsm` holds
-// rw_smem_bytes(n) bytes of dynamic shared memory).
+// rw_smem_bytes(n) bytes of dynamic shared memory).  Each step waits at most
+// `polls` polls for its row copy; when that runs out the CTA sets *err to
+// kErrTimeout, drains the copy (a wait of kRwSpin polls) and stops.
 template <int PREC>
 __device__ __forceinline__ void rw_ant(const void* __restrict__ Pv, int n, int ld, uint2 key, uint32_t it, int k,
-                                       int32_t* __restrict__ tour, int32_t* __restrict__ err, uint4* rsm) {
+                                       int32_t* __restrict__ tour, int32_t* __restrict__ err, uint32_t polls,
+                                       uint4* rsm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kRwThreads / 32;
   constexpr int EB = PREC == ACO_FP32 ? 4 : 2;
@@ -158,11 +161,11 @@ __device__ __forceinline__ void rw_ant(const void* __restrict__ Pv, int n, int l
   uint32_t phase = 0u;
   for (int t = 1; t < n; ++t) {
     if (tid == 0) bulk_load(srow, P + (size_t)cur * row_stride, row_bytes, sbar);
-    const bool landed = mbar_wait(sbar, phase);
+    const bool landed = mbar_wait(sbar, phase, polls);
     phase ^= 1u;
-    if (__syncthreads_or(!landed)) {  // a copy that never lands: report, wait once more, stop
-      if (tid == 0 && err) atomicExch(err, kErrConstruct);
-      mbar_wait(sbar, phase ^ 1u);
+    if (__syncthreads_or(!landed)) {  // the wait ran out: report, let the copy land, stop
+      if (tid == 0 && err) atomicExch(err, kErrTimeout);
+      mbar_wait(sbar, phase ^ 1u, kRwSpin);
       return;
     }
     // pass 1: the largest unvisited value; the lowest unvisited column
@@ -262,12 +265,12 @@ __global__ void __launch_bounds__(kRwThreads) construct_rw_kernel(const void* __
                                                                   uint2 key, uint32_t it_arg,
                                                                   const uint32_t* __restrict__ it_dev,
                                                                   int32_t* __restrict__ tours,
-                                                                  int32_t* __restrict__ err) {
+                                                                  int32_t* __restrict__ err, uint32_t polls) {
   extern __shared__ __align__(16) uint4 rsm[];
   const int k = blockIdx.x;
   if (k >= m) return;
   const uint32_t it = it_dev ? *it_dev : it_arg;
-  rw_ant<PREC>(Pv, n, ld, key, it, k, tours + (size_t)k * n, err, rsm);
+  rw_ant<PREC>(Pv, n, ld, key, it, k, tours + (size_t)k * n, err, polls, rsm);
 }
 
 // Multi-instance form: one CTA per ant of the `count` roulette-wheel
@@ -282,25 +285,25 @@ __global__ void __launch_bounds__(kRwThreads) batch_construct_rw_kernel(const In
   const InstDev& I = insts[i];
   const int k = (int)blockIdx.x - __ldg(ant_off + i);
   if (!I.rw || k >= I.m) return;  // cannot happen for consistent tables
-  rw_ant<PREC>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err, rsm);
+  rw_ant<PREC>(I.P, I.n, I.ld, I.key, *I.it, k, I.tours + (size_t)k * I.n, err, kRwSpin, rsm);
 }
 
 }  // namespace
 
 int launch_construct_rw(const void* P, int prec, int n, int ld, int m, uint2 key, uint32_t it,
-                        const uint32_t* it_dev, int32_t* tours, int32_t* err, cudaStream_t st) {
+                        const uint32_t* it_dev, int32_t* tours, int32_t* err, uint32_t polls, cudaStream_t st) {
   if (n > kRwMaxN) return set_error(ACO_ERR_UNSUPPORTED, "roulette-wheel construction serves n <= %d", kRwMaxN);
   const int eb = prec == ACO_FP32 ? 4 : 2;
   const size_t smem = rw_smem_bytes(n, eb);
   switch (prec) {
     case ACO_FP32:
-      construct_rw_kernel<ACO_FP32><<<m, kRwThreads, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err);
+      construct_rw_kernel<ACO_FP32><<<m, kRwThreads, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err, polls);
       break;
     case ACO_BF16:
-      construct_rw_kernel<ACO_BF16><<<m, kRwThreads, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err);
+      construct_rw_kernel<ACO_BF16><<<m, kRwThreads, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err, polls);
       break;
     case ACO_FP16:
-      construct_rw_kernel<ACO_FP16><<<m, kRwThreads, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err);
+      construct_rw_kernel<ACO_FP16><<<m, kRwThreads, smem, st>>>(P, n, ld, m, key, it, it_dev, tours, err, polls);
       break;
     default:
       return set_error(ACO_ERR_ARG, "unknown precision %d", prec);

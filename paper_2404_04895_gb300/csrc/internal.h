@@ -12,6 +12,9 @@ namespace aco {
 
 int set_error(int code, const char* fmt, ...);
 int cuda_error(cudaError_t e, const char* what);
+// status for a nonzero kernel error word: ACO_ERR_TIMEOUT for a wait that
+// ran out (kErrTimeout), ACO_ERR_CUDA for any other kernel-side check
+int kernel_check_error(int32_t code);
 
 #define ACO_CUDA_TRY(expr)                                  \
   do {                                                      \
@@ -80,8 +83,11 @@ int launch_batch_construct_lean(const InstDev* insts, const int* ant_off, int co
                                 cudaStream_t st);
 int prepare_construct_lean();
 // Roulette-wheel construction (Sec. 2.4 baseline), n <= 16384, one 256-thread CTA per ant.
+// polls: bound on each step's wait for its row copy (kRwWaitPolls by default);
+// a wait that runs out sets *err to kErrTimeout.
+constexpr uint32_t kRwWaitPolls = ACO_WAIT_POLLS_DEFAULT;
 int launch_construct_rw(const void* P, int prec, int n, int ld, int m, uint2 key, uint32_t it,
-                        const uint32_t* it_dev, int32_t* tours, int32_t* err, cudaStream_t st);
+                        const uint32_t* it_dev, int32_t* tours, int32_t* err, uint32_t polls, cudaStream_t st);
 // Every ant of `count` roulette-wheel instances (insts; ant_off: exclusive
 // prefix sums of their ant counts, `total` ants; max_n: their largest n).
 int launch_batch_construct_rw(const InstDev* insts, const int* ant_off, int count, int total, int32_t* err,

@@ -1,7 +1,7 @@
 // The non-construction kernels of one TensorACO iteration (sm_103a):
 //   heuristic   Sec. 2.1: fp64 distances and eta^beta           (once per instance)
 //   build_P     Eq. 1:   M_p = tau^alpha * eta^beta [^(1/gamma)] (per iteration)
-//   tour_length Eq. 3:   f(s) in fp64, Q/f, and the index mapping of Eq. 2
+//   tour_length Eq. 3:   f(s) exact, rounded once to fp64; Q/f; the index mapping of Eq. 2
 //   best        iteration best merged into the running best
 //   deposit     Sec. 2.3: evaporation + Delta M_tau (deterministic / atomic)
 #include <cuda_bf16.h>
@@ -83,14 +83,18 @@ __global__ void __launch_bounds__(256) build_lists_kernel(const void* __restrict
                        lists + (size_t)i * kListMax, lcnt + i, lkey + i, scratch);
 }
 
+// One CTA of W warps per ant (W = 1: 8 ants per CTA, one warp each).
+template <int W>
 __global__ void __launch_bounds__(256) tour_length_kernel(const double* __restrict__ D, int n,
                                                           const int32_t* __restrict__ tours,
                                                           int m, float Q, double* __restrict__ L,
                                                           double* __restrict__ c,
                                                           int32_t* __restrict__ nbr) {
-  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  __shared__ unsigned long long sacc[W * kLenDigits + 1];
+  const int k = W == 1 ? blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) : blockIdx.x;
   if (k >= m) return;
-  tour_length_ant(D, n, tours + (size_t)k * n, m, k, Q, L, c, nbr);
+  tour_length_exact<W>(D, n, tours + (size_t)k * n, m, k, Q, L, c, nbr, W == 1 ? 0 : (int)(threadIdx.x >> 5),
+                       sacc);
 }
 
 __global__ void __launch_bounds__(1024) best_kernel(const double* __restrict__ L,
@@ -259,9 +263,22 @@ int launch_build_lists(const void* P, int prec, int n, int ld, uint2* lists, int
   return check_launch("build_lists_kernel");
 }
 
+// Warps per ant: enough that every warp has a few rounds of four edges per
+// lane, and that a thousand ants fill the GPU several times over.
+int tour_length_warps(int n) { return n >= 2048 ? 4 : (n >= 512 ? 2 : 1); }
+
 int launch_tour_length(const double* D, int n, const int32_t* tours, int m, float Q, double* L,
                        double* c, int32_t* nbr, cudaStream_t st) {
-  tour_length_kernel<<<(m + 7) / 8, 256, 0, st>>>(D, n, tours, m, Q, L, c, nbr);
+  switch (tour_length_warps(n)) {
+    case 4:
+      tour_length_kernel<4><<<m, 128, 0, st>>>(D, n, tours, m, Q, L, c, nbr);
+      break;
+    case 2:
+      tour_length_kernel<2><<<m, 64, 0, st>>>(D, n, tours, m, Q, L, c, nbr);
+      break;
+    default:
+      tour_length_kernel<1><<<(m + 7) / 8, 256, 0, st>>>(D, n, tours, m, Q, L, c, nbr);
+  }
   return check_launch("tour_length_kernel");
 }
 

@@ -330,6 +330,7 @@ struct aco_solver {
   uint32_t* it_dev;
   uint32_t it;                 // iterations completed (host mirror)
   ConstructShape shape;        // {0,0}: default for (n, m, prec)
+  uint32_t wait_polls;         // bound on the roulette-wheel kernel's row-copy waits
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   bool graph_ok;
@@ -388,7 +389,7 @@ static int enqueue_iteration(aco_solver* s) {
   probe(2);
   const uint2 key = make_uint2((uint32_t)p.seed, (uint32_t)(p.seed >> 32));
   if (rw)
-    rc = launch_construct_rw(s->P_f, p.prec, n, s->ld, m, key, 0u, s->it_dev, s->tours, s->err, st);
+    rc = launch_construct_rw(s->P_f, p.prec, n, s->ld, m, key, 0u, s->it_dev, s->tours, s->err, s->wait_polls, st);
   else
     rc = launch_construct(s->P_f, p.prec, n, s->ld, m, key, 0u, s->it_dev, s->tours, s->err, s->shape,
                           lists ? s->lists : nullptr, s->lcnt, s->lkey, st);
@@ -432,12 +433,24 @@ static int build_graph(aco_solver* s) {
   return ACO_OK;
 }
 
+// The host's reading of an error word the kernels set: a wait that ran out
+// is ACO_ERR_TIMEOUT, any other check ACO_ERR_CUDA.
+int kernel_check_error(int32_t code) {
+  if (code == kErrTimeout)
+    return set_error(ACO_ERR_TIMEOUT, "a bounded device-side wait ran out (code %d)", code);
+  return set_error(ACO_ERR_CUDA, "a kernel-side check failed (code %d)", code);
+}
+
+// Waits for the solver's work and reports a kernel-side check once: the
+// error word is cleared when it is read, so the solver stays usable (its
+// state after a failed iteration is not meaningful; restore a checkpoint).
 static int solver_sync_check(aco_solver* s) {
   ACO_CUDA_TRY(cudaStreamSynchronize(s->stream));
   int32_t err = 0;
   ACO_CUDA_TRY(cudaMemcpy(&err, s->err, 4, cudaMemcpyDeviceToHost));
-  if (err) return set_error(ACO_ERR_CUDA, "a kernel-side check failed (code %d)", err);
-  return ACO_OK;
+  if (!err) return ACO_OK;
+  ACO_CUDA_TRY(cudaMemset(s->err, 0, 4));
+  return kernel_check_error(err);
 }
 
 }  // namespace aco
@@ -494,6 +507,7 @@ int aco_create(aco_solver** out, const float* coords_host, const aco_params* p, 
   if (rc) return rc;
   aco_solver* s = new aco_solver();
   s->p = *p;
+  s->wait_polls = kRwWaitPolls;
   s->ld = ld_of(p->n);
   s->stream = static_cast<cudaStream_t>(stream);
   s->lay = layout_of(p->n, p->m);
@@ -812,6 +826,13 @@ int aco_solver_kernel_ms(aco_solver* s, float* ms6) {
   return ACO_OK;
 }
 
+int aco_solver_set_wait_polls(aco_solver* s, uint32_t polls) {
+  if (!s) return set_error(ACO_ERR_ARG, "solver is NULL");
+  s->wait_polls = polls;
+  drop_graph(s);  // the bound is a launch argument of the captured graph
+  return ACO_OK;
+}
+
 int aco_solver_set_shape(aco_solver* s, int warps, int chunks, int mode) {
   if (!s) return set_error(ACO_ERR_ARG, "solver is NULL");
   if (warps || chunks) {
@@ -1108,7 +1129,7 @@ int aco_op_construct_rw(const void* P_dev, int prec, int n, int ld, int m, uint6
   rc = prepare_kernels();
   if (rc) return rc;
   return launch_construct_rw(P_dev, prec, n, ld, m, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), it,
-                             nullptr, tours_dev, err_dev, static_cast<cudaStream_t>(stream));
+                             nullptr, tours_dev, err_dev, kRwWaitPolls, static_cast<cudaStream_t>(stream));
 }
 
 int aco_op_construct(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,

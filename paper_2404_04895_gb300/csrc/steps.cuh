@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "exact.cuh"
+#include "exact_len.cuh"
 
 namespace aco {
 
@@ -94,52 +95,86 @@ __device__ __forceinline__ void build_P_row(const void* __restrict__ tau_row,
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 3 + Eq. 2 for ant k (one warp).  f in fp64 in blocks of 32 consecutive
-// edges: in round r lane l sums block b = 32r + l (edges 32b .. 32b+31) in
-// edge order, then the round's block sums are added to the total in block
-// order -- chains of 32 + n/32 additions instead of n.  For city a = p_t the
-// index mapping nbr[a][k] = (p_{t-1}, p_{t+1}); L_k and c_k = Q / L_k.
+// Eq. 3 + Eq. 2 for ant k, by W cooperating warps (w: this warp's index among
+// them; all W warps of the CTA when W > 1).  f is the exact sum of the n fp64
+// edge lengths D[p_t][p_{t+1 mod n}] rounded once (exact_len.cuh): lane l of
+// warp w takes edges t = 32 w + l + 32 W i, four in flight at a time, adds
+// each to its own fixed-point digits, and the digit sums are combined across
+// lanes (redux on 16-bit halves) and warps (shared memory) -- integer sums, so
+// the split changes no bit.  For city a = p_t the index mapping
+// nbr[a][k] = (p_{t-1}, p_{t+1}); L_k and c_k = Q / L_k.  A tour with an edge
+// length outside the fixed-point range (impossible for distances of fp32
+// coordinates) gets L_k = c_k = NaN.  sacc: W * kLenDigits + 1 shared words
+// (unused when W == 1).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tour_length_ant(const double* __restrict__ D, int n,
-                                                const int32_t* __restrict__ p, int m, int k,
-                                                float Q, double* __restrict__ L,
-                                                double* __restrict__ c,
-                                                int32_t* __restrict__ nbr) {
+template <int W>
+__device__ __forceinline__ void tour_length_exact(const double* __restrict__ D, int n,
+                                                  const int32_t* __restrict__ p, int m, int k,
+                                                  float Q, double* __restrict__ L,
+                                                  double* __restrict__ c,
+                                                  int32_t* __restrict__ nbr, int w,
+                                                  unsigned long long* sacc) {
+  constexpr int U = 4;
   const int lane = threadIdx.x & 31;
-  const int nb = (n + 31) >> 5;
-  double total = 0.0;
-  for (int b0 = 0; b0 < nb; b0 += 32) {
-    const int b = b0 + lane;
-    double s = 0.0;
-    if (b < nb) {
-      const int t0 = b << 5;
-      const int cnt = min(32, n - t0);
-      int prev = __ldg(p + (t0 > 0 ? t0 - 1 : n - 1));
-      int cur = __ldg(p + t0);
-      double d[32];
+  uint64_t acc[kLenDigits];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        d[i] = 0.0;  // past the last edge: adding +0 leaves s unchanged
-        if (i < cnt) {
-          const int t = t0 + i;
-          const int nx = __ldg(p + (t + 1 < n ? t + 1 : 0));
-          // tours come from the construction kernel; an entry out of range
-          // (only after a failed construction, which the host reports) is skipped
-          if ((unsigned)cur < (unsigned)n && (unsigned)nx < (unsigned)n) {
-            d[i] = __ldg(D + (size_t)cur * n + nx);
-            if (nbr) reinterpret_cast<int2*>(nbr)[(size_t)cur * m + k] = make_int2(prev, nx);
+  for (int i = 0; i < kLenDigits; ++i) acc[i] = 0ull;
+  bool bad = false;
+  for (int t0 = 32 * w + lane; t0 < n; t0 += U * 32 * W) {
+    uint64_t db[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + u * 32 * W;
+      db[u] = 0ull;
+      if (t < n) {
+        const int cur = __ldg(p + t);
+        const int nx = __ldg(p + (t + 1 < n ? t + 1 : 0));
+        // tours come from the construction kernel; an entry out of range
+        // (only after a failed construction, which the host reports) is skipped
+        if ((unsigned)cur < (unsigned)n && (unsigned)nx < (unsigned)n) {
+          db[u] = (uint64_t)__double_as_longlong(__ldg(D + (size_t)cur * n + nx));
+          if (nbr) {
+            const int pv = __ldg(p + (t > 0 ? t - 1 : n - 1));
+            reinterpret_cast<int2*>(nbr)[(size_t)cur * m + k] = make_int2(pv, nx);
           }
-          prev = cur;
-          cur = nx;
         }
       }
-#pragma unroll
-      for (int i = 0; i < 32; ++i) s = __dadd_rn(s, d[i]);
     }
-    const int nr = min(32, nb - b0);
-    for (int q = 0; q < nr; ++q) total = __dadd_rn(total, __shfl_sync(ACO_FULL_MASK, s, q));
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      bad |= !len_in_range(db[u]);
+      len_acc_add(acc, db[u]);
+    }
+  }
+  len_acc_carry(acc);  // digits < 2^32 (the last < 2^27): 16-bit halves sum without overflow
+  uint64_t sum[kLenDigits];
+#pragma unroll
+  for (int i = 0; i < kLenDigits; ++i) {
+    const uint32_t lo = __reduce_add_sync(ACO_FULL_MASK, (uint32_t)acc[i] & 0xFFFFu);
+    const uint32_t hi = __reduce_add_sync(ACO_FULL_MASK, (uint32_t)(acc[i] >> 16));
+    sum[i] = (uint64_t)lo + ((uint64_t)hi << 16);
+  }
+  bad = __any_sync(ACO_FULL_MASK, bad);
+  if (W > 1) {
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < kLenDigits; ++i) sacc[w * kLenDigits + i] = sum[i];
+      if (w == 0) sacc[W * kLenDigits] = 0ull;
+    }
+    __syncthreads();
+    if (lane == 0 && bad) atomicOr(sacc + W * kLenDigits, 1ull);
+    __syncthreads();
+    if (w != 0) return;
+#pragma unroll
+    for (int i = 0; i < kLenDigits; ++i) {
+      uint64_t v = 0ull;
+      for (int q = 0; q < W; ++q) v += sacc[q * kLenDigits + i];
+      sum[i] = v;
+    }
+    bad = sacc[W * kLenDigits] != 0ull;
   }
   if (lane == 0) {
+    const double total = bad ? __longlong_as_double(0x7FF8000000000000ll) : len_acc_round(sum);
     L[k] = total;
     if (c) c[k] = __ddiv_rn((double)Q, total);
   }
@@ -357,7 +392,10 @@ __device__ __forceinline__ int2 deposit_scale_block(const double* __restrict__ c
 //      order gives the same bits)
 //   4. one coalesced pass over the row writes tau' or the rounded sum
 // At most `cap` slots are summed per pass; rows with more touched columns
-// take further passes (only their touched columns are rewritten).
+// take further passes (only their touched columns are rewritten).  With
+// weights the fixed point cannot hold (mode kDepBad: a weight negative or NaN,
+// or the positive ones spanning more than kDepSpan binades) every touched
+// entry becomes NaN and the others tau'.
 // smem: deposit_smem_bytes(n, cap).
 // ---------------------------------------------------------------------------
 constexpr int kDepThreads = 256;
@@ -389,17 +427,15 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
   // 1. touched columns
   for (int w = tid; w < nw; w += nthr) bm[w] = 0u;
   __syncthreads();
-  if (mode != kDepBad) {
-    // a bit already seen set needs no atomic (a stale read only repeats one);
-    // ants of weight 0 (not selected) leave their entries at tau'
-    for (int k = tid; k < m; k += nthr) {
-      if (__ldg(c + k) == 0.0) continue;
-      const int2 e = __ldg(nbr_row + k);
-      if ((unsigned)e.x < (unsigned)n && !((bm[e.x >> 5] >> (e.x & 31)) & 1u))
-        atomicOr(bm + (e.x >> 5), 1u << (e.x & 31));
-      if ((unsigned)e.y < (unsigned)n && !((bm[e.y >> 5] >> (e.y & 31)) & 1u))
-        atomicOr(bm + (e.y >> 5), 1u << (e.y & 31));
-    }
+  // a bit already seen set needs no atomic (a stale read only repeats one);
+  // ants of weight 0 (not selected) leave their entries at tau'
+  for (int k = tid; k < m; k += nthr) {
+    if (__ldg(c + k) == 0.0) continue;
+    const int2 e = __ldg(nbr_row + k);
+    if ((unsigned)e.x < (unsigned)n && !((bm[e.x >> 5] >> (e.x & 31)) & 1u))
+      atomicOr(bm + (e.x >> 5), 1u << (e.x & 31));
+    if ((unsigned)e.y < (unsigned)n && !((bm[e.y >> 5] >> (e.y & 31)) & 1u))
+      atomicOr(bm + (e.y >> 5), 1u << (e.y & 31));
   }
   __syncthreads();
 
@@ -445,7 +481,9 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
 
   float* row = static_cast<float*>(row_v);                // fp32 storage
   unsigned short* rowh = static_cast<unsigned short*>(row_v);  // bf16 storage
-  const int npass = D > 0 ? (D + cap - 1) / cap : 1;
+  // weights the fixed point cannot hold (mode kDepBad): one pass that writes
+  // NaN to every touched entry, so the failure shows in tau itself
+  const int npass = D > 0 && mode != kDepBad ? (D + cap - 1) / cap : 1;
   for (int p = 0; p < npass; ++p) {
     const int s0 = p * cap;
     const int used = min(cap, D - s0);
@@ -453,7 +491,7 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
     __syncthreads();
 
     // 3. exact sums
-    if (used > 0) {
+    if (used > 0 && mode != kDepBad) {
       for (int kb = warp * 32; kb < m; kb += nthr) {
         const int k = kb + lane;
         const bool valid = k < m;
@@ -522,6 +560,10 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
           } else {
             write[i] = false;
           }
+          continue;
+        }
+        if (mode == kDepBad) {
+          out[i] = TB ? 0x7FC0u : 0x7FC00000u;
           continue;
         }
         const int sl = slot_of(j0 + i) - s0;

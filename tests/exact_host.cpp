@@ -1,12 +1,17 @@
-// Host build of the library's exact deposit arithmetic (csrc/exact.cuh, the
-// integer code the deposit kernel runs) for the CPU tests: one touched
-// pheromone entry, tau' + the exact sum of its paths' weights (Sec. 2.3,
-// Eq. 3), formed the way the kernel forms it -- weights split into 24-bit
-// chunks in units of 2^E0 (E0 the smallest weight exponent), the chunks
-// summed per word in any order, then rounded once.
+// Host build of the library's exact arithmetic for the CPU tests:
+//   - the deposit (csrc/exact.cuh, the integer code the deposit kernel runs):
+//     one touched pheromone entry, tau' + the exact sum of its paths' weights
+//     (Sec. 2.3, Eq. 3), formed the way the kernel forms it -- weights split
+//     into 24-bit chunks in units of 2^E0 (E0 the smallest weight exponent),
+//     the chunks summed per word in any order, then rounded once;
+//   - the tour length (csrc/exact_len.cuh, the tour-length kernel's code):
+//     the edge lengths dealt to `groups` partial sums the way lanes and warps
+//     take them, each partial sum normalised, the digit sums added, then
+//     rounded once (Eq. 3).
 #include <climits>
 
 #include "exact.cuh"
+#include "exact_len.cuh"
 
 extern "C" {
 
@@ -34,4 +39,25 @@ int hx_deposit_entry(float tp, const double* c, int k, int bf16, uint32_t* out) 
 }
 
 int hx_dep_span() { return aco::kDepSpan; }
+
+// Sum of count edge lengths split round-robin over `groups` partial sums, in
+// reverse order within each group.  Returns -1 (and writes nothing) if an
+// edge is outside the fixed-point range.
+int hx_tour_length(const double* d, int count, int groups, double* out) {
+  if (groups < 1) groups = 1;
+  uint64_t total[aco::kLenDigits] = {};
+  for (int g = 0; g < groups; ++g) {
+    uint64_t acc[aco::kLenDigits] = {};
+    for (int i = count - 1; i >= 0; --i) {
+      if (i % groups != g) continue;
+      const uint64_t b = aco::bits_of(d[i]);
+      if (!aco::len_in_range(b)) return -1;
+      aco::len_acc_add(acc, b);
+    }
+    aco::len_acc_carry(acc);
+    for (int q = 0; q < aco::kLenDigits; ++q) total[q] += acc[q];
+  }
+  *out = aco::len_acc_round(total);
+  return 0;
+}
 }

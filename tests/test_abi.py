@@ -164,7 +164,7 @@ def test_calls_refuse_null_buffers_and_handles_before_device_work(lib):
         ("aco_op_best", (N, N, 10, 4, N, N, N)),
         ("aco_op_deposit", (N, 10, 16, N, N, 4, 0.5, N, N)),
         ("aco_op_deposit_atomic", (N, 10, 16, N, N, 4, 0.5, N)),
-        ("aco_op_deposit_tours_noalloc", (N, 10, 16, N, N, 4, 0.5, 1.0, N, N)),
+        ("aco_op_deposit_tours_noalloc", (N, 10, 16, N, N, 4, 0.5, 1.0, N, N, N)),
         ("aco_op_select_topk", (N, 4, 2, N, N)),
         ("aco_op_selection_counts", (N, N, 10, 100, 0, 0, N, N)),
         ("aco_op_philox", (N, 0, N, 4, N)),

@@ -120,3 +120,25 @@ def test_batch_mixes_roulette_wheel_instances(orc, case):
     assert L == ref.best_len[0] and np.array_equal(tour, ref.best_tour)
     assert np.array_equal(bt.tau(slot), ref.tau)
     bt.close()
+
+
+def test_batch_over_the_batched_workloads_size_range(orc):
+    """24 instances drawn like the batched workload (uniform cities, n from
+    100 to 2000, m = n, rho 0.1, bf16 M_p), the largest at n = 2000: after 3
+    batched iterations the largest and a mid-size instance equal the oracle's
+    whole runs (tours of the last iteration, tau, best) bit for bit."""
+    sizes = [int(x) for x in instances.batch_sizes(24, 100, 2000, seed=8)]
+    sizes[0] = 2000
+    arena = sum(B.instance_bytes(n, n) for n in sizes) + (16 << 20)
+    bt = B.Batch(len(sizes), arena, prec="bf16", stream=torch.cuda.Stream())
+    slots = [bt.add(instances.uniform(n, 1000 + i), n, iters=0, rho=0.1, seed=i) for i, n in enumerate(sizes)]
+    assert all(sl is not None for sl in slots)
+    bt.step(3)
+    mid = int(np.argsort(sizes)[len(sizes) // 2])
+    for i in (0, mid):
+        n = sizes[i]
+        ref = orc.State(instances.uniform(n, 1000 + i), n, rho=0.1, seed=i, prec=orc.BF16).run(3)
+        tour, L = bt.best(slots[i])
+        assert L == ref.best_len[0] and np.array_equal(tour, ref.best_tour), (i, n)
+        assert np.array_equal(bt.tau(slots[i]).view(np.uint32), ref.tau.view(np.uint32)), (i, n)
+    bt.close()

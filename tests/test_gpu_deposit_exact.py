@@ -2,8 +2,9 @@
 for bit, on the cases the fixed-point design has to get right: half-way
 ties, weights spanning the widest allowed range, infinite weights (a zero
 tour length), fp32 subnormal and overflow results, rows with more touched
-columns than one pass holds, and the out-of-range error.  The blocked fp64
-tour length (Eq. 3) is checked at sizes with many rounds of blocks."""
+columns than one pass holds, and the out-of-range error.  The exact tour
+length (Eq. 3) is checked at sizes that split a tour over many lanes and
+warps."""
 import warnings
 
 import numpy as np
@@ -75,9 +76,20 @@ def test_weight_span_limit(orc, span, ok):
     got, ref, err = _deposit(orc, tours, L, tau0, 0.3)
     if ok:
         assert err == 0 and _same(got, ref)
-    else:  # the weights are not summed: the kernel reports it and only evaporates
+    else:  # the weights cannot be summed: the kernel reports it, touched entries are NaN
         assert err == 2
-        assert _same(got, (np.float32(1) - np.float32(0.3)) * tau0)
+        _check_refused(got, tours, tau0, 0.3)
+
+
+def _check_refused(got, tours, tau0, rho):
+    """Every entry some path uses is NaN, every other one evaporated."""
+    n = tau0.shape[0]
+    touched = np.zeros((n, n), bool)
+    for p in tours:
+        for t in range(n):
+            touched[p[t], p[t - 1]] = touched[p[t - 1], p[t]] = True
+    assert np.all(np.isnan(got[touched]))
+    assert _same(got[~touched], ((np.float32(1) - np.float32(rho)) * tau0)[~touched])
 
 
 def test_negative_weight_reports_error(orc):
@@ -86,7 +98,8 @@ def test_negative_weight_reports_error(orc):
     tours = np.stack([rng.permutation(n) for _ in range(m)]).astype(np.int32)
     tau0 = rng.uniform(0.5, 2, size=(n, n)).astype(np.float32)
     got, _, err = _deposit(orc, tours, np.array([2.0, -3.0, 4.0]), tau0, 0.25)
-    assert err == 2 and _same(got, (np.float32(1) - np.float32(0.25)) * tau0)
+    assert err == 2
+    _check_refused(got, tours, tau0, 0.25)
 
 
 def test_infinite_weights(orc):
@@ -133,8 +146,8 @@ def test_random_colonies_bit_exact(orc, n, m, converged):
     assert err == 0 and _same(got, ref)
 
 
-@pytest.mark.parametrize("n,m", [(1025, 9), (5000, 5), (65, 3)])
-def test_blocked_tour_length_bit_exact(orc, n, m):
+@pytest.mark.parametrize("n,m", [(1025, 9), (5000, 5), (65, 3), (3, 4), (511, 7), (2048, 3), (8192, 2)])
+def test_exact_tour_length_bit_exact(orc, n, m):
     xy = instances.uniform(n, 21)
     Dr = orc.distances(xy)
     rng = np.random.default_rng(n)

@@ -1,8 +1,10 @@
 """GPU parity at the benchmark workloads' full sizes, in the solvers' launch
-configuration (CUDA graph, autotuner-free default shape).  The oracle checks
-sampled outputs it can compute one by one: ant tours of a chosen iteration,
-rebuilt from the GPU's own pheromone state, and the deposit of that
-iteration's tours, bit for bit."""
+configuration (CUDA graph, candidate lists, the default shape).  The oracle
+rebuilds a chosen iteration from the GPU's own pheromone state: every ant's
+tour (Sec. 2.2, 2.4), every tour length (Eq. 3) and the deposit of that
+iteration (Sec. 2.3), element by element, bit for bit.  Late iterations are
+included: there the lists decide almost every step and the rare fallback
+paths are the ones exercised."""
 import numpy as np
 import pytest
 import torch
@@ -19,9 +21,10 @@ def cuda():
     B.lib()
 
 
-def _check_iteration(orc, coords, w, prec, run_iters, sample_ants, nthreads=None):
+def _check_iteration(orc, coords, w, prec, run_iters, sample_ants=None, nthreads=None):
     """Run run_iters iterations on the GPU, then one more; check that iteration's
-    sampled tours and its deposit against the oracle started from the GPU's tau."""
+    tours (every ant, or sample_ants) and its deposit against the oracle
+    started from the GPU's tau."""
     kw = dict(m=w["m"], alpha=w["alpha"], beta=w["beta"], rho=w["rho"], Q=w["Q"], seed=w["seed"],
               prec=prec, roulette="adair" if w["adair"] else "ir")
     if w["adair"]:
@@ -46,9 +49,14 @@ def _check_iteration(orc, coords, w, prec, run_iters, sample_ants, nthreads=None
         inv = orc.inv_gamma(orc.gamma(it, w["iters"], 1.5, 0.5))
     pid = {"fp32": orc.FP32, "bf16": orc.BF16, "fp16": orc.FP16}[prec]
     P, _, _ = orc.build_P(tau_before, H, w["alpha"], inv, pid)
-    for k in sample_ants:
-        ref = orc.construct(P, w["seed"], it, k, k + 1, nthreads)
-        assert np.array_equal(tours[k], ref[0]), (prec, it, k)
+    if sample_ants is None:
+        ref = orc.construct(P, w["seed"], it, 0, w["m"], nthreads)
+        bad = np.flatnonzero((ref != tours).any(axis=1))
+        assert bad.size == 0, (prec, it, bad[:10].tolist())
+    else:
+        for k in sample_ants:
+            ref = orc.construct(P, w["seed"], it, k, k + 1, nthreads)
+            assert np.array_equal(tours[k], ref[0]), (prec, it, k)
     # lengths and the deposit of this iteration
     assert np.array_equal(lengths, orc.tour_lengths(D, tours))
     ref_tau = orc.deposit(tau_before, tours, lengths, w["rho"], w["Q"])
@@ -69,15 +77,18 @@ def test_n1000_adair_full_trajectory_start(orc):
     assert g.best()[1] == ref.best_len[0]
 
 
-def test_n1000_adair_late_iteration_sampled(orc):
+def test_n1000_adair_last_iteration_every_ant(orc):
+    # iteration 199, the last of the workload's budget (gamma at its minimum)
     w = instances.WORKLOADS["n1000_adair"]
-    _check_iteration(orc, instances.coords_for(w), w, "fp32", 199, sample_ants=[0, 1, 499, 998, 999])
+    _check_iteration(orc, instances.coords_for(w), w, "fp32", 199)
 
 
+@pytest.mark.parametrize("it", [3, 99])
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
-def test_n5000_clustered_sampled(orc, prec):
+def test_n5000_clustered_every_ant(orc, prec, it):
+    # all 1024 ants of iteration 3 and of iteration 99 (the last of the budget)
     w = instances.WORKLOADS["n5000_clustered"]
-    _check_iteration(orc, instances.coords_for(w), w, prec, 3, sample_ants=[0, 511, 1023])
+    _check_iteration(orc, instances.coords_for(w), w, prec, it)
 
 
 def test_n50_plain_all_iterations(orc):

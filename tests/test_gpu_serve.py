@@ -33,3 +33,25 @@ def test_served_results_equal_solo_results(prec):
         assert r.best_len == L and np.array_equal(r.tour, tour), r.rid
     stats = serve.summarize(done, wall)
     assert stats["latency_p99_s"] >= stats["latency_p50_s"] > 0
+
+
+def test_large_request_in_a_mix_equals_its_solo_run():
+    """A request of 5000 cities (m = 1024) served beside smaller ones that
+    arrive while it runs gives the result of solving it alone, bit for bit."""
+    from paper_2404_04895_gb300 import instances
+    sizes = [5000, 300, 1200, 64, 700]
+    reqs = []
+    for i, n in enumerate(sizes):
+        reqs.append(serve.Request(rid=i, arrival=0.003 * i, coords=instances.uniform(n, 900 + i),
+                                  m=min(n, 1024), seed=40 + i, iters=6 + (i % 3), params=dict(rho=0.1)))
+    arena = sum(B.instance_bytes(n, min(n, 1024)) for n in sizes) + (16 << 20)
+    gb = serve.GpuBatch(arena, 8, "bf16")
+    done, wall, steps = serve.Server(gb).run(reqs, realtime=True)
+    gb.close()
+    assert sorted(r.rid for r in done) == list(range(len(sizes)))
+    assert steps < sum(r.iters for r in done)
+    for r in done:
+        s = B.Solver(r.coords, m=r.m, prec="bf16", seed=r.seed, rho=0.1, stream=torch.cuda.Stream())
+        tour, L = s.iterate(r.iters).best()
+        s.close()
+        assert r.best_len == L and np.array_equal(r.tour, tour), r.rid
