@@ -58,6 +58,8 @@ def parse():
                     help="skip the RW / IR / AdaIR comparison on the bench workload")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched measurement (256 instances, n ~ U{100..2000}, m = n, bf16)")
+    ap.add_argument("--no-ceilings", action="store_true",
+                    help="skip the live ceiling measurements (L2 row reads, Philox, dependent loads)")
     return ap.parse_args()
 
 
@@ -66,6 +68,17 @@ def workload(args):
     if args.prec:
         w["prec"] = args.prec
     return w
+
+
+def config_of(args, w, world):
+    """The workload as both arms name it (identical dicts)."""
+    lists = not args.no_lists
+    return {"workload": args.workload, "kind": w["kind"], "n": w["n"], "m": w["m"], "alpha": w["alpha"],
+            "beta": w["beta"], "rho": w["rho"], "Q": w["Q"], "roulette": "adair" if w["adair"] else "ir",
+            "deposit": "deterministic", "P_dtype": w["prec"], "iterations_budget": w["iters"],
+            "construction": "candidate lists (exact pruning)" if lists else "full scan",
+            "l2": "GPU arm: flushed between timed steps (512 MiB write)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def solver_kwargs(w, seed):
@@ -226,57 +239,57 @@ def whole_job_value(units_per_rank_step, world, t_max_ms, steps):
 
 
 # ---------------------------------------------------------------- CPU oracle leg
-def oracle_sample(w, coords, seed, budget_s=10.0, min_ants=None):
-    """Construct tours with the CPU oracle for a sample of the workload's ants
-    at iteration 0 (the dominant step), on all host cores."""
+def oracle_state(w, coords, seed):
+    import oracle
+    prec = {"fp32": oracle.FP32, "bf16": oracle.BF16, "fp16": oracle.FP16}[w["prec"]]
+    return oracle.State(coords, w["m"], alpha=w["alpha"], beta=w["beta"], rho=w["rho"], Q=w["Q"], seed=seed,
+                        prec=prec, adair=bool(w["adair"]), gamma_max=1.5, gamma_min=0.5, gamma_T=w["iters"])
+
+
+def oracle_iterations(w, coords, seed, max_iters=1, budget_s=None, warmup=0):
+    """Whole iterations of the CPU oracle on the workload (M_p, all m tours,
+    lengths, best, deposit), on all host cores: `warmup` untimed ones, then
+    timed ones until max_iters are done or budget_s is spent (at least one)."""
     import oracle
     threads = oracle.default_threads()
-    n, m = w["n"], w["m"]
-    D = oracle.distances(coords)
-    H = oracle.heuristic(D, w["beta"])
-    inv = oracle.inv_gamma(oracle.gamma(0, w["iters"], 1.5, 0.5)) if w["adair"] else 1.0
-    prec = {"fp32": oracle.FP32, "bf16": oracle.BF16, "fp16": oracle.FP16}[w["prec"]]
-    P, _, _ = oracle.build_P(oracle.init_tau(n), H, w["alpha"], inv, prec)
-    ants, secs = 0, 0.0
-    batch = min_ants or threads
-    while True:
-        k0 = ants % m
-        k1 = min(m, k0 + batch)
+    st = oracle_state(w, coords, seed)
+    for _ in range(warmup):
+        st.run(1, nthreads=threads)
+    times = []
+    while len(times) < max_iters:
         t0 = time.perf_counter()
-        oracle.construct(P, seed, 0, k0, k1, threads)
-        secs += time.perf_counter() - t0
-        ants += k1 - k0
-        if secs >= budget_s or ants >= 1000 * m:
+        st.run(1, nthreads=threads)
+        times.append(time.perf_counter() - t0)
+        if budget_s is not None and sum(times) + times[-1] > budget_s:
             break
-        per_ant = max(secs / ants, 1e-7)
-        batch = max(threads, min(m, int((budget_s - secs) / per_ant)))
-    return {"value": ants * (n - 1) / secs, "unit": METRIC, "cores": threads, "kind": "oracle",
-            "sample": f"{ants} ant tours (ants 0..{m - 1} cyclically, m={m}) of iteration 0 on n={n}, "
-                      f"{secs:.3f} s", "_secs": secs}
+    secs = sum(times)
+    n, m = w["n"], w["m"]
+    return {"value": round(len(times) * m * (n - 1) / secs, 1), "unit": METRIC, "cores": threads,
+            "kind": "oracle", "iterations": len(times), "first_iteration": warmup,
+            "sample": f"{len(times)} whole iteration(s) {warmup}..{warmup + len(times) - 1} of the workload "
+                      f"(M_p, all {m} tours, lengths, best, deposit; n={n}), {secs:.2f} s",
+            "_times": times}
 
 
-def oracle_batch_sample(sizes, budget_s=10.0, stride=32, ants=128):
-    """The CPU oracle on a sample of the batch workload: the first `ants` ants'
-    tours (bf16 M_p at iteration 0) of every `stride`-th instance, on all host
-    cores, until the budget is spent."""
+def oracle_batch_sample(sizes, budget_s=15.0, stride=32):
+    """The CPU oracle on a sample of the batch workload: one whole iteration
+    (bf16 M_p, all m = n tours, lengths, deposit) of every `stride`-th
+    instance, on all host cores, until the budget is spent."""
     import oracle
     threads = oracle.default_threads()
     ant_steps, secs, ids = 0, 0.0, []
     for i in range(0, len(sizes), stride):
         n = int(sizes[i])
-        xy = instances.uniform(n, 1000 + i)
-        H = oracle.heuristic(oracle.distances(xy), 2)
-        P, _, _ = oracle.build_P(oracle.init_tau(n), H, 1, 1.0, oracle.BF16)
-        k = min(n, ants)
+        st = oracle.State(instances.uniform(n, 1000 + i), n, rho=0.1, seed=i, prec=oracle.BF16)
         t0 = time.perf_counter()
-        oracle.construct(P, i, 0, 0, k, threads)
+        st.run(1, nthreads=threads)
         secs += time.perf_counter() - t0
-        ant_steps += k * (n - 1)
+        ant_steps += n * (n - 1)
         ids.append(i)
         if secs >= budget_s:
             break
     return {"value": round(ant_steps / secs, 1), "unit": METRIC, "cores": threads, "kind": "oracle",
-            "sample": f"the first {ants} ants' tours of iteration 0 (bf16 M_p) of instances {ids} "
+            "sample": f"one whole iteration (bf16 M_p, m = n tours, lengths, deposit) of instances {ids} "
                       f"(one in {stride}; n = {[int(sizes[i]) for i in ids]}), {secs:.3f} s"}
 
 
@@ -341,49 +354,71 @@ def run_native(args, w, dist):
     ant_steps = m * (n - 1)
     value = whole_job_value(ant_steps, dist.world, t_max, args.steps)
 
-    def full_scan_roofline(construct_ms, shape):
+    def full_scan_roofline(construct_ms, shape, ceil=None):
         achieved = alg_bytes / (construct_ms / 1e3) / 1e9
         kh = kernel_source_hash("construct_kernel")
-        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_note,
-                "traffic": traffic_from_profile("construct_kernel", kh, args.workload, w["prec"]),
-                "kernel": "construct_kernel", "algorithmic_bytes_per_launch": alg_bytes,
-                "avg_launch_ms": round(construct_ms, 4), "kernel_source_hash": kh,
-                "construct_shape": {"warps_per_ant": shape[0], "chunks_per_lane": shape[1],
-                                    "mode": ["staged", "direct"][shape[2]] if shape[0] else "default"}}
+        out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+               "frac": round(achieved / peak, 4), "peak_source": peak_note,
+               "traffic": traffic_from_profile("construct_kernel", kh, args.workload, w["prec"]),
+               "kernel": "construct_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+               "avg_launch_ms": round(construct_ms, 4), "kernel_source_hash": kh,
+               "construct_shape": {"warps_per_ant": shape[0], "chunks_per_lane": shape[1],
+                                   "mode": ["staged", "direct"][shape[2]] if shape[0] else "default"}}
+        # M_p (100 MB fp32, 50 MB in 16 bits at n = 5000) mostly stays in the L2:
+        # the ceiling its random row reads can reach is measured, not HBM's
+        fp = (n * n * bp) >> 20
+        rr = [r for r in (ceil or {}).get("row_reads", []) if r["footprint_MB"] == (100 if bp == 4 else 50)]
+        if rr and fp <= 128:
+            out["l2_ceiling_GBps"] = rr[0]["GBps"]
+            out["frac_of_l2_ceiling"] = round(achieved / rr[0]["GBps"], 4)
+        return out
 
     construct_ms = kern[2] / args.steps
-    if lists:
-        # the candidate-list kernel decides most steps from a row's top entries
-        # and reads the row only when the list cannot; achieved counts the
-        # algorithmic bytes of a full scan, so frac > 1 is the pruning's effect
-        kh = kernel_source_hash("construct_lean_kernel")
-        achieved = alg_bytes / (construct_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "peak_source": peak_note,
-                    "traffic": traffic_from_profile("construct_lean_kernel", kh, args.workload, w["prec"]),
-                    "kernel": "construct_lean_kernel", "algorithmic_bytes_per_launch": alg_bytes,
-                    "avg_launch_ms": round(construct_ms, 4), "kernel_source_hash": kh,
-                    "note": "exact pruning: achieved = full-scan algorithmic bytes (m*n*(n-1)/2 M_p "
-                            "entries) / launch time; traffic = DRAM bytes the kernel moves (ncu)"}
-    else:
-        roofline = full_scan_roofline(construct_ms, tuned[0])
     kernel_ms = dict(zip(STEPS, [round(x / args.steps, 4) for x in kern]))
-    issue = None
-    if lists:
-        # the list kernel is bound by each ant's dependent step chain: its
-        # instruction issue rate is the figure that moves with its speed
+    sms = torch.cuda.get_device_properties(dist.local).multi_processor_count
+    ceil = None
+    if dist.rank == 0 and not args.no_ceilings:
+        from paper_2404_04895_gb300 import ceilings
         try:
-            issue = issue_roofline("construct_lean_kernel",
-                                   profile_counter("construct_lean_kernel", kh, args.workload, w["prec"],
-                                                   "inst_executed_per_launch"),
-                                   construct_ms,
-                                   torch.cuda.get_device_properties(dist.local).multi_processor_count,
-                                   clocks.get("sm_mhz"))
-            issue["note"] = ("instructions of one captured launch (ncu, 3rd iteration); later iterations "
-                             "take fewer slow paths, so frac is an upper estimate")
+            ceil = ceilings.measure(reps=3)
         except Exception as e:  # an auxiliary figure never costs the bench line
-            issue = {"bound": "issue", "error": repr(e)}
+            ceil = {"error": repr(e)}
+    fs = None
+    if lists and not args.no_full_scan and dist.rank == 0:
+        steps_f = min(args.steps, 20)
+        _, kf, _ = timed_run(w["prec"], steps_f, 3, False)
+        fs = full_scan_roofline(kf[2] / steps_f, tuned[0], ceil)
+    if lists:
+        # The candidate-list kernel decides most steps from a row's top
+        # entries and reads a row only when the list cannot: it moves a small
+        # fraction of the full scan's bytes and is bound by each ant's
+        # dependent step chain, i.e. by instruction issue.  Its roofline is
+        # issue: warp instructions per launch (ncu, this kernel source) over
+        # the launch time, against 4 schedulers x 1 instruction per cycle per
+        # SM at the sampled SM clock.
+        kh = kernel_source_hash("construct_lean_kernel")
+        inst = profile_counter("construct_lean_kernel", kh, args.workload, w["prec"], "inst_executed_per_launch")
+        roofline = issue_roofline("construct_lean_kernel", inst, construct_ms, sms, clocks.get("sm_mhz"))
+        roofline.update({
+            "bound": "alu",
+            "traffic": traffic_from_profile("construct_lean_kernel", kh, args.workload, w["prec"]),
+            "kernel_source_hash": kh,
+            "peak_source": f"{sms} SMs x {SCHEDULERS_PER_SM} schedulers x 1 warp instruction per cycle "
+                           "x the SM clock sampled during the timed region",
+            "inst_source": "ncu inst_executed of one launch of this kernel source (profiles/); None if the "
+                           "source changed since the capture"})
+        clk_mhz = clocks.get("sm_mhz") or 0.0
+        chain = {"cycles_per_ant_step": round(construct_ms * 1e-3 * clk_mhz * 1e6 / (n - 1), 1) if clk_mhz else None,
+                 "note": "launch time x SM clock / (n - 1): every ant walks its n - 1 steps concurrently"}
+        if ceil and "chase" in ceil:
+            chain["dependent_l2_load_cycles"] = ceil["chase"]["cycles_per_load_median"]
+        roofline["step_chain"] = chain
+        if fs:
+            roofline["pruning_speedup"] = round(fs["avg_launch_ms"] / construct_ms, 3)
+            roofline["pruning_note"] = ("full-scan construction time / candidate-list construction time on the "
+                                        "same workload, same tours (both checked against the oracle)")
+    else:
+        roofline = full_scan_roofline(construct_ms, tuned[0], ceil)
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC, "n_gpus": dist.world,
@@ -391,24 +426,18 @@ def run_native(args, w, dist):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[w["prec"]],
         "data": "synthetic",
-        "config": {"workload": args.workload, "kind": w["kind"], "n": n, "m": m, "alpha": w["alpha"],
-                   "beta": w["beta"], "rho": w["rho"], "Q": w["Q"],
-                   "roulette": "adair" if w["adair"] else "ir", "deposit": "deterministic",
-                   "P_dtype": w["prec"], "construction": "candidate lists" if lists else "full scan",
-                   "l2": "flushed between timed steps (512 MiB write)",
-                   "parallelism": f"replicas x{dist.world}" if dist.world > 1 else "single GPU",
-                   "iters_per_s": round(1e3 / ms_per_step, 2)},
+        "config": config_of(args, w, dist.world),
+        "iters_per_s": round(1e3 / ms_per_step, 2),
         "roofline": roofline,
-        "issue_roofline": issue,
         "kernel_ms": kernel_ms,
         "gpu_launches": args.steps * (6 if lists else 5),
         "clocks": clocks,
         "best_len_after_steps": best_len,
     }
-    if lists and not args.no_full_scan and dist.rank == 0:
-        steps_f = min(args.steps, 20)
-        _, kf, _ = timed_run(w["prec"], steps_f, 3, False)
-        out["full_scan_roofline"] = full_scan_roofline(kf[2] / steps_f, tuned[0])
+    if fs and lists:
+        out["full_scan_roofline"] = fs
+    if ceil is not None:
+        out["ceilings"] = ceil
 
     if dist.rank == 0 and not args.no_variants:
         # BF16 / FP16 M_p against fp32 on the same GPU: throughput and best-length gap
@@ -453,8 +482,9 @@ def run_native(args, w, dist):
     if dist.rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, w, coords, seed)
     if dist.rank == 0 and not args.no_cpu_baseline and dist.world == 1:
-        out["cpu_baseline"] = oracle_sample(w, coords, seed)
-        out["cpu_baseline"].pop("_secs")
+        cb = oracle_iterations(w, coords, seed, max_iters=1)
+        cb.pop("_times")
+        out["cpu_baseline"] = cb
     return out
 
 
@@ -582,35 +612,32 @@ def run_e2e(args, w, coords, seed):
 
 
 # ---------------------------------------------------------------- reference leg
+REFERENCE_BUDGET_S = 120.0   # timed whole iterations of the oracle stop once this is spent
+
+
 def run_reference(args, w, dist):
+    """The CPU oracle as it stands, on the host cores: whole iterations of the
+    workload.  The steps actually timed (at most --steps, fewer once the time
+    budget is spent) and warm-up iterations (at most one) are what the line
+    reports, so steps x ms_per_step is the timed wall time."""
     coords = instances.coords_for(w)
     if dist.rank != 0:
         return None
-    per_step_budget = max(0.5, min(8.0, 120.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        oracle_sample(w, coords, w["seed"], budget_s=per_step_budget * 0.25)
-    tot_ants_steps, tot_s, samples = 0.0, 0.0, []
-    for _ in range(args.steps):
-        r = oracle_sample(w, coords, w["seed"], budget_s=per_step_budget)
-        secs = r.pop("_secs")
-        tot_s += secs
-        tot_ants_steps += r["value"] * secs
-        samples.append(r)
-    value = tot_ants_steps / tot_s
-    ms_per_step = (w["m"] * (w["n"] - 1)) / value * 1e3
+    warm = min(args.warmup, 1)
+    r = oracle_iterations(w, coords, w["seed"], max_iters=args.steps, budget_s=REFERENCE_BUDGET_S, warmup=warm)
+    times = r.pop("_times")
+    ms_per_step = 1e3 * sum(times) / len(times)
     return {
-        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": METRIC,
-        "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+        "impl": "reference", "metric": METRIC, "value": r["value"], "unit": METRIC,
+        "n_gpus": dist.world, "steps": len(times), "warmup": warm,
+        "steps_requested": args.steps, "warmup_requested": args.warmup,
         "ms_per_step": round(ms_per_step, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[w["prec"]],
         "data": "synthetic",
-        "config": {"workload": args.workload, "kind": w["kind"], "n": w["n"], "m": w["m"],
-                   "P_dtype": w["prec"], "roulette": "adair" if w["adair"] else "ir"},
-        "cpu_baseline": {"value": round(value, 1), "unit": METRIC, "cores": samples[0]["cores"],
-                         "kind": "oracle",
-                         "sample": f"each step: ant tours of iteration 0 for ~{per_step_budget:.1f} s; "
-                                   f"ms_per_step extrapolates one full iteration's m*(n-1) ant-steps"},
-        "e2e": {"value": round(value, 1), "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": config_of(args, w, dist.world),
+        "cpu_baseline": {"value": r["value"], "unit": METRIC, "cores": r["cores"], "kind": "oracle",
+                         "sample": r["sample"] + f"; timing stops once {REFERENCE_BUDGET_S:.0f} s are spent"},
+        "e2e": {"value": r["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 

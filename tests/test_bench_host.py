@@ -36,11 +36,22 @@ def test_kernel_source_hash_follows_the_files(bench):
 
 
 def test_batch_cpu_baseline_record(bench):
-    from paper_2404_04895_gb300 import instances
-    sizes = [int(x) for x in instances.batch_sizes(256, 100, 2000, seed=7)]
-    r = bench.oracle_batch_sample(sizes, budget_s=0.5, stride=128, ants=2)
+    """Whole oracle iterations of sampled batch instances (small sizes here)."""
+    r = bench.oracle_batch_sample([60, 70, 80, 90], budget_s=0.0, stride=2)
     assert r["kind"] == "oracle" and r["unit"] == bench.METRIC and r["cores"] >= 1
-    assert r["value"] > 0 and "instances [0" in r["sample"]
+    assert r["value"] > 0 and "instances [0]" in r["sample"] and "whole iteration" in r["sample"]
+
+
+def test_cpu_baseline_times_whole_iterations(bench):
+    """The oracle leg runs complete iterations (M_p, tours, lengths, deposit)
+    and reports what it timed; the budget stops it after at least one."""
+    from paper_2404_04895_gb300 import instances
+    w = dict(instances.WORKLOADS["n50_ir"])
+    r = bench.oracle_iterations(w, instances.coords_for(w), 0, max_iters=3, warmup=1)
+    assert r["iterations"] == 3 and len(r["_times"]) == 3 and r["first_iteration"] == 1
+    assert r["value"] == round(3 * w["m"] * (w["n"] - 1) / sum(r["_times"]), 1)
+    r = bench.oracle_iterations(w, instances.coords_for(w), 0, max_iters=50, budget_s=0.0)
+    assert r["iterations"] == 1
 
 
 def test_issue_roofline(bench):
@@ -78,3 +89,21 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference" and d["config"]["workload"] == "n50_ir" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # whole iterations, as many as were timed: steps x ms_per_step is the timed work
+    assert d["steps"] == 1 and d["warmup"] == 1
+    w = dict(__import__("paper_2404_04895_gb300.instances", fromlist=["x"]).WORKLOADS["n50_ir"])
+    assert abs(d["value"] - w["m"] * (w["n"] - 1) / (d["ms_per_step"] / 1e3)) / d["value"] < 1e-2
+
+
+def test_both_arms_name_the_same_config(bench):
+    """The native and reference lines carry the identical config dict."""
+    from paper_2404_04895_gb300 import instances
+
+    class Args:
+        workload, no_lists = "n5000_clustered", False
+    w = dict(instances.WORKLOADS["n5000_clustered"])
+    c = bench.config_of(Args(), w, 1)
+    for k in ("workload", "n", "m", "alpha", "beta", "rho", "Q", "roulette", "deposit", "P_dtype", "construction",
+              "l2", "parallelism"):
+        assert k in c, k
+    assert c == bench.config_of(Args(), dict(w), 1)
