@@ -434,6 +434,21 @@ int aco_op_philox(const uint32_t* ctr_dev, uint64_t seed, uint32_t* out_dev, int
                   void* stream);
 int aco_op_pow_own(const float* x_dev, float e, float* out_dev, int count, void* stream);
 
+/* Construction with step probes (a measurement utility; the paper has no
+ * counterpart): aco_op_construct_ex's candidate-list construction of all m
+ * ants (same tours; 32 <= n <= 16384, lists from aco_op_build_lists) in which
+ * ant probe_ant also records each step t = 1..n-1 as 8 u32 at
+ * probe_dev[8*t ..]: the SM clock at the step's start; the cycles from it
+ * until the step's first list entry is available, its Philox block is done,
+ * its speculative list loads are issued, the first round's decision, the
+ * decision after any slower path, and the end of the step; flags (1: the
+ * first round decided, 2: later list rounds ran, 4: a full scan ran, 8 / 16:
+ * the next list came from speculation slot 0 / 1).  probe_dev: 8*n u32.  The
+ * clock reads cost a few cycles of their own. */
+int aco_op_construct_probe(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,
+                           int32_t* tours_dev, int32_t* err_dev, const void* lists_dev, const uint32_t* lkey_dev,
+                           int probe_ant, uint32_t* probe_dev, void* stream);
+
 /* Roofline ceilings of the construction step (measurement utilities; the
  * paper has no counterpart).  Each launch is asynchronous on `stream`; time it
  * with events and divide the work it states by the time.  sink_dev: one

@@ -75,6 +75,7 @@ _SIGS = {
     "aco_solver_kernel_ms": (i32, [v, v]),
     "aco_solver_set_shape": (i32, [v, i32, i32, i32]),
     "aco_solver_set_wait_polls": (i32, [v, u32]),
+    "aco_op_construct_probe": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, v, v, i32, v, v]),
     "aco_ceiling_row_reads": (i32, [v, sz, i32, i32, i32, u32, v, v]),
     "aco_ceiling_philox": (i32, [u64, i32, i32, u32, v, v]),
     "aco_ceiling_chase": (i32, [v, sz, i32, i32, v, v, v]),
@@ -244,6 +245,11 @@ def op_deposit_tours_noalloc(tau, n, ld, D, tours, m, rho, Q, L, err=None, strea
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def op_construct_probe(P, prec, n, ld, m, seed, it, tours, lists, lkey, probe_ant, probe, err=None, stream=None):
+    call("aco_op_construct_probe", ptr(P), prec, n, ld, m, seed, it, ptr(tours), ptr(err), ptr(lists), ptr(lkey),
+         probe_ant, ptr(probe), stream_ptr(stream))
 
 
 def ceiling_row_reads(buf, nbytes, row_bytes, warps, rows_per_warp, salt, sink, stream=None):

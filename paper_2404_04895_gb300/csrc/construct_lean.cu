@@ -42,6 +42,14 @@ cudaError_t launch_batch_lean(int grid, size_t smem, cudaStream_t st, const Inst
   return cudaGetLastError();
 }
 
+template <int PREC>
+void launch_probe(size_t smem, cudaStream_t st, const void* P, int n, int ld, int m, uint2 key, uint32_t it,
+                  int32_t* tours, int32_t* err, const uint2* lists, const uint32_t* lkey, int probe_ant,
+                  uint32_t* probe) {
+  construct_lean_probe_kernel<PREC><<<m, 32, smem, st>>>(P, n, ld, m, key, it, tours, err, lists, lkey, probe_ant,
+                                                         probe);
+}
+
 template <int PREC, bool FULL0>
 cudaError_t allow_smem(int most) {
   cudaError_t e = cudaFuncSetAttribute(construct_lean_kernel<PREC, FULL0, true>,
@@ -52,6 +60,8 @@ cudaError_t allow_smem(int most) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(batch_construct_lean_kernel<PREC, FULL0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              most);
+  if (e == cudaSuccess && FULL0)
+    e = cudaFuncSetAttribute(construct_lean_probe_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
   return e;
 }
 
@@ -122,3 +132,30 @@ int prepare_construct_lean() {
 }
 
 }  // namespace aco
+
+using namespace aco;
+
+extern "C" int aco_op_construct_probe(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,
+                                      int32_t* tours_dev, int32_t* err_dev, const void* lists_dev,
+                                      const uint32_t* lkey_dev, int probe_ant, uint32_t* probe_dev, void* stream) {
+  if (!P_dev || !tours_dev || !lists_dev || !lkey_dev || !probe_dev) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (n < 32 || n > kLeanMaxN) return set_error(ACO_ERR_ARG, "the probed construction serves 32 <= n <= %d", kLeanMaxN);
+  if (ld < n || (ld & 7) || !aligned16(P_dev)) return set_error(ACO_ERR_ARG, "P: ld >= n, a multiple of 8, 16-byte aligned");
+  if (m < 1 || m > ACO_MAX_M || probe_ant < 0 || probe_ant >= m) return set_error(ACO_ERR_ARG, "m or probe_ant out of range");
+  if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  int rc = prepare_kernels();
+  if (rc) return rc;
+  const int eb = prec == ACO_FP32 ? 4 : 2;
+  const size_t smem = lean_smem_bytes(n, eb, 1);
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint2* L = static_cast<const uint2*>(lists_dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (prec == ACO_FP32)
+    launch_probe<ACO_FP32>(smem, st, P_dev, n, ld, m, key, it, tours_dev, err_dev, L, lkey_dev, probe_ant, probe_dev);
+  else if (prec == ACO_BF16)
+    launch_probe<ACO_BF16>(smem, st, P_dev, n, ld, m, key, it, tours_dev, err_dev, L, lkey_dev, probe_ant, probe_dev);
+  else
+    launch_probe<ACO_FP16>(smem, st, P_dev, n, ld, m, key, it, tours_dev, err_dev, L, lkey_dev, probe_ant, probe_dev);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? ACO_OK : cuda_error(e, "construct_lean_probe_kernel launch");
+}

@@ -193,19 +193,39 @@ __device__ __forceinline__ int lean_full_scan(const char* __restrict__ row, int 
   return next;
 }
 
+// Step probes (PROBE instantiations only): the SM clock (%clock) read after
+// `dep` is available, so that the stamp cannot come before the value.
+__device__ __forceinline__ uint32_t clock_after(uint32_t dep) {
+  uint32_t t;
+  asm volatile("mov.u32 %0, %%clock;" : "=r"(t) : "r"(dep) : "memory");
+  return t;
+}
+
+// Probe record of one step of one ant: 8 words.
+//   [0] clock at the step's start   [1..6] cycles from it until: the step's
+//   first list entry is available, its Philox block is done, the speculative
+//   list loads are issued, the first round's decision, the slow paths'
+//   decision, the end of the step's bookkeeping   [7] flags: 1 the first
+//   round decided, 2 later list rounds ran, 4 a full scan ran, 8/16 the next
+//   list came from speculation slot 0/1 (else it was loaded after the step).
+constexpr int kProbeWords = 8;
+
 // NA ants walked by one warp: ants k[q], tours tour[q], visited flags svis[q].
 // FULL0: every list has >= 32 entries (n >= 32: a list holds at least
 // min(kListTarget, n) of the row's n columns), so its first round has no
 // padded slot.  LISTS: candidate lists are given (else every step is a
 // compact full scan).  Both are compile-time: with them fixed the step's
 // control flow is straight (measured 17-19% faster than testing them per step).
-template <int PREC, int NA, bool FULL0, bool LISTS>
+// PROBE: lane 0 of ant 0 writes one probe record per step to probe[t * 8]
+// (NA == 1; a measurement build: the clock reads change the schedule a little).
+template <int PREC, int NA, bool FULL0, bool LISTS, bool PROBE = false>
 __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv, int n, int ld, uint2 key,
                                                     uint32_t it, const int* k, int32_t* const* tour,
                                                     int32_t* __restrict__ err,
                                                     const uint2* __restrict__ lists,
                                                     const uint32_t* __restrict__ lkey,
-                                                    uint4* __restrict__ srow, uint32_t* const* svis) {
+                                                    uint4* __restrict__ srow, uint32_t* const* svis,
+                                                    uint32_t* __restrict__ probe = nullptr) {
   using E = Elem<PREC>;
   const int lane = threadIdx.x & 31;
   const char* __restrict__ P = static_cast<const char*>(Pv);
@@ -236,6 +256,8 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
     float bs[NA];
     int bj[NA];
     bool more[NA];
+    uint32_t pr[kProbeWords] = {};
+    if constexpr (PROBE) pr[0] = clock_after(0u);
     // ---- first list round of every ant: one straight-line block
 #pragma unroll
     for (int q = 0; q < NA; ++q) {
@@ -245,6 +267,7 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
       more[q] = false;
       if (LISTS) {
         const uint2 e = lr[q].e;
+        if constexpr (PROBE) pr[1] = clock_after(e.y) - pr[0];
         const bool valid = FULL0 || e.y != kListPad;
         const int j = FULL0 ? (int)e.y : (valid ? (int)e.y : 0);
         uint4 xc = make_uint4((uint32_t)(j >> 2), (uint32_t)t, (uint32_t)k[q], it);
@@ -264,6 +287,7 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
         philox_round(xc, ks, 7);
         sp[q][0] = load_list_row(lists, lkey, sj);
         sp[q][1] = load_list_row(lists, lkey, sj2);
+        if constexpr (PROBE) pr[3] = clock_after((uint32_t)sj2) - pr[0];
         if (!un) sp[q][0].row = -1;
         if (!un2) sp[q][1].row = -1;
         more[q] = (vm >> 31) != 0u && kListMax / 32 > 1;
@@ -272,6 +296,7 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
         philox_round(xc, ks, 8);
         philox_round(xc, ks, 9);
         const uint4 x = xc;
+        if constexpr (PROBE) pr[2] = clock_after(x.x ^ x.y ^ x.z ^ x.w) - pr[0];
         const uint32_t w = (j & 2) ? ((j & 1) ? x.w : x.z) : ((j & 1) ? x.y : x.x);
         const float sc = __fmul_rn(uniform01(w), __uint_as_float(e.x));
         {
@@ -284,20 +309,28 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
         const uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs[q]));
         const int win = (int)__reduce_min_sync(ACO_FULL_MASK, score_key(bs[q]) == lk ? (uint32_t)bj[q] : 0x7FFFFFFFu);
         if (lk > rest) next[q] = win;
+        if constexpr (PROBE) {
+          pr[4] = clock_after((uint32_t)win) - pr[0];
+          pr[7] |= next[q] >= 0 ? 1u : 0u;
+        }
       }
     }
     // ---- later rounds and full scans, ant by ant (rare)
 #pragma unroll
     for (int q = 0; q < NA; ++q) {
 
-      if (next[q] < 0 && LISTS && (FULL0 || more[q]))
+      if (next[q] < 0 && LISTS && (FULL0 || more[q])) {
         next[q] = lean_more_rounds(lists, lr[q], svis[q], ks, it, k[q], t, bs[q], bj[q]);
+        if constexpr (PROBE) pr[7] |= 2u;
+      }
       if (next[q] < 0) {
         const uint32_t hi = (LISTS && lr[q].lb) ? lr[q].lb - 1u : 0xFFFFFFFFu;
         next[q] = lean_full_scan<PREC>(P + (size_t)cur[q] * row_bytes, n, hi, svis[q], srow, ks, it, k[q], t,
                                        bs[q], bj[q]);
+        if constexpr (PROBE) pr[7] |= 4u;
       }
     }
+    if constexpr (PROBE) pr[5] = clock_after((uint32_t)next[0]) - pr[0];
     // ---- bookkeeping
     bool bad = false;
 #pragma unroll
@@ -319,11 +352,21 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
       if (LISTS) {  // after the last step: one unused load of a valid row
         if (sp[q][0].row == next[q]) {
           lr[q] = sp[q][0];
+          if constexpr (PROBE) pr[7] |= 8u;
         } else if (sp[q][1].row == next[q]) {
           lr[q] = sp[q][1];
+          if constexpr (PROBE) pr[7] |= 16u;
         } else {
           lr[q] = load_list_row(lists, lkey, next[q]);
         }
+      }
+    }
+    if constexpr (PROBE) {
+      pr[6] = clock_after((uint32_t)cur[0]) - pr[0];
+      if (lane == 0) {
+        uint4* o = reinterpret_cast<uint4*>(probe + (size_t)t * kProbeWords);
+        o[0] = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+        o[1] = make_uint4(pr[4], pr[5], pr[6], pr[7]);
       }
     }
   }
@@ -354,6 +397,28 @@ __global__ void __launch_bounds__(32) construct_lean_kernel(
   }
   const uint32_t it = it_dev ? *it_dev : it_arg;
   construct_ants_lean<PREC, kLeanAnts, FULL0, LISTS>(Pv, n, ld, key, it, k, tour, err, lists, lkey, lsm, svis);
+}
+
+// The lean kernel with step probes: every ant walks as in construct_lean_kernel
+// (lists, n >= 32); ant `probe_ant` also writes one probe record per step to
+// probe[t * kProbeWords] (t = 1 .. n-1).
+template <int PREC>
+__global__ void __launch_bounds__(32) construct_lean_probe_kernel(
+    const void* __restrict__ Pv, int n, int ld, int m, uint2 key, uint32_t it, int32_t* __restrict__ tours,
+    int32_t* __restrict__ err, const uint2* __restrict__ lists, const uint32_t* __restrict__ lkey, int probe_ant,
+    uint32_t* __restrict__ probe) {
+  extern __shared__ __align__(16) uint4 lsm[];
+  const int k0 = blockIdx.x;
+  if (k0 >= m) return;
+  const int eb = PREC == ACO_FP32 ? 4 : 2;
+  const int chunks = (n + 16 / eb - 1) / (16 / eb);
+  uint32_t* svis[1] = {reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(lsm + ((chunks + 31) / 32) * 32))};
+  int k[1] = {k0};
+  int32_t* tour[1] = {tours + (size_t)k0 * n};
+  if (k0 == probe_ant)
+    construct_ants_lean<PREC, 1, true, true, true>(Pv, n, ld, key, it, k, tour, err, lists, lkey, lsm, svis, probe);
+  else
+    construct_ants_lean<PREC, 1, true, true, false>(Pv, n, ld, key, it, k, tour, err, lists, lkey, lsm, svis);
 }
 
 // Multi-instance form: persistent warps pull (instance, ant) items; every
