@@ -168,37 +168,135 @@ def summarize(done, wall):
 
 
 class GpuBatch:
-    """binding.Batch on its own stream, with the sync the server needs."""
+    """binding.Batch on its own stream of one device (default: the current
+    one), with the sync the server needs; every call runs with that device
+    current."""
 
-    def __init__(self, arena_bytes, max_slots, prec):
+    def __init__(self, arena_bytes, max_slots, prec, device=None):
         import torch
 
         from . import binding
         binding.lib()
         self.torch = torch
-        self.stream = torch.cuda.Stream()
-        self.b = binding.Batch(max_slots, arena_bytes, prec=prec, stream=self.stream)
+        self.device = torch.cuda.current_device() if device is None else device
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.Stream()
+            self.b = binding.Batch(max_slots, arena_bytes, prec=prec, stream=self.stream)
+
+    def _on(self):
+        return self.torch.cuda.device(self.device)
 
     def add(self, coords, m, iters, **kw):
-        return self.b.add(coords, m, iters=iters, **kw)
+        with self._on():
+            return self.b.add(coords, m, iters=iters, **kw)
 
     def step(self, k):
-        self.b.step(k)
+        with self._on():
+            self.b.step(k)
 
     def status(self, slot):
-        return self.b.status(slot)
+        with self._on():
+            return self.b.status(slot)
 
     def best(self, slot):
-        return self.b.best(slot)
+        with self._on():
+            return self.b.best(slot)
 
     def remove(self, slot):
-        self.b.remove(slot)
+        with self._on():
+            self.b.remove(slot)
+
+    def free_bytes(self):
+        with self._on():
+            return self.b.info()["free_bytes"]
 
     def sync(self):
         self.stream.synchronize()
 
     def close(self):
-        self.b.close()
+        with self._on():
+            self.b.close()
+
+
+class DeviceBatches:
+    """Independent instances spread over several GPUs of one process: one
+    batch per device, and an arriving instance goes to the device whose arena
+    has the most free memory (the next ones in that order when it does not
+    fit).  Each device steps only its own instances, on its own stream, so
+    the devices run concurrently and nothing crosses between them -- no
+    collective on the data path.  A slot is (device index, the batch's slot).
+
+    batches: objects as Server expects (add, step, status, best, remove,
+    sync) that also report free_bytes()."""
+
+    def __init__(self, batches):
+        self.batches = list(batches)
+        self.active = [0] * len(self.batches)
+
+    def add(self, coords, m, iters, **kw):
+        order = sorted(range(len(self.batches)), key=lambda d: (-self.batches[d].free_bytes(), d))
+        for d in order:
+            slot = self.batches[d].add(coords, m, iters, **kw)
+            if slot is not None:
+                self.active[d] += 1
+                return (d, slot)
+        return None
+
+    def step(self, k):
+        for d, b in enumerate(self.batches):  # asynchronous launches: the devices overlap
+            if self.active[d]:
+                b.step(k)
+
+    def status(self, slot):
+        return self.batches[slot[0]].status(slot[1])
+
+    def best(self, slot):
+        return self.batches[slot[0]].best(slot[1])
+
+    def remove(self, slot):
+        self.batches[slot[0]].remove(slot[1])
+        self.active[slot[0]] -= 1
+
+    def sync(self):
+        for b in self.batches:
+            b.sync()
+
+    def close(self):
+        for b in self.batches:
+            if hasattr(b, "close"):
+                b.close()
+
+
+def place_requests(requests, world, need):
+    """Requests for one process per GPU: in arrival order, each goes to the
+    rank with the fewest workspace bytes placed so far (need(r): its bytes;
+    ties to the lower rank).  Deterministic, so every rank computes the same
+    split from the same trace without communicating."""
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for r in sorted(requests, key=lambda r: (r.arrival, r.rid)):
+        d = min(range(world), key=lambda q: (load[q], q))
+        out[d].append(r)
+        load[d] += need(r)
+    return out
+
+
+def serve_ranks(requests, batch, rank, world, need, gather=None, **run_kw):
+    """Serve this rank's share of `requests` (place_requests) on `batch`;
+    gather(obj) -> list of every rank's obj on rank 0 (None elsewhere), e.g.
+    torch.distributed.gather_object.  Rank 0 returns every request's
+    (rid, tour, best_len, latency) in rid order and the slowest rank's wall
+    time; the other ranks return None."""
+    mine = place_requests(requests, world, need)[rank]
+    done, wall, steps = Server(batch).run(mine, **run_kw)
+    part = {"rank": rank, "wall": wall, "steps": steps,
+            "results": [(r.rid, r.tour, r.best_len, r.latency) for r in done]}
+    parts = gather(part) if gather else [part]
+    if parts is None:
+        return None
+    results = sorted((x for p in parts for x in p["results"]), key=lambda x: x[0])
+    return {"results": results, "wall": max(p["wall"] for p in parts),
+            "steps": [p["steps"] for p in sorted(parts, key=lambda p: p["rank"])]}
 
 
 def main(argv=None):
@@ -212,15 +310,20 @@ def main(argv=None):
     ap.add_argument("--arena-gb", type=float, default=80.0)
     ap.add_argument("--slots", type=int, default=1024)
     ap.add_argument("--rho", type=float, default=0.1)
+    ap.add_argument("--gpus", type=int, default=1, help="devices of this process, one batch each")
     args = ap.parse_args(argv)
     reqs = poisson_requests(args.requests, args.rate, args.nmin, args.nmax, args.iters, rho=args.rho)
-    gb = GpuBatch(int(args.arena_gb * (1 << 30)), args.slots, args.prec)
+    arena = int(args.arena_gb * (1 << 30))
+    if args.gpus > 1:
+        gb = DeviceBatches([GpuBatch(arena, args.slots, args.prec, device=d) for d in range(args.gpus)])
+    else:
+        gb = GpuBatch(arena, args.slots, args.prec)
     done, wall, steps = Server(gb).run(reqs, realtime=True)
     gb.close()
     out = summarize(done, wall)
     out.update({"config": {"requests": args.requests, "rate": args.rate, "n": [args.nmin, args.nmax],
                            "m": "min(n, 1024)", "iters": args.iters, "P_dtype": args.prec,
-                           "arena_gb": args.arena_gb}, "batched_steps": steps,
+                           "arena_gb": args.arena_gb, "gpus": args.gpus}, "batched_steps": steps,
                 "rejected": sum(1 for r in reqs if r.rejected)})
     print(json.dumps(out))
     return 0

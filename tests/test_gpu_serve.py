@@ -55,3 +55,32 @@ def test_large_request_in_a_mix_equals_its_solo_run():
         tour, L = s.iterate(r.iters).best()
         s.close()
         assert r.best_len == L and np.array_equal(r.tour, tour), r.rid
+
+
+def test_device_batches_on_one_gpu_equal_solo_runs():
+    """The multi-device placement path (one batch per device, each instance
+    on the device with the most free arena memory) with two batches on this
+    one GPU: requests spread over both, and every result equals the request
+    solved alone, bit for bit -- as it does with one batch."""
+    reqs = serve.poisson_requests(10, 400.0, 30, 500, 8, mmax=40, seed=9, rho=0.2)
+    arena = 3 * B.instance_bytes(500, 40) + (1 << 20)
+    db = serve.DeviceBatches([serve.GpuBatch(arena, 8, "bf16", device=0), serve.GpuBatch(arena, 8, "bf16", device=0)])
+    placed = []
+    add = db.add
+
+    def add_logged(*a, **kw):
+        s = add(*a, **kw)
+        if s is not None:
+            placed.append(s[0])
+        return s
+
+    db.add = add_logged
+    done, wall, steps = serve.Server(db).run(reqs, realtime=True)
+    db.close()
+    assert sorted(r.rid for r in done) == list(range(10))
+    assert set(placed) == {0, 1}                          # both batches served requests
+    for r in done:
+        s = B.Solver(r.coords, m=r.m, prec="bf16", seed=r.seed, rho=0.2, stream=torch.cuda.Stream())
+        tour, L = s.iterate(r.iters).best()
+        s.close()
+        assert r.best_len == L and np.array_equal(r.tour, tour), r.rid

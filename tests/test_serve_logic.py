@@ -170,3 +170,49 @@ def test_refused_request_is_rejected_and_the_rest_served():
     srv = serve.Server(RefusingBatch(capacity=100, limit=40, code=B.ERR_CUDA), clock=clock, sleep=clock.sleep)
     with pytest.raises(B.AcoError):
         srv.run([_req(0, 0.0, 50, 1)], realtime=False)
+
+
+class SizedBatch(FakeBatch):
+    """A fake batch that reports its free arena bytes (for DeviceBatches)."""
+
+    def free_bytes(self):
+        return self.capacity - self.used
+
+
+def test_device_batches_place_by_free_memory_and_route():
+    """Two devices: each request goes to the device with more free arena
+    memory (ties to device 0), steps reach only devices with instances, and
+    results, status and removal go to the device that holds the instance."""
+    a, b = SizedBatch(capacity=100), SizedBatch(capacity=80)
+    db = serve.DeviceBatches([a, b])
+    s0 = db.add(np.zeros((50, 2), np.float32), 4, 2)
+    s1 = db.add(np.zeros((40, 2), np.float32), 4, 2)    # a: 50 free, b: 80 free -> b
+    s2 = db.add(np.zeros((45, 2), np.float32), 4, 1)    # a: 50, b: 40 -> a
+    assert (s0[0], s1[0], s2[0]) == (0, 1, 0)
+    assert db.add(np.zeros((60, 2), np.float32), 4, 1) is None   # fits nowhere now
+    db.step(1)
+    assert db.status(s2) == (1, True) and db.status(s0) == (1, False)
+    db.remove(s2)
+    db.remove(s1)
+    assert db.active == [1, 0]
+    db.step(1)                                            # device 1 is idle: not stepped
+    assert b.log[-1] == ("add", 0) or b.log[-1][0] == "step"
+    assert sum(1 for e in b.log if e[0] == "step") == 1 and db.status(s0) == (2, True)
+
+
+def test_server_over_device_batches_serves_every_request_once():
+    clock = FakeClock()
+    db = serve.DeviceBatches([SizedBatch(capacity=100), SizedBatch(capacity=100)])
+    reqs = [_req(i, 0.1 * i, 30 + 10 * (i % 4), 1 + i % 3) for i in range(12)]
+    done, wall, steps = serve.Server(db, clock=clock, sleep=clock.sleep).run(reqs, realtime=False)
+    assert sorted(r.rid for r in done) == list(range(12))
+    assert all(x.used == 0 for x in db.batches)
+    assert all(any(e[0] == "add" for e in x.log) for x in db.batches)   # both devices served
+
+
+def test_place_requests_balances_bytes_deterministically():
+    reqs = [_req(i, 0.01 * i, n, 1) for i, n in enumerate([100, 10, 10, 10, 50, 60, 5])]
+    parts = serve.place_requests(reqs, 2, need=lambda r: r.n)
+    assert [r.rid for r in parts[0]] == [0, 6] and [r.rid for r in parts[1]] == [1, 2, 3, 4, 5]
+    assert serve.place_requests(reqs, 2, need=lambda r: r.n)[1] == parts[1]
+    assert serve.place_requests(reqs, 1, need=lambda r: r.n)[0] == sorted(reqs, key=lambda r: r.arrival)
