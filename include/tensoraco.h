@@ -329,6 +329,18 @@ int aco_op_construct_shape(const void* P_dev, int prec, int n, int ld, int m, ui
 int aco_op_build_lists(const void* P_dev, int prec, int n, int ld, void* lists_dev, int* lcnt_dev,
                        uint32_t* lkey_dev, void* stream);
 
+/* aco_op_build_P and aco_op_build_lists in one pass (the solvers' and
+ * batches' form): the same M_p, lists, counts and bounds.  lkey_dev also
+ * serves as input: each row's previous bound, scaled by the evaporation
+ * (1 - rho)^alpha, is the threshold above which the pass collects candidates;
+ * when that collects between ACO_LIST_TARGET and ACO_LIST_MAX columns the
+ * list is sorted from them, otherwise it is selected from the whole row as
+ * aco_op_build_lists does.  Any lkey_dev contents give the same results; only
+ * the time depends on them.  tau_dev fp32. */
+int aco_op_build_P_lists(const float* tau_dev, const float* H_dev, int n, int ld, int alpha, float inv_gamma,
+                         float rho, int prec, void* P_dev, void* lists_dev, int* lcnt_dev, uint32_t* lkey_dev,
+                         void* stream);
+
 /* Sec. 2.4 roulette wheel (ACO_RW above) for all m ants on M_p; n <= 16384
  * (ACO_ERR_UNSUPPORTED beyond).  Arguments as for aco_op_construct. */
 int aco_op_construct_rw(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,

@@ -76,6 +76,7 @@ _SIGS = {
     "aco_solver_set_shape": (i32, [v, i32, i32, i32]),
     "aco_solver_set_wait_polls": (i32, [v, u32]),
     "aco_op_construct_probe": (i32, [v, i32, i32, i32, i32, u64, u32, v, v, v, v, i32, v, v]),
+    "aco_op_build_P_lists": (i32, [v, v, i32, i32, i32, f32, f32, i32, v, v, v, v, v]),
     "aco_ceiling_row_reads": (i32, [v, sz, i32, i32, i32, u32, v, v]),
     "aco_ceiling_philox": (i32, [u64, i32, i32, u32, v, v]),
     "aco_ceiling_chase": (i32, [v, sz, i32, i32, v, v, v]),
@@ -200,6 +201,12 @@ def _check_lists(n, lists, lcnt, lkey):
 def op_build_lists(P, prec, n, ld, lists, lcnt, lkey, stream=None):
     _check_lists(n, lists, lcnt, lkey)
     call("aco_op_build_lists", ptr(P), prec, n, ld, ptr(lists), ptr(lcnt), ptr(lkey), stream_ptr(stream))
+
+
+def op_build_P_lists(tau, H, n, ld, alpha, inv_gamma, rho, prec, P, lists, lcnt, lkey, stream=None):
+    _check_lists(n, lists, lcnt, lkey)
+    call("aco_op_build_P_lists", ptr(tau), ptr(H), n, ld, alpha, inv_gamma, rho, prec, ptr(P), ptr(lists),
+         ptr(lcnt), ptr(lkey), stream_ptr(stream))
 
 
 def op_construct_rw(P, prec, n, ld, m, seed, it, tours, err=None, stream=None):

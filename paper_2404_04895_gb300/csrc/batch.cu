@@ -1,7 +1,7 @@
 // Batches: many independent TSP instances advanced together.
 //
 // Every step of an iteration is one launch over all active instances:
-//   build_P      one CTA per (instance, row)
+//   build_P      one CTA per (instance, row): M_p and its candidate list in one pass
 //   construct    one persistent launch; CTAs pull (instance, ant) items from a
 //                global counter, biggest instances first
 //   tour_length  one warp per (instance, ant)
@@ -27,42 +27,44 @@
 namespace aco {
 
 // ------------------------------------------------------------------ kernels
+// M_p and (for instances with lists) the candidate list of one row per CTA,
+// in one pass (build_P_lists_row); the list threshold is guessed from the
+// row's previous bound as in the single-instance kernel.
 template <int PREC>
-__global__ void __launch_bounds__(256) batch_build_P_kernel(const InstDev* __restrict__ insts,
-                                                            const int* __restrict__ row_off,
-                                                            int count) {
+__global__ void __launch_bounds__(256) batch_build_P_lists_kernel(const InstDev* __restrict__ insts,
+                                                                  const int* __restrict__ row_off, int count) {
+  __shared__ uint32_t scratch[kListScratchWords];
   __shared__ float red[32];
   const int r = blockIdx.x;
   const int i = find_instance(row_off, count, r);
   const InstDev& I = insts[i];
   const int row = r - __ldg(row_off + i);
-  float inv_gamma = 1.0f;
+  float inv_gamma = 1.0f, ig_prev = 1.0f;
   if (I.adair) {
     const uint32_t it = *I.it;
-    inv_gamma = I.sched[it < (uint32_t)I.n_sched ? it : (uint32_t)(I.n_sched - 1)];
+    const uint32_t last = (uint32_t)(I.n_sched - 1);
+    inv_gamma = I.sched[it < last ? it : last];
+    ig_prev = it > 0u ? I.sched[it - 1u < last ? it - 1u : last] : 0.0f;
   }
   const size_t eb = PREC == ACO_FP32 ? 4 : 2;
   void* P_row = static_cast<char*>(I.P) + (size_t)row * I.ld * eb;
   const char* tau_row = reinterpret_cast<const char*>(I.tau) + (size_t)row * I.ld * (I.tau_bf16 ? 2 : 4);
+  const float* H_row = I.H + (size_t)row * I.ld;
+  if (!I.lists) {
+    if (I.tau_bf16)
+      build_P_row<PREC, true>(tau_row, H_row, I.n, I.ld, row, I.alpha, inv_gamma, P_row, red);
+    else
+      build_P_row<PREC, false>(tau_row, H_row, I.n, I.ld, row, I.alpha, inv_gamma, P_row, red);
+    return;
+  }
+  const uint32_t guess = list_guess(I.lkey[row], 1.0f - I.rho, I.alpha, inv_gamma, ig_prev);
+  uint2* list = I.lists + (size_t)row * kListMax;
   if (I.tau_bf16)
-    build_P_row<PREC, true>(tau_row, I.H + (size_t)row * I.ld, I.n, I.ld, row, I.alpha, inv_gamma, P_row, red);
+    build_P_lists_row<PREC, true>(tau_row, H_row, I.n, I.ld, row, I.alpha, inv_gamma, P_row, list, I.lcnt + row,
+                                  I.lkey + row, guess, scratch, red);
   else
-    build_P_row<PREC, false>(tau_row, I.H + (size_t)row * I.ld, I.n, I.ld, row, I.alpha, inv_gamma, P_row, red);
-}
-
-template <int PREC>
-__global__ void __launch_bounds__(256) batch_build_lists_kernel(const InstDev* __restrict__ insts,
-                                                                const int* __restrict__ row_off,
-                                                                int count) {
-  __shared__ uint32_t scratch[kListScratchWords];
-  const int r = blockIdx.x;
-  const int i = find_instance(row_off, count, r);
-  const InstDev& I = insts[i];
-  if (!I.lists) return;
-  const int row = r - __ldg(row_off + i);
-  const size_t eb = PREC == ACO_FP32 ? 4 : 2;
-  build_list_row<PREC>(static_cast<const char*>(I.P) + (size_t)row * I.ld * eb, I.n,
-                       I.lists + (size_t)row * kListMax, I.lcnt + row, I.lkey + row, scratch);
+    build_P_lists_row<PREC, false>(tau_row, H_row, I.n, I.ld, row, I.alpha, inv_gamma, P_row, list, I.lcnt + row,
+                                   I.lkey + row, guess, scratch, red);
 }
 
 __global__ void __launch_bounds__(256) batch_tour_length_kernel(const InstDev* __restrict__ insts,
@@ -346,26 +348,15 @@ static int batch_enqueue(aco_batch* b) {
   cudaStream_t st = b->stream;
   switch (b->prec) {
     case ACO_FP32:
-      batch_build_P_kernel<ACO_FP32><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
+      batch_build_P_lists_kernel<ACO_FP32><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
       break;
     case ACO_BF16:
-      batch_build_P_kernel<ACO_BF16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
+      batch_build_P_lists_kernel<ACO_BF16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
       break;
     default:
-      batch_build_P_kernel<ACO_FP16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
+      batch_build_P_lists_kernel<ACO_FP16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
   }
-  ACO_CHECK_LAUNCH("batch_build_P_kernel");
-  switch (b->prec) {
-    case ACO_FP32:
-      batch_build_lists_kernel<ACO_FP32><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
-      break;
-    case ACO_BF16:
-      batch_build_lists_kernel<ACO_BF16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
-      break;
-    default:
-      batch_build_lists_kernel<ACO_FP16><<<b->total_rows, 256, 0, st>>>(b->d_insts, b->d_row_off, cnt);
-  }
-  ACO_CHECK_LAUNCH("batch_build_lists_kernel");
+  ACO_CHECK_LAUNCH("batch_build_P_lists_kernel");
   ACO_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int) * std::max<size_t>(1, b->classes.size()), st));
   if (b->rw_count) {  // one CTA per roulette-wheel ant
     const int rc = launch_batch_construct_rw(b->d_rw_insts, b->d_rw_off, b->rw_count, b->rw_ants, b->d_err,

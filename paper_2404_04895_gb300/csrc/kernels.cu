@@ -83,6 +83,33 @@ __global__ void __launch_bounds__(256) build_lists_kernel(const void* __restrict
                        lists + (size_t)i * kListMax, lcnt + i, lkey + i, scratch);
 }
 
+// Eq. 1 and the candidate list of row i in one pass; the list's collection
+// threshold comes from the row's previous bound (lkey, rewritten here) and
+// the evaporation keep^alpha, AdaIR's exponent from the schedule.
+template <int PREC, bool TB>
+__global__ void __launch_bounds__(256) build_P_lists_kernel(const void* __restrict__ tau, const float* __restrict__ H,
+                                                            int n, int ld, int alpha, float inv_gamma_arg,
+                                                            const float* __restrict__ inv_gamma_dev,
+                                                            const uint32_t* __restrict__ it_dev, int n_sched,
+                                                            float keep, void* __restrict__ Pv, uint2* __restrict__ lists,
+                                                            int* __restrict__ lcnt, uint32_t* __restrict__ lkey) {
+  __shared__ uint32_t scratch[kListScratchWords];
+  __shared__ float red[32];
+  const int i = blockIdx.x;
+  float inv_gamma = inv_gamma_arg, ig_prev = inv_gamma_arg;
+  if (inv_gamma_dev) {
+    const uint32_t it = *it_dev;
+    const uint32_t last = (uint32_t)(n_sched - 1);
+    inv_gamma = inv_gamma_dev[it < last ? it : last];
+    ig_prev = it > 0u ? inv_gamma_dev[it - 1u < last ? it - 1u : last] : 0.0f;
+  }
+  const uint32_t guess = list_guess(lkey[i], keep, alpha, inv_gamma, ig_prev);
+  const size_t eb = PREC == ACO_FP32 ? 4 : 2;
+  build_P_lists_row<PREC, TB>(static_cast<const char*>(tau) + (size_t)i * ld * (TB ? 2 : 4), H + (size_t)i * ld, n, ld,
+                              i, alpha, inv_gamma, static_cast<char*>(Pv) + (size_t)i * ld * eb,
+                              lists + (size_t)i * kListMax, lcnt + i, lkey + i, guess, scratch, red);
+}
+
 // One CTA of W warps per ant (W = 1: 8 ants per CTA, one warp each).
 template <int W>
 __global__ void __launch_bounds__(256) tour_length_kernel(const double* __restrict__ D, int n,
@@ -243,6 +270,37 @@ int launch_build_P(const void* tau, int tau_prec, const float* H, int n, int ld,
   }
 #undef ACO_BUILD_P
   return check_launch("build_P_kernel");
+}
+
+int launch_build_P_lists(const void* tau, int tau_prec, const float* H, int n, int ld, int alpha, float inv_gamma,
+                         const float* inv_gamma_dev, const uint32_t* it_dev, int n_sched, float rho, int prec, void* P,
+                         uint2* lists, int* lcnt, uint32_t* lkey, cudaStream_t st) {
+  const bool tb = tau_prec == ACO_BF16;
+  const float keep = 1.0f - rho;
+#define ACO_BUILD_PL(PR)                                                                                            \
+  do {                                                                                                              \
+    if (tb)                                                                                                         \
+      build_P_lists_kernel<PR, true><<<n, 256, 0, st>>>(tau, H, n, ld, alpha, inv_gamma, inv_gamma_dev, it_dev,     \
+                                                        n_sched, keep, P, lists, lcnt, lkey);                       \
+    else                                                                                                            \
+      build_P_lists_kernel<PR, false><<<n, 256, 0, st>>>(tau, H, n, ld, alpha, inv_gamma, inv_gamma_dev, it_dev,    \
+                                                         n_sched, keep, P, lists, lcnt, lkey);                      \
+  } while (0)
+  switch (prec) {
+    case ACO_FP32:
+      ACO_BUILD_PL(ACO_FP32);
+      break;
+    case ACO_BF16:
+      ACO_BUILD_PL(ACO_BF16);
+      break;
+    case ACO_FP16:
+      ACO_BUILD_PL(ACO_FP16);
+      break;
+    default:
+      return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  }
+#undef ACO_BUILD_PL
+  return check_launch("build_P_lists_kernel");
 }
 
 int launch_build_lists(const void* P, int prec, int n, int ld, uint2* lists, int* lcnt,

@@ -377,15 +377,17 @@ static int enqueue_iteration(aco_solver* s) {
     if (s->profiling) cudaEventRecordWithFlags(s->ev[q], st, cudaEventRecordExternal);
   };
   probe(0);
-  int rc = launch_build_P(s->tau, p.tau_prec, s->H, n, s->ld, p.alpha, 1.0f,
-                          p.roulette == ACO_ADAIR ? s->sched : nullptr, s->it_dev, n_sched, p.prec,
-                          s->P_f, st);
-  if (rc) return rc;
-  probe(1);
   const bool rw = p.roulette == ACO_RW;
   const bool lists = p.cand_lists != 0 && !rw;
-  if (lists) rc = launch_build_lists(s->P_f, p.prec, n, s->ld, s->lists, s->lcnt, s->lkey, st);
+  const float* sched = p.roulette == ACO_ADAIR ? s->sched : nullptr;
+  // with lists: M_p and its lists in one pass (the probe between them then
+  // gives the list step 0 ms)
+  int rc = lists ? launch_build_P_lists(s->tau, p.tau_prec, s->H, n, s->ld, p.alpha, 1.0f, sched, s->it_dev, n_sched,
+                                        p.rho, p.prec, s->P_f, s->lists, s->lcnt, s->lkey, st)
+                 : launch_build_P(s->tau, p.tau_prec, s->H, n, s->ld, p.alpha, 1.0f, sched, s->it_dev, n_sched, p.prec,
+                                  s->P_f, st);
   if (rc) return rc;
+  probe(1);
   probe(2);
   const uint2 key = make_uint2((uint32_t)p.seed, (uint32_t)(p.seed >> 32));
   if (rw)
@@ -1100,6 +1102,23 @@ int aco_op_build_lists(const void* P_dev, int prec, int n, int ld, void* lists_d
   if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
   return launch_build_lists(P_dev, prec, n, ld, static_cast<uint2*>(lists_dev), lcnt_dev, lkey_dev,
                             static_cast<cudaStream_t>(stream));
+}
+
+int aco_op_build_P_lists(const float* tau_dev, const float* H_dev, int n, int ld, int alpha, float inv_gamma,
+                         float rho, int prec, void* P_dev, void* lists_dev, int* lcnt_dev, uint32_t* lkey_dev,
+                         void* stream) {
+  int rc = check_mat(tau_dev, n, ld, "tau");
+  if (!rc) rc = check_mat(H_dev, n, ld, "H");
+  if (!rc) rc = check_mat(P_dev, n, ld, "P");
+  if (rc) return rc;
+  if (!lists_dev || !lcnt_dev || !lkey_dev) return set_error(ACO_ERR_ARG, "NULL argument");
+  if (((uintptr_t)lists_dev & 7) != 0) return set_error(ACO_ERR_ARG, "lists must be 8-byte aligned");
+  if (prec < ACO_FP32 || prec > ACO_FP16) return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  if (alpha < 0 || alpha > 8) return set_error(ACO_ERR_UNSUPPORTED, "alpha must be an integer in [0, 8]");
+  if (!(rho >= 0.0f && rho <= 1.0f)) return set_error(ACO_ERR_ARG, "rho outside [0, 1]");
+  return launch_build_P_lists(tau_dev, ACO_FP32, H_dev, n, ld, alpha, inv_gamma, nullptr, nullptr, 1, rho, prec,
+                              P_dev, static_cast<uint2*>(lists_dev), lcnt_dev, lkey_dev,
+                              static_cast<cudaStream_t>(stream));
 }
 
 int aco_op_construct_ex(const void* P_dev, int prec, int n, int ld, int m, uint64_t seed, uint32_t it,

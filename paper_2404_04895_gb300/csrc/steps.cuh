@@ -626,21 +626,25 @@ constexpr int kListMax = ACO_LIST_MAX;
 constexpr int kListScratchWords = 256 + 8 + 2 * kListMax * 2;
 constexpr uint32_t kListPad = 0xFFFFFFFFu;  // column of the slots past the count
 
-template <int PREC>
+// COH: the row was written by the same kernel (read through the L2 with
+// ordinary loads, not the read-only path)
+template <int PREC, bool COH = false>
 __device__ __forceinline__ uint32_t p_key(const void* __restrict__ row, int j) {
-  if (PREC == ACO_FP32) return __ldg(static_cast<const uint32_t*>(row) + j);
-  const uint32_t h = __ldg(static_cast<const unsigned short*>(row) + j);
+  if (PREC == ACO_FP32)
+    return COH ? __ldcg(static_cast<const uint32_t*>(row) + j) : __ldg(static_cast<const uint32_t*>(row) + j);
+  const uint32_t h = COH ? __ldcg(static_cast<const unsigned short*>(row) + j)
+                         : __ldg(static_cast<const unsigned short*>(row) + j);
   if (PREC == ACO_BF16) return h << 16;
   return __float_as_uint(__half2float(__ushort_as_half((unsigned short)h)));
 }
 
 // Keys (fp32 bit patterns) of the KV columns of 16-byte chunk q of a row.
-template <int PREC>
+template <int PREC, bool COH = false>
 struct RowKeys {
   static constexpr int KV = PREC == ACO_FP32 ? 4 : 8;
   uint32_t k[KV];
   __device__ __forceinline__ void load(const void* __restrict__ row, int q) {
-    const uint4 d = __ldg(static_cast<const uint4*>(row) + q);
+    const uint4 d = COH ? __ldcg(static_cast<const uint4*>(row) + q) : __ldg(static_cast<const uint4*>(row) + q);
     if (PREC == ACO_FP32) {
       k[0] = d.x;
       k[1] = d.y;
@@ -688,12 +692,12 @@ __device__ __forceinline__ unsigned long long list_sort_key(uint32_t key, int j)
   return ((unsigned long long)key << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)j);
 }
 
-template <int PREC>
+template <int PREC, bool COH = false>
 __device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, int n,
                                                uint2* __restrict__ list, int* __restrict__ cnt_out,
                                                uint32_t* __restrict__ bkey_out,
                                                uint32_t* scratch) {
-  using RK = RowKeys<PREC>;
+  using RK = RowKeys<PREC, COH>;
   constexpr int KV = RK::KV;
   uint32_t* hist = scratch;                 // [256]
   uint32_t* sh = scratch + 256;             // [0] prefix [1] need [2] above [3] count [4] eq
@@ -704,7 +708,7 @@ __device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, i
 
   if (n <= kListMax) {  // every column listed, bound 0
     while (S < n) S <<= 1;
-    for (int q = tid; q < S; q += nt) sk[q] = q < n ? list_sort_key(p_key<PREC>(P_row, q), q) : 0ull;
+    for (int q = tid; q < S; q += nt) sk[q] = q < n ? list_sort_key(p_key<PREC, COH>(P_row, q), q) : 0ull;
     if (tid == 0) {
       *cnt_out = n;
       *bkey_out = 0u;
@@ -788,7 +792,7 @@ __device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, i
       const int span = (n + nt - 1) / nt;
       const int j0 = tid * span, j1 = min(n, j0 + span);
       uint32_t my_eq = 0u;
-      for (int j = j0; j < j1; ++j) my_eq += p_key<PREC>(P_row, j) == T;
+      for (int j = j0; j < j1; ++j) my_eq += p_key<PREC, COH>(P_row, j) == T;
       uint32_t inc = my_eq;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
@@ -801,7 +805,7 @@ __device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, i
       uint32_t rank = inc - my_eq;
       for (int w = 0; w < wid; ++w) rank += hist[w];
       for (int j = j0; j < j1 && rank < eq_take; ++j)
-        if (p_key<PREC>(P_row, j) == T) sk[n_gt + rank++] = list_sort_key(T, j);
+        if (p_key<PREC, COH>(P_row, j) == T) sk[n_gt + rank++] = list_sort_key(T, j);
     }
     while (S < cnt) S <<= 1;
     __syncthreads();
@@ -819,6 +823,149 @@ __device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, i
     list[q] = v ? make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v) : make_uint2(0u, kListPad);
   }
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 1 and the candidate list of the same row in one pass (solvers and
+// batches): the row of M_p is computed and stored exactly as build_P_row
+// does, and every column whose stored value's key reaches `guess` is
+// collected on the way (at most kListMax).  If between kListTarget and
+// kListMax columns reached it, they include every column whose key is >= T,
+// the kListTarget-th largest key (at least kListTarget keys are >= guess, so
+// T >= guess): sorted, they give T, and the list and bound of
+// build_list_row's definition -- every key >= T then fits, so nothing is
+// cut and the bound is T.  Any other count (a guess too high or too low, or
+// none) falls back to build_list_row's radix select on the stored row.  The
+// result is the same either way; the guess only decides the cost.
+// guess: 0xFFFFFFFF for none.  scratch: kListScratchWords shared words plus
+// `red` (32 floats) for the FP16 row maximum.
+// ---------------------------------------------------------------------------
+template <int PREC, bool TB = false>
+__device__ __forceinline__ void build_P_lists_row(const void* __restrict__ tau_row, const float* __restrict__ H_row,
+                                                  int n, int ld, int i, int alpha, float inv_gamma,
+                                                  void* __restrict__ P_row, uint2* __restrict__ list,
+                                                  int* __restrict__ cnt_out, uint32_t* __restrict__ bkey_out,
+                                                  uint32_t guess, uint32_t* scratch, float* red) {
+  const float4* h4 = reinterpret_cast<const float4*>(H_row);
+  const int nq = ld >> 2;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  uint32_t* sh = scratch + 256;
+  unsigned long long* sk = reinterpret_cast<unsigned long long*>(scratch + 256 + 8);
+  if (n <= kListMax) guess = 0u;  // every column is listed: collect them all
+  float scale = 1.0f;
+  if (PREC == ACO_FP16) {
+    float mx = 0.0f;
+    for (int q = tid; q < nq; q += nt) {
+      const float4 a = load_tau4<TB>(tau_row, q), b = __ldg(h4 + q);
+      const int j = 4 * q;
+      mx = fmaxf(mx, p_entry(a.x, b.x, i, j, n, alpha, inv_gamma));
+      mx = fmaxf(mx, p_entry(a.y, b.y, i, j + 1, n, alpha, inv_gamma));
+      mx = fmaxf(mx, p_entry(a.z, b.z, i, j + 2, n, alpha, inv_gamma));
+      mx = fmaxf(mx, p_entry(a.w, b.w, i, j + 3, n, alpha, inv_gamma));
+    }
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(ACO_FULL_MASK, mx, off));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+    for (int w = 1; w < (int)(nt >> 5); ++w) mx = fmaxf(mx, red[w]);
+    int e = 0;
+    if (mx > 0.0f) {
+      const int ef = (int)((__float_as_uint(mx) >> 23) & 0xFF);
+      e = (ef == 0 ? -127 : ef - 127) - 14;
+      e = e < -126 ? -126 : (e > 113 ? 113 : e);
+    }
+    scale = __uint_as_float((uint32_t)(127 - e) << 23);
+  }
+  if (tid == 0) sh[3] = 0u;
+  __syncthreads();
+  auto collect = [&](uint32_t key, int j) {
+    if (j < n && key >= guess) {
+      const uint32_t slot = atomicAdd(sh + 3, 1u);
+      if (slot < (uint32_t)kListMax) sk[slot] = list_sort_key(key, j);
+    }
+  };
+  for (int q = tid; q < nq; q += nt) {
+    const float4 a = load_tau4<TB>(tau_row, q), b = __ldg(h4 + q);
+    const int j = 4 * q;
+    const float x0 = p_entry(a.x, b.x, i, j, n, alpha, inv_gamma);
+    const float x1 = p_entry(a.y, b.y, i, j + 1, n, alpha, inv_gamma);
+    const float x2 = p_entry(a.z, b.z, i, j + 2, n, alpha, inv_gamma);
+    const float x3 = p_entry(a.w, b.w, i, j + 3, n, alpha, inv_gamma);
+    uint32_t k0, k1, k2, k3;
+    if (PREC == ACO_FP32) {
+      reinterpret_cast<float4*>(P_row)[q] = make_float4(x0, x1, x2, x3);
+      k0 = __float_as_uint(x0);
+      k1 = __float_as_uint(x1);
+      k2 = __float_as_uint(x2);
+      k3 = __float_as_uint(x3);
+    } else if (PREC == ACO_BF16) {
+      const uint32_t b0 = __bfloat16_as_ushort(__float2bfloat16_rn(x0)), b1 = __bfloat16_as_ushort(__float2bfloat16_rn(x1));
+      const uint32_t b2 = __bfloat16_as_ushort(__float2bfloat16_rn(x2)), b3 = __bfloat16_as_ushort(__float2bfloat16_rn(x3));
+      reinterpret_cast<uint2*>(P_row)[q] = make_uint2(b0 | (b1 << 16), b2 | (b3 << 16));
+      k0 = b0 << 16;
+      k1 = b1 << 16;
+      k2 = b2 << 16;
+      k3 = b3 << 16;
+    } else {
+      const __half h0 = __float2half_rn(__fmul_rn(x0, scale)), h1 = __float2half_rn(__fmul_rn(x1, scale));
+      const __half h2 = __float2half_rn(__fmul_rn(x2, scale)), h3 = __float2half_rn(__fmul_rn(x3, scale));
+      reinterpret_cast<uint2*>(P_row)[q] =
+          make_uint2((uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16),
+                     (uint32_t)__half_as_ushort(h2) | ((uint32_t)__half_as_ushort(h3) << 16));
+      k0 = __float_as_uint(__half2float(h0));
+      k1 = __float_as_uint(__half2float(h1));
+      k2 = __float_as_uint(__half2float(h2));
+      k3 = __float_as_uint(__half2float(h3));
+    }
+    collect(k0, j);
+    collect(k1, j + 1);
+    collect(k2, j + 2);
+    collect(k3, j + 3);
+  }
+  __syncthreads();
+  const uint32_t cnt = sh[3];
+  const bool all = n <= kListMax;
+  if (all || (cnt >= (uint32_t)kListTarget && cnt <= (uint32_t)kListMax)) {
+    int S = 2;
+    while (S < (int)cnt) S <<= 1;
+    for (int q = (int)cnt + tid; q < S; q += nt) sk[q] = 0ull;  // padding sorts last
+    __syncthreads();
+    bitonic_desc(sk, S);
+    // T and the number of collected keys >= T (all of them >= T when n <= kListMax)
+    const uint32_t T = all ? 0u : (uint32_t)(sk[kListTarget - 1] >> 32);
+    if (tid == 0) sh[5] = cnt;
+    __syncthreads();
+    for (int q = tid; q < (int)cnt; q += nt)
+      if ((uint32_t)(sk[q] >> 32) >= T && (q + 1 == (int)cnt || (uint32_t)(sk[q + 1] >> 32) < T)) sh[5] = (uint32_t)(q + 1);
+    __syncthreads();
+    const int take = (int)sh[5];
+    for (int q = tid; q < kListMax; q += nt) {
+      const unsigned long long v = q < take ? sk[q] : 0ull;
+      list[q] = q < take ? make_uint2((uint32_t)(v >> 32), 0xFFFFFFFFu - (uint32_t)v) : make_uint2(0u, kListPad);
+    }
+    if (tid == 0) {
+      *cnt_out = take;
+      *bkey_out = T;
+    }
+    __syncthreads();
+  } else {
+    __syncthreads();  // the row's stores are visible to the whole CTA
+    build_list_row<PREC, true>(P_row, n, list, cnt_out, bkey_out, scratch);
+  }
+}
+
+// The collection threshold for a row's list from its previous bound bkey_prev:
+// an entry's value changes by the evaporation keep^alpha (raised to AdaIR's
+// exponent), so the previous T scaled by that and by 0.95 usually leaves a
+// few hundred columns above it.  Any value gives the same list (see
+// build_P_lists_row); 0xFFFFFFFF (none) when there is no previous bound.
+__device__ __forceinline__ uint32_t list_guess(uint32_t bkey_prev, float keep, int alpha, float ig_now,
+                                               float ig_prev) {
+  if (bkey_prev == 0u || bkey_prev >= 0x7F800000u || !(keep > 0.0f) || !(ig_prev > 0.0f)) return 0xFFFFFFFFu;
+  const float lx = log2f(__uint_as_float(bkey_prev)) / ig_prev + (float)alpha * log2f(keep);
+  const float g = exp2f(ig_now * lx) * 0.95f;
+  if (!(g > 0.0f) || !(g < 3.0e38f)) return 0xFFFFFFFFu;
+  return __float_as_uint(g);
 }
 
 }  // namespace aco

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import P_device, covers, dev, host, shapes
+from gpu_util import P_device, covers, dev, host, padded_dev, shapes
 from paper_2404_04895_gb300 import binding as B
 from paper_2404_04895_gb300 import instances
 
@@ -151,3 +151,54 @@ def test_solver_with_and_without_lists(orc, lists):
     ref = orc.State(xy, **kw).run(15)
     assert np.array_equal(g.tours(), ref.last_tours)
     assert np.array_equal(g.tau(), ref.tau)
+
+
+def _fused_case(orc, n, seed, ties):
+    xy = instances.clustered(-(-n // 40), 40, 0.02, seed=seed)[:n] if n >= 80 else instances.uniform(n, seed)
+    H = orc.heuristic(orc.distances(xy), 2)
+    tau = np.random.default_rng(seed).uniform(0.3, 2.0, size=(n, n)).astype(np.float32)
+    if ties:
+        tau[:] = 1.0
+        H = np.where(H > np.median(H), np.float32(7.0), np.float32(3.0)).astype(np.float32)
+        np.fill_diagonal(H, 0)
+    return tau, H
+
+
+@pytest.mark.parametrize("prec", [B.FP32, B.BF16, B.FP16])
+@pytest.mark.parametrize("n,ties", [(40, False), (B.LIST_MAX, False), (B.LIST_MAX + 1, False), (900, True),
+                                    (2001, False), (5000, False)])
+def test_fused_build_equals_two_passes(orc, prec, n, ties):
+    """aco_op_build_P_lists (M_p and lists in one pass, the threshold guessed
+    from lkey) gives the M_p, lists, counts and bounds of aco_op_build_P +
+    aco_op_build_lists whatever lkey holds: the previous bounds (the fast
+    path), none, garbage, far too high or far too low (the fallback)."""
+    tau, H = _fused_case(orc, n, 11 + n, ties)
+    ld = B.ld_of(n)
+    taud, Hd = padded_dev(tau, ld, np.float32), padded_dev(H, ld, np.float32)
+    esz = torch.float32 if prec == B.FP32 else torch.int16
+    P2 = torch.zeros((n, ld), dtype=esz, device="cuda")
+    B.op_build_P(taud, Hd, n, ld, 1, 1.0, prec, P2)
+    l2, c2, k2 = _build(P2, prec, n, ld)
+    ref = (host(P2).view(np.uint8), host(l2), host(c2), host(k2))
+    kb = host(k2).view(np.uint32)
+    rng = np.random.default_rng(n)
+    guesses = {"previous": kb.copy(), "none": np.zeros(n, np.uint32),
+               "garbage": rng.integers(0, 2 ** 32, size=n, dtype=np.uint64).astype(np.uint32),
+               "high": np.full(n, 0x7F000000, np.uint32), "low": np.full(n, 0x00800000, np.uint32)}
+    for name, g in guesses.items():
+        P1 = torch.zeros((n, ld), dtype=esz, device="cuda")
+        l1 = torch.zeros((n, LMAX, 2), dtype=torch.int32, device="cuda")
+        c1 = torch.zeros(n, dtype=torch.int32, device="cuda")
+        k1 = dev(g.view(np.int32))
+        B.op_build_P_lists(taud, Hd, n, ld, 1, 1.0, 0.0, prec, P1, l1, c1, k1)
+        got = (host(P1).view(np.uint8), host(l1), host(c1), host(k1))
+        for a, b, what in zip(got, ref, ("M_p", "lists", "counts", "bounds")):
+            assert np.array_equal(a, b), (name, what)
+    if n >= 2000 and not ties:
+        # the previous bounds scaled by 0.95 put a few hundred columns above the
+        # threshold in most rows: the one-pass path is the one exercised
+        keys = host(P2).view(np.uint32) if prec == B.FP32 else None
+        if keys is not None:
+            g95 = (kb.view(np.float32) * np.float32(0.95)).view(np.uint32)
+            cnt = (keys[:, :n] >= g95[:, None]).sum(axis=1)
+            assert np.mean((cnt > 260) & (cnt < 500)) > 0.3
