@@ -384,7 +384,7 @@ int aco_op_deposit(float* tau_dev, int n, int ld, const int32_t* nbr_dev, const 
                    int m, float rho, int32_t* err_dev, void* stream);
 
 /* Selection frequencies of independent roulette on one row (the Bernoulli
- * trials of the paper's AdaIR visualisation, Sec. 4.3.1): for each of
+ * trials of the paper's AdaIR visualisation, Sec. 3.3.1): for each of
  * `trials` trials, r_j from Philox4x32-10 with key seed and counter
  * (j >> 2, tr mod 2^32, tr div 2^32, salt), word j & 3, mapped as in the
  * construction; the unvisited j maximising fl32(r_j * q_dev[j]) (lowest j on

@@ -255,7 +255,7 @@ void orc_construct_rw(const float* P_val, int n, uint64_t seed, uint32_t it, int
 }
 
 // Selection frequencies of independent roulette on one row (the Bernoulli
-// trials of the AdaIR visualisation, Sec. 4.3.1): trial tr draws r_j from
+// trials of the AdaIR visualisation, Sec. 3.3.1): trial tr draws r_j from
 // Philox counter (j >> 2, tr mod 2^32, tr div 2^32, salt), word j & 3, and
 // the unvisited j maximising fl32(r_j * q_j) (lowest j on ties) wins;
 // counts[j] += its wins.

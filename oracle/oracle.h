@@ -116,7 +116,7 @@ int32_t orc_select_rw(const float* row, const uint8_t* visited, int n, uint64_t 
 void orc_construct_rw(const float* P_val, int n, uint64_t seed, uint32_t it, int k_begin,
                       int k_end, int32_t* tours, int nthreads);
 
-/* Bernoulli trials of IR on one row q (Sec. 4.3.1): trial tr's deviates
+/* Bernoulli trials of IR on one row q (Sec. 3.3.1): trial tr's deviates
  * come from Philox counter (j>>2, tr lo, tr hi, salt); counts[j] += wins. */
 void orc_selection_counts(const float* q, const uint8_t* visited, int n, uint64_t trials,
                           uint64_t seed, uint32_t salt, uint64_t* counts);

@@ -1,4 +1,4 @@
-"""The AdaIR visualisation study (Sec. 4.3.1, Fig. 4 of the paper), on
+"""The AdaIR visualisation study (Sec. 3.3.1, Fig. 4 of the paper), on
 synthetic instances and on the GPU.
 
 Rows of the transition matrix M_p are sampled while a solver runs.  For the

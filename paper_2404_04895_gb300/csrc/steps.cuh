@@ -667,13 +667,14 @@ struct RowKeys {
 };
 
 // Bitonic sort, descending, of the first S (a power of two, <= 2 * blockDim.x)
-// 64-bit keys of sk; all threads of the CTA.
+// 64-bit keys of sk; all threads of the CTA.  Strides are powers of two, so
+// a thread's pair index is formed with masks and a shift (no division).
 __device__ __forceinline__ void bitonic_desc(unsigned long long* sk, int S) {
   const int tid = threadIdx.x;
   for (int size = 2; size <= S; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       if (tid < S / 2) {
-        const int i = 2 * stride * (tid / stride) + (tid % stride);
+        const int i = ((tid & ~(stride - 1)) << 1) | (tid & (stride - 1));  // 2*stride*(tid/stride) + tid%stride
         const int partner = i + stride;
         const bool desc = (i & size) == 0;
         const unsigned long long a = sk[i], b = sk[partner];

@@ -1,5 +1,5 @@
 // Selection frequencies of independent roulette on one row (the Bernoulli
-// trials of the paper's AdaIR visualisation, Sec. 4.3.1 / Fig. 4).
+// trials of the paper's AdaIR visualisation, Sec. 3.3.1 / Fig. 4).
 //
 // Trial tr draws r_j for every candidate j from Philox4x32-10 with counter
 // (j >> 2, tr mod 2^32, tr div 2^32, salt), word j & 3, r = ((x >> 8) | 1)

@@ -1,4 +1,4 @@
-"""The AdaIR visualisation study (Sec. 4.3.1, Fig. 4): the exact law of the
+"""The AdaIR visualisation study (Sec. 3.3.1, Fig. 4): the exact law of the
 row maximum under independent roulette, the GPU Bernoulli-trial kernel
 against the oracle and against that law, and an end-to-end run."""
 import numpy as np
