@@ -99,9 +99,9 @@ def peaks():
 
 KERNEL_SOURCES = {
     # the candidate-list construction kernel and what shapes its traffic (the lists)
-    "construct_lean_kernel": ("construct_lean.cuh", "construct.cuh", "common.cuh", "steps.cuh"),
+    "construct_lean_kernel": ("construct_lean.cuh", "construct.cuh", "common.cuh", "lists.cuh"),
     # the full-scan construction kernel
-    "construct_kernel": ("construct.cuh", "shapes.h", "common.cuh"),
+    "construct_kernel": ("construct.cuh", "shapes.h", "common.cuh", "lists.cuh"),
 }
 
 

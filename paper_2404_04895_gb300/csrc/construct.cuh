@@ -27,7 +27,7 @@
 
 #include "batch.cuh"
 #include "common.cuh"
-#include "steps.cuh"
+#include "lists.cuh"
 
 namespace aco {
 

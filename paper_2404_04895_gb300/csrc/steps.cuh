@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "exact.cuh"
 #include "exact_len.cuh"
+#include "lists.cuh"
 
 namespace aco {
 
@@ -621,10 +622,7 @@ namespace aco {
 // listed entry from its own slot.  All threads of the CTA (blockDim.x <= 256);
 // scratch: kListScratchWords shared words.
 // ---------------------------------------------------------------------------
-constexpr int kListTarget = ACO_LIST_TARGET;
-constexpr int kListMax = ACO_LIST_MAX;
 constexpr int kListScratchWords = 256 + 8 + 2 * kListMax * 2;
-constexpr uint32_t kListPad = 0xFFFFFFFFu;  // column of the slots past the count
 
 // COH: the row was written by the same kernel (read through the L2 with
 // ordinary loads, not the read-only path)
@@ -686,6 +684,57 @@ __device__ __forceinline__ void bitonic_desc(unsigned long long* sk, int S) {
       __syncthreads();
     }
   }
+}
+
+// The same network as bitonic_desc(sk, 512), for a CTA of exactly 256
+// threads and mostly in registers: thread t = 32w + l holds elements e =
+// 64w + 2l and e + 1, so a partner at distance 1 is the thread's other
+// element, one at distance 2..32 the same element of lane l ^ (d / 2) (a
+// shuffle), and only distances >= 64 (6 of the 45 stages) go through sk with
+// a barrier each.  Ends with sk sorted and a barrier.
+__device__ __forceinline__ void bitonic512_desc_cta(unsigned long long* sk) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int e0 = ((tid >> 5) << 6) | (lane << 1);
+  unsigned long long v0 = sk[e0], v1 = sk[e0 + 1];
+#pragma unroll
+  for (int size = 2; size <= 512; size <<= 1) {
+    const bool desc = (e0 & size) == 0;  // the same for e0 + 1 (size >= 2)
+    int stride = size >> 1;
+    if (stride >= 64) {
+      sk[e0] = v0;
+      sk[e0 + 1] = v1;
+      __syncthreads();
+#pragma unroll
+      for (; stride >= 64; stride >>= 1) {
+        const int i = ((tid & ~(stride - 1)) << 1) | (tid & (stride - 1));
+        const bool d = (i & size) == 0;
+        const unsigned long long a = sk[i], b = sk[i + stride];
+        if (d ? (a < b) : (a > b)) {
+          sk[i] = b;
+          sk[i + stride] = a;
+        }
+        __syncthreads();
+      }
+      v0 = sk[e0];  // each thread reloads (and later stores) only its own two
+      v1 = sk[e0 + 1];
+    }
+#pragma unroll
+    for (; stride >= 2; stride >>= 1) {
+      const int ld = stride >> 1;
+      const bool keep_max = ((lane & ld) == 0) == desc;  // lower element of a descending pair, or upper of an ascending
+      const unsigned long long o0 = __shfl_xor_sync(ACO_FULL_MASK, v0, ld);
+      const unsigned long long o1 = __shfl_xor_sync(ACO_FULL_MASK, v1, ld);
+      v0 = (keep_max == (v0 > o0)) ? v0 : o0;
+      v1 = (keep_max == (v1 > o1)) ? v1 : o1;
+    }
+    const bool gt = v0 > v1;
+    const unsigned long long hi = gt ? v0 : v1, lo = gt ? v1 : v0;
+    v0 = desc ? hi : lo;
+    v1 = desc ? lo : hi;
+  }
+  sk[e0] = v0;
+  sk[e0 + 1] = v1;
+  __syncthreads();
 }
 
 // composite sort key: value bits high, complemented column low (ties: lower column first)
@@ -931,7 +980,10 @@ __device__ __forceinline__ void build_P_lists_row(const void* __restrict__ tau_r
     while (S < (int)cnt) S <<= 1;
     for (int q = (int)cnt + tid; q < S; q += nt) sk[q] = 0ull;  // padding sorts last
     __syncthreads();
-    bitonic_desc(sk, S);
+    if (S == 512 && nt == 256)
+      bitonic512_desc_cta(sk);
+    else
+      bitonic_desc(sk, S);
     // T and the number of collected keys >= T (all of them >= T when n <= kListMax)
     const uint32_t T = all ? 0u : (uint32_t)(sk[kListTarget - 1] >> 32);
     if (tid == 0) sh[5] = cnt;
