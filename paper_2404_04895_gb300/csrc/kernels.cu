@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) build_lists_kernel(const void* __restrict
 // threshold comes from the row's previous bound (lkey, rewritten here) and
 // the evaporation keep^alpha, AdaIR's exponent from the schedule.
 template <int PREC, bool TB>
-__global__ void __launch_bounds__(256) build_P_lists_kernel(const void* __restrict__ tau, const float* __restrict__ H,
+__global__ void __launch_bounds__(256, 6) build_P_lists_kernel(const void* __restrict__ tau, const float* __restrict__ H,
                                                             int n, int ld, int alpha, float inv_gamma_arg,
                                                             const float* __restrict__ inv_gamma_dev,
                                                             const uint32_t* __restrict__ it_dev, int n_sched,
