@@ -16,25 +16,57 @@
 namespace aco {
 
 // ---------------------------------------------------------------------------
-// Sec. 2.1: D_ij = sqrt(dx^2 + dy^2) (fp64), H_ij = fl32((1/max(d,1e-9))^beta).
-// Grid: (ceil(ld/256), n); each thread one (i, j); coalesced row writes.
+// Sec. 2.1: D_ij = sqrt(dx^2 + dy^2) (fp64), H_ij = fl32((1/max(d,1e-9))^beta),
+// H_ii = 0, H zero in the padding columns n <= j < ld.  Both are symmetric
+// bit for bit: x_j - x_i is exactly -(x_i - x_j) (rounding to nearest is
+// symmetric) and squaring drops the sign.  So one CTA takes a 32 x 32 tile
+// (I, J) with I <= J, computes each entry once (1/d by the correctly rounded
+// reciprocal, the same value as a correctly rounded 1.0 / d), writes it
+// row-wise at (i, j) and, through shared memory, row-wise at (j, i).
+// Grid (T, T), T = ceil(n / 32); blocks with I > J return at once.
 // ---------------------------------------------------------------------------
-__global__ void heuristic_kernel(const float* __restrict__ xy, int n, int beta,
-                                 double* __restrict__ D, float* __restrict__ H, int ld) {
-  const int i = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ld) return;
-  if (j >= n) {
-    H[(size_t)i * ld + j] = 0.0f;
-    return;
+__global__ void __launch_bounds__(256) heuristic_kernel(const float* __restrict__ xy, int n, int beta,
+                                                        double* __restrict__ D, float* __restrict__ H, int ld) {
+  __shared__ double sd[32][33];
+  __shared__ float sh[32][33];
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (I > J) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int j = 32 * J + tx;
+  double xj = 0.0, yj = 0.0;
+  if (j < n) {
+    xj = (double)xy[2 * j];
+    yj = (double)xy[2 * j + 1];
   }
-  const double dx = __dsub_rn((double)xy[2 * i], (double)xy[2 * j]);
-  const double dy = __dsub_rn((double)xy[2 * i + 1], (double)xy[2 * j + 1]);
-  const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-  if (D) D[(size_t)i * n + j] = d;
-  float h = 0.0f;
-  if (i != j) h = __double2float_rn(powi_f64(__ddiv_rn(1.0, d > 1e-9 ? d : 1e-9), beta));
-  H[(size_t)i * ld + j] = h;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = ty + 8 * k, i = 32 * I + r;
+    double d = 0.0;
+    float h = 0.0f;
+    if (i < n && j < n) {
+      const double dx = __dsub_rn((double)xy[2 * i], xj);
+      const double dy = __dsub_rn((double)xy[2 * i + 1], yj);
+      d = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+      if (i != j) h = __double2float_rn(powi_f64(__drcp_rn(d > 1e-9 ? d : 1e-9), beta));
+      if (D) D[(size_t)i * n + j] = d;
+      H[(size_t)i * ld + j] = h;
+    }
+    sd[r][tx] = d;
+    sh[r][tx] = h;
+    if (J == (int)gridDim.x - 1 && i < n)  // this row's padding columns
+      for (int c = n + tx; c < ld; c += 32) H[(size_t)i * ld + c] = 0.0f;
+  }
+  if (I == J) return;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = ty + 8 * k;  // row 32J + r of the mirrored tile, column 32I + tx
+    const int jr = 32 * J + r, ic = 32 * I + tx;
+    if (jr < n && ic < n) {
+      if (D) D[(size_t)jr * n + ic] = sd[tx][r];
+      H[(size_t)jr * ld + ic] = sh[tx][r];
+    }
+  }
 }
 
 __global__ void fill_u16_kernel(unsigned short* __restrict__ a, size_t count, unsigned short v) {
@@ -221,7 +253,8 @@ static int check_launch(const char* what) {
 
 int launch_heuristic(const float* xy, int n, int beta, double* D, float* H, int ld,
                      cudaStream_t st) {
-  dim3 grid((ld + 255) / 256, n);
+  const int T = (n + 31) / 32;
+  dim3 grid(T, T);
   heuristic_kernel<<<grid, 256, 0, st>>>(xy, n, beta, D, H, ld);
   return check_launch("heuristic_kernel");
 }

@@ -51,13 +51,16 @@ def test_pow_own_bit_exact(orc):
         assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), e
 
 
-@pytest.mark.parametrize("n", [3, 50, 257])
+@pytest.mark.parametrize("n", [3, 50, 257, 1000])
 @pytest.mark.parametrize("beta", [0, 2, 5])
-def test_heuristic_bit_exact(orc, n, beta):
+@pytest.mark.parametrize("extra_ld", [0, 72])
+def test_heuristic_bit_exact(orc, n, beta, extra_ld):
+    """Every entry (both triangles, the diagonal, and the padding columns up
+    to a caller's ld beyond the last 32-column tile) against the oracle."""
     xy = instances.uniform(n, n)
     xy[n // 2] = xy[0]  # a coincident pair exercises the 1e-9 floor
-    ld = B.ld_of(n)
-    D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    ld = B.ld_of(n) + extra_ld
+    D = torch.full((n, n), np.nan, dtype=torch.float64, device="cuda")
     H = torch.full((n, ld), 7.0, dtype=torch.float32, device="cuda")
     B.op_heuristic(dev(xy), n, beta, D, H, ld)
     Dr = orc.distances(xy)
