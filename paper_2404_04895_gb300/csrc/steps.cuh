@@ -391,7 +391,8 @@ __device__ __forceinline__ int2 deposit_scale_block(const double* __restrict__ c
 //      one redux per chunk, and the group's leader adds the sums to the
 //      slot's carry-save words with shared 64-bit atomics (integer sums: any
 //      order gives the same bits)
-//   4. one coalesced pass over the row writes tau' or the rounded sum
+//   4. one thread per slot rounds tau' + its sum once (into a shared table),
+//      then one coalesced pass over the row writes tau' or the slot's result
 // At most `cap` slots are summed per pass; rows with more touched columns
 // take further passes (only their touched columns are rewritten).  With
 // weights the fixed point cannot hold (mode kDepBad: a weight negative or NaN,
@@ -409,7 +410,7 @@ __host__ __device__ inline int deposit_cap(int n, long long m) {
 
 __host__ __device__ inline size_t deposit_smem_bytes(int n, int cap) {
   const size_t nw = (size_t)(n + 31) / 32;
-  return (size_t)cap * 32 + nw * 8 + 33 * 4;
+  return (size_t)cap * 32 + nw * 8 + 33 * 4 + (size_t)cap * 8;
 }
 
 template <bool TB = false>
@@ -424,6 +425,8 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
   uint32_t* bm = reinterpret_cast<uint32_t*>(acc + (size_t)cap * 4);      // [nw]
   uint32_t* base = bm + nw;                                                // [nw]
   int* sc = reinterpret_cast<int*>(base + nw);                             // [33]
+  int* tcol = sc + 33;                                                     // [cap] column of each slot of a pass
+  uint32_t* res = reinterpret_cast<uint32_t*>(tcol + cap);                 // [cap] its rounded result
 
   // 1. touched columns
   for (int w = tid; w < nw; w += nthr) bm[w] = 0u;
@@ -530,8 +533,40 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
     }
     __syncthreads();
 
-    // 4. the row: tau' everywhere on the first pass, rounded sums on touched
-    //    entries; stored in fp32, or in bf16 (rounded once, to nearest even)
+    // 4a. each slot of this pass: its column (from the bitmap), then tau' +
+    //     the slot's sum rounded once, from the entry's stored value (not yet
+    //     rewritten: the row pass below and later passes leave it alone
+    //     until then); stored in fp32, or in bf16 (to nearest even)
+    if (used > 0 && mode != kDepBad) {
+      for (int q = 0; q < per; ++q) {
+        const int w = wb + q;
+        if (w >= nw) break;
+        uint32_t bits = bm[w];
+        int sl = (int)base[w] - s0;
+        while (bits) {
+          if (sl >= used) break;
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          if (sl >= 0) tcol[sl] = 32 * w + b;
+          ++sl;
+        }
+      }
+      __syncthreads();
+      for (int sl = tid; sl < used; sl += nthr) {
+        const int j = tcol[sl];
+        const float tp = __fmul_rn(keep, TB ? __uint_as_float((uint32_t)rowh[j] << 16) : row[j]);
+        const unsigned long long* a = acc + 4 * sl;
+        if (mode == kDepInf && a[3])
+          res[sl] = TB ? 0x7F80u : 0x7F800000u;
+        else
+          res[sl] = TB ? round_sum_bf16(tp, a[0], a[1], a[2], E0)
+                       : __float_as_uint(round_sum_f32(tp, a[0], a[1], a[2], E0));
+      }
+      __syncthreads();
+    }
+
+    // 4b. the row: tau' everywhere on the first pass, each touched entry's
+    //     result from its slot
     for (int q = tid; 4 * q < n; q += nthr) {
       const int j0 = 4 * q;
       const uint32_t nib = (bm[j0 >> 5] >> (j0 & 31)) & 0xFu;
@@ -572,12 +607,7 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
           write[i] = false;
           continue;
         }
-        const unsigned long long* a = acc + 4 * sl;
-        if (mode == kDepInf && a[3])
-          out[i] = TB ? 0x7F80u : 0x7F800000u;
-        else
-          out[i] = TB ? round_sum_bf16(tp, a[0], a[1], a[2], E0)
-                      : __float_as_uint(round_sum_f32(tp, a[0], a[1], a[2], E0));
+        out[i] = res[sl];
       }
       // entries not written in this pass keep their stored bits
       if (full && write[0] && write[1] && write[2] && write[3]) {
