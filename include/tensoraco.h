@@ -140,7 +140,10 @@ int aco_workspace_bytes(int n, int m, int prec, size_t* bytes);
 /* Give the next aco_init a caller-owned device workspace (e.g. a torch
  * tensor) of `bytes` >= aco_workspace_bytes(), 256-byte aligned, and the
  * stream all its work is issued on.  The caller keeps ownership and must keep
- * the memory alive until aco_free().  dev_workspace NULL unbinds. */
+ * the memory alive until aco_free().  dev_workspace NULL unbinds.  stream
+ * NULL: the library's own stream, created once per process with default
+ * flags (so ordered with the legacy default stream both ways), on which an
+ * iteration is replayed as one CUDA graph. */
 int aco_bind(void* dev_workspace, size_t bytes, void* stream);
 
 /* ======================================================================

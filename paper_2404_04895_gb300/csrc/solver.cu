@@ -912,6 +912,10 @@ static aco_solver* g_solver = nullptr;
 static void* g_ws = nullptr;
 static size_t g_ws_bytes = 0;
 static void* g_stream = nullptr;
+// The global solver's stream when none is bound: created on first use, kept
+// for the process.  A created stream (unlike the legacy default stream) can
+// be captured, so the global solver's iterations replay as one graph.
+static cudaStream_t g_own_stream = nullptr;
 static aco_params g_pending = [] {
   aco_params p;
   aco_params_default(&p);
@@ -941,7 +945,18 @@ int aco_init(const float* coords_host, int n, int m, float alpha, float beta, fl
     aco_destroy(g_solver);
     g_solver = nullptr;
   }
-  return aco_create(&g_solver, coords_host, &p, g_ws, g_ws_bytes, g_stream);
+  void* stream = g_stream;
+  if (!stream) {
+    if (!g_own_stream) {
+      const cudaError_t e = cudaStreamCreate(&g_own_stream);
+      if (e != cudaSuccess) {
+        g_own_stream = nullptr;
+        return cuda_error(e, "cudaStreamCreate");
+      }
+    }
+    stream = g_own_stream;
+  }
+  return aco_create(&g_solver, coords_host, &p, g_ws, g_ws_bytes, stream);
 }
 
 int aco_set_variant(int roulette, float gamma_max, float gamma_min, int T) {
