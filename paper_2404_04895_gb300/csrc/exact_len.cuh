@@ -52,6 +52,40 @@ ACO_HD void len_acc_add(uint64_t acc[kLenDigits], uint64_t b) {
   }
 }
 
+// Fast window.  One instance's edge lengths span few binades, so nearly every
+// edge of a tour starts at digit kLenWin or kLenWin + 1 (d in [2^-21, 2^43)).
+// Such an edge goes into a four-digit window (digits kLenWin .. kLenWin + 3)
+// with two-way selects instead of the full accumulator's eleven; any other
+// edge goes to the full accumulator, and len_win_merge adds the window back.
+// Integer sums again: the total is the same bits.
+constexpr int kLenWin = 4;
+
+// win += d and true if the in-range edge length with bit pattern b is 0 or
+// starts at digit kLenWin or kLenWin + 1; else win unchanged and false.
+ACO_HD bool len_win_add(uint64_t win[4], uint64_t b) {
+  if (b == 0ull) return true;
+  const int s = (int)(b >> 52) - kLenMinBiased;
+  const int t = (s >> 5) - kLenWin;
+  if ((unsigned)t > 1u) return false;
+  const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int r = s & 31;
+  const uint64_t lo = M << r;
+  const uint32_t w0 = (uint32_t)lo, w1 = (uint32_t)(lo >> 32);
+  const uint32_t w2 = r ? (uint32_t)(M >> (64 - r)) : 0u;
+  const bool z = t == 0;
+  win[0] += z ? w0 : 0u;
+  win[1] += z ? w1 : w0;
+  win[2] += z ? w2 : w1;
+  win[3] += z ? 0u : w2;
+  return true;
+}
+
+// acc += the window (before len_acc_carry).
+ACO_HD void len_win_merge(uint64_t acc[kLenDigits], const uint64_t win[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[kLenWin + i] += win[i];
+}
+
 // Carry propagation: afterwards every digit but the last is < 2^32 and the
 // value is unchanged (the last holds the rest: < 2^27 for any tour sum).
 ACO_HD void len_acc_carry(uint64_t acc[kLenDigits]) {

@@ -100,7 +100,8 @@ __device__ __forceinline__ void build_P_row(const void* __restrict__ tau_row,
 // them; all W warps of the CTA when W > 1).  f is the exact sum of the n fp64
 // edge lengths D[p_t][p_{t+1 mod n}] rounded once (exact_len.cuh): lane l of
 // warp w takes edges t = 32 w + l + 32 W i, four in flight at a time, adds
-// each to its own fixed-point digits, and the digit sums are combined across
+// each to its own fixed-point digits (the four-digit fast window when the
+// edge fits it, else all eleven), and the digit sums are combined across
 // lanes (redux on 16-bit halves) and warps (shared memory) -- integer sums, so
 // the split changes no bit.  For city a = p_t the index mapping
 // nbr[a][k] = (p_{t-1}, p_{t+1}); L_k and c_k = Q / L_k.  A tour with an edge
@@ -117,7 +118,7 @@ __device__ __forceinline__ void tour_length_exact(const double* __restrict__ D, 
                                                   unsigned long long* sacc) {
   constexpr int U = 4;
   const int lane = threadIdx.x & 31;
-  uint64_t acc[kLenDigits];
+  uint64_t acc[kLenDigits], win[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
   for (int i = 0; i < kLenDigits; ++i) acc[i] = 0ull;
   bool bad = false;
@@ -144,9 +145,10 @@ __device__ __forceinline__ void tour_length_exact(const double* __restrict__ D, 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       bad |= !len_in_range(db[u]);
-      len_acc_add(acc, db[u]);
+      if (!len_win_add(win, db[u])) len_acc_add(acc, db[u]);
     }
   }
+  len_win_merge(acc, win);
   len_acc_carry(acc);  // digits < 2^32 (the last < 2^27): 16-bit halves sum without overflow
   uint64_t sum[kLenDigits];
 #pragma unroll

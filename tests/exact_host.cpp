@@ -41,19 +41,21 @@ int hx_deposit_entry(float tp, const double* c, int k, int bf16, uint32_t* out) 
 int hx_dep_span() { return aco::kDepSpan; }
 
 // Sum of count edge lengths split round-robin over `groups` partial sums, in
-// reverse order within each group.  Returns -1 (and writes nothing) if an
+// reverse order within each group, each edge into the fast window or the
+// full digits as the tour-length kernel adds it.  Returns -1 (and writes nothing) if an
 // edge is outside the fixed-point range.
 int hx_tour_length(const double* d, int count, int groups, double* out) {
   if (groups < 1) groups = 1;
   uint64_t total[aco::kLenDigits] = {};
   for (int g = 0; g < groups; ++g) {
-    uint64_t acc[aco::kLenDigits] = {};
+    uint64_t acc[aco::kLenDigits] = {}, win[4] = {};
     for (int i = count - 1; i >= 0; --i) {
       if (i % groups != g) continue;
       const uint64_t b = aco::bits_of(d[i]);
       if (!aco::len_in_range(b)) return -1;
-      aco::len_acc_add(acc, b);
+      if (!aco::len_win_add(win, b)) aco::len_acc_add(acc, b);  // as the kernel adds them
     }
+    aco::len_win_merge(acc, win);
     aco::len_acc_carry(acc);
     for (int q = 0; q < aco::kLenDigits; ++q) total[q] += acc[q];
   }
