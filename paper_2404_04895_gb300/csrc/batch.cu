@@ -70,12 +70,16 @@ __global__ void __launch_bounds__(256) batch_build_P_lists_kernel(const InstDev*
 __global__ void __launch_bounds__(256) batch_tour_length_kernel(const InstDev* __restrict__ insts,
                                                                 const int* __restrict__ ant_off,
                                                                 int count, int total) {
-  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  __shared__ unsigned long long sacc[8 * (kLenDigits + 1)];
+  const int wid = (int)(threadIdx.x >> 5);
+  const int item = blockIdx.x * (blockDim.x >> 5) + wid;
   if (item >= total) return;
   const int i = find_instance(ant_off, count, item);
   const InstDev& I = insts[i];
   const int k = item - __ldg(ant_off + i);
-  tour_length_exact<1>(I.D, I.n, I.tours + (size_t)k * I.n, I.m, k, I.Q, I.L, I.c, I.nbr, 0, nullptr);
+  tour_length_exact<1>(I.D, I.n, I.tours + (size_t)k * I.n, k, I.Q, I.L, I.c,
+                       I.nbr ? static_cast<void*>(reinterpret_cast<int2*>(I.nbr) + k) : nullptr, I.m, 0,
+                       sacc + wid * (kLenDigits + 1));
 }
 
 __global__ void __launch_bounds__(256) batch_best_kernel(const InstDev* __restrict__ insts,

@@ -36,6 +36,20 @@ ACO_HD bool len_in_range(uint64_t b) {
   return b == 0ull || (eb >= (uint32_t)kLenMinBiased && eb <= (uint32_t)kLenMaxBiased);
 }
 
+// The digits of a nonzero in-range edge length with bit pattern b: d is
+// (w0 + w1 2^32 + w2 2^64) units of 2^-201 times 2^(32 q); returns q (0..8,
+// so q + 2 is a digit of the sum).
+ACO_HD int len_digits(uint64_t b, uint32_t* w0, uint32_t* w1, uint32_t* w2) {
+  const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int s = (int)(b >> 52) - kLenMinBiased;  // [0, 278]
+  const int r = s & 31;
+  const uint64_t lo = M << r;
+  *w0 = (uint32_t)lo;
+  *w1 = (uint32_t)(lo >> 32);
+  *w2 = r ? (uint32_t)(M >> (64 - r)) : 0u;
+  return s >> 5;
+}
+
 // acc += d for an in-range edge length with bit pattern b.
 ACO_HD void len_acc_add(uint64_t acc[kLenDigits], uint64_t b) {
   const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
@@ -84,6 +98,19 @@ ACO_HD bool len_win_add(uint64_t win[4], uint64_t b) {
 ACO_HD void len_win_merge(uint64_t acc[kLenDigits], const uint64_t win[4]) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc[kLenWin + i] += win[i];
+}
+
+// The window as five digits below 2^32 (the fifth takes the carry out of the
+// fourth), digit kLenWin + i in out[i]; the same value.
+ACO_HD void len_win_digits(const uint64_t win[4], uint64_t out[5]) {
+  uint64_t carry = 0ull;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint64_t v = win[i] + carry;  // win[i] < 2^48: no overflow
+    out[i] = v & 0xFFFFFFFFull;
+    carry = v >> 32;
+  }
+  out[4] = carry;
 }
 
 // Carry propagation: afterwards every digit but the last is < 2^32 and the

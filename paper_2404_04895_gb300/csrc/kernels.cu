@@ -149,11 +149,45 @@ __global__ void __launch_bounds__(256) tour_length_kernel(const double* __restri
                                                           int m, float Q, double* __restrict__ L,
                                                           double* __restrict__ c,
                                                           int32_t* __restrict__ nbr) {
-  __shared__ unsigned long long sacc[W * kLenDigits + 1];
-  const int k = W == 1 ? blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5) : blockIdx.x;
+  __shared__ unsigned long long sacc[(W == 1 ? 8 : 1) * (kLenDigits + 1)];
+  const int wid = (int)(threadIdx.x >> 5);
+  const int k = W == 1 ? blockIdx.x * (blockDim.x >> 5) + wid : blockIdx.x;
   if (k >= m) return;
-  tour_length_exact<W>(D, n, tours + (size_t)k * n, m, k, Q, L, c, nbr, W == 1 ? 0 : (int)(threadIdx.x >> 5),
-                       sacc);
+  tour_length_exact<W>(D, n, tours + (size_t)k * n, k, Q, L, c,
+                       nbr ? static_cast<void*>(reinterpret_cast<int2*>(nbr) + k) : nullptr, m, W == 1 ? 0 : wid,
+                       sacc + (W == 1 ? wid * (kLenDigits + 1) : 0));
+}
+
+// Two ants per CTA, W warps each.  Their index mappings are staged in shared
+// memory by city, 16 bits per neighbour (filled with 0xFFFF first: a city
+// missing from a tour reads as no neighbour, -1), and written out row by row,
+// both ants' int2 entries of a city in one 16-byte store: half the scattered
+// stores of writing every entry on its own, which dominate this step.  Ants
+// 2 blockIdx.x and 2 blockIdx.x + 1; m even (rows of nbr 16-byte aligned),
+// nbr 16-byte aligned,
+// n <= kTourPairMaxN.  Dynamic shared memory: 8 n bytes.
+template <int W>
+__global__ void __launch_bounds__(64 * W) tour_length_pair_kernel(const double* __restrict__ D, int n,
+                                                                  const int32_t* __restrict__ tours,
+                                                                  int m, float Q, double* __restrict__ L,
+                                                                  double* __restrict__ c,
+                                                                  int32_t* __restrict__ nbr) {
+  extern __shared__ __align__(16) uint2 stage[];  // [n]: packed (pred, succ) of ant 2b, then of ant 2b + 1
+  __shared__ unsigned long long sacc[2 * (kLenDigits + 1)];
+  const int wid = (int)(threadIdx.x >> 5);
+  const int a = wid / W;
+  const int k = 2 * (int)blockIdx.x + a;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) stage[q] = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
+  __syncthreads();
+  tour_length_exact<W, true>(D, n, tours + (size_t)k * n, k, Q, L, c, reinterpret_cast<uint32_t*>(stage) + a, 2,
+                             wid - a * W, sacc + a * (kLenDigits + 1));
+  __syncthreads();
+  auto wide = [](uint32_t h) { return h == 0xFFFFu ? -1 : (int)h; };
+  int4* out = reinterpret_cast<int4*>(nbr) + blockIdx.x;  // row q of nbr holds m / 2 int4
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const uint2 v = stage[q];
+    out[(size_t)q * (m / 2)] = make_int4(wide(v.x & 0xFFFFu), wide(v.x >> 16), wide(v.y & 0xFFFFu), wide(v.y >> 16));
+  }
 }
 
 __global__ void __launch_bounds__(1024) best_kernel(const double* __restrict__ L,
@@ -358,9 +392,27 @@ int launch_build_lists(const void* P, int prec, int n, int ld, uint2* lists, int
 // lane, and that a thousand ants fill the GPU several times over.
 int tour_length_warps(int n) { return n >= 2048 ? 4 : (n >= 512 ? 2 : 1); }
 
+// The paired form: 8 warps per ant (4 of its 512-thread CTAs per SM, one
+// wave for m = 1024); staging of 8 bytes per city, at most 56 KB.
+constexpr int kTourPairW = 8;
+constexpr int kTourPairMaxN = 7168;
+
+int prepare_tour_length() {
+  ACO_CUDA_TRY(cudaFuncSetAttribute(tour_length_pair_kernel<kTourPairW>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kTourPairMaxN * 8));
+  return ACO_OK;
+}
+
 int launch_tour_length(const double* D, int n, const int32_t* tours, int m, float Q, double* L,
                        double* c, int32_t* nbr, cudaStream_t st) {
-  switch (tour_length_warps(n)) {
+  const int W = tour_length_warps(n);
+  // pairs write 16-byte halves of nbr's rows: m even keeps every row aligned
+  if (nbr && W == 4 && n <= kTourPairMaxN && m % 2 == 0 && aligned16(nbr)) {
+    tour_length_pair_kernel<kTourPairW><<<m / 2, 64 * kTourPairW, (size_t)n * 8, st>>>(D, n, tours, m, Q, L, c,
+                                                                                       nbr);
+    return check_launch("tour_length_pair_kernel");
+  }
+  switch (W) {
     case 4:
       tour_length_kernel<4><<<m, 128, 0, st>>>(D, n, tours, m, Q, L, c, nbr);
       break;

@@ -130,6 +130,7 @@ int prepare_kernels() {
     if (!rc) rc = prepare_construct_bf16();
     if (!rc) rc = prepare_construct_f16();
     if (!rc) rc = prepare_deposit();
+    if (!rc) rc = prepare_tour_length();
     if (!rc) rc = prepare_construct_lean();
     if (!rc) rc = prepare_construct_rw();
   });
@@ -1176,6 +1177,8 @@ int aco_op_tour_length(const double* D_dev, int n, const int32_t* tours_dev, int
   if (!D_dev || !tours_dev || !L_dev) return set_error(ACO_ERR_ARG, "NULL argument");
   if (n < 3 || n > ACO_MAX_N || m < 1 || m > ACO_MAX_M) return set_error(ACO_ERR_ARG, "n or m out of range");
   if (nbr_dev && ((uintptr_t)nbr_dev & 7)) return set_error(ACO_ERR_ARG, "nbr must be 8-byte aligned");
+  const int rc = prepare_kernels();
+  if (rc) return rc;
   return launch_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c_dev, nbr_dev, static_cast<cudaStream_t>(stream));
 }
 

@@ -99,28 +99,35 @@ __device__ __forceinline__ void build_P_row(const void* __restrict__ tau_row,
 // Eq. 3 + Eq. 2 for ant k, by W cooperating warps (w: this warp's index among
 // them; all W warps of the CTA when W > 1).  f is the exact sum of the n fp64
 // edge lengths D[p_t][p_{t+1 mod n}] rounded once (exact_len.cuh): lane l of
-// warp w takes edges t = 32 w + l + 32 W i, four in flight at a time, adds
-// each to its own fixed-point digits (the four-digit fast window when the
-// edge fits it, else all eleven), and the digit sums are combined across
-// lanes (redux on 16-bit halves) and warps (shared memory) -- integer sums, so
-// the split changes no bit.  For city a = p_t the index mapping
-// nbr[a][k] = (p_{t-1}, p_{t+1}); L_k and c_k = Q / L_k.  A tour with an edge
-// length outside the fixed-point range (impossible for distances of fp32
-// coordinates) gets L_k = c_k = NaN.  sacc: W * kLenDigits + 1 shared words
-// (unused when W == 1).
+// warp w takes edges t = 32 w + l + 32 W i, four in flight at a time, and
+// adds each to its four-digit fast window in registers, or, if the edge does
+// not fit it, to the ant's eleven shared digits (atomics); the windows are
+// summed over lanes (redux on 16-bit halves) and added to the shared digits
+// by each warp -- integer sums, so the split changes no bit.  For city
+// a = p_t the index mapping nbr[a][k] = (p_{t-1}, p_{t+1}); L_k and
+// c_k = Q / L_k.  A tour with an edge length outside the fixed-point range
+// (impossible for distances of fp32 coordinates) gets L_k = c_k = NaN.
+// The index-mapping entry of city a goes to element a * nbs of nb (nb null:
+// none): an int2 in global memory, or with PACK16 (n <= 65535) one 32-bit
+// word (pred | succ << 16) of a shared staging area.  sacc: kLenDigits + 1
+// shared words for this ant (one area per warp when W == 1, per W-warp group
+// when W > 1).  W > 1: every warp of the CTA calls this (its block barriers).
 // ---------------------------------------------------------------------------
-template <int W>
+template <int W, bool PACK16 = false>
 __device__ __forceinline__ void tour_length_exact(const double* __restrict__ D, int n,
-                                                  const int32_t* __restrict__ p, int m, int k,
+                                                  const int32_t* __restrict__ p, int k,
                                                   float Q, double* __restrict__ L,
                                                   double* __restrict__ c,
-                                                  int32_t* __restrict__ nbr, int w,
+                                                  void* nb, int nbs, int w,
                                                   unsigned long long* sacc) {
   constexpr int U = 4;
   const int lane = threadIdx.x & 31;
-  uint64_t acc[kLenDigits], win[4] = {0ull, 0ull, 0ull, 0ull};
-#pragma unroll
-  for (int i = 0; i < kLenDigits; ++i) acc[i] = 0ull;
+  if (32 * w + lane <= kLenDigits) sacc[32 * w + lane] = 0ull;
+  if (W == 1)
+    __syncwarp();
+  else
+    __syncthreads();
+  uint64_t win[4] = {0ull, 0ull, 0ull, 0ull};
   bool bad = false;
   for (int t0 = 32 * w + lane; t0 < n; t0 += U * 32 * W) {
     uint64_t db[U];
@@ -135,52 +142,55 @@ __device__ __forceinline__ void tour_length_exact(const double* __restrict__ D, 
         // (only after a failed construction, which the host reports) is skipped
         if ((unsigned)cur < (unsigned)n && (unsigned)nx < (unsigned)n) {
           db[u] = (uint64_t)__double_as_longlong(__ldg(D + (size_t)cur * n + nx));
-          if (nbr) {
+          if (nb) {
             const int pv = __ldg(p + (t > 0 ? t - 1 : n - 1));
-            reinterpret_cast<int2*>(nbr)[(size_t)cur * m + k] = make_int2(pv, nx);
+            if (PACK16)
+              static_cast<uint32_t*>(nb)[(size_t)cur * nbs] = ((uint32_t)pv & 0xFFFFu) | ((uint32_t)nx << 16);
+            else
+              static_cast<int2*>(nb)[(size_t)cur * nbs] = make_int2(pv, nx);
           }
         }
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      bad |= !len_in_range(db[u]);
-      if (!len_win_add(win, db[u])) len_acc_add(acc, db[u]);
+      const bool ok = len_in_range(db[u]);
+      bad |= !ok;
+      if (ok && !len_win_add(win, db[u])) {  // rare: an edge outside the window's binades
+        uint32_t w0, w1, w2;
+        const int q = len_digits(db[u], &w0, &w1, &w2);
+        atomicAdd(sacc + q, (unsigned long long)w0);
+        atomicAdd(sacc + q + 1, (unsigned long long)w1);
+        atomicAdd(sacc + q + 2, (unsigned long long)w2);
+      }
     }
   }
-  len_win_merge(acc, win);
-  len_acc_carry(acc);  // digits < 2^32 (the last < 2^27): 16-bit halves sum without overflow
-  uint64_t sum[kLenDigits];
+  uint64_t wd[5];
+  len_win_digits(win, wd);
 #pragma unroll
-  for (int i = 0; i < kLenDigits; ++i) {
-    const uint32_t lo = __reduce_add_sync(ACO_FULL_MASK, (uint32_t)acc[i] & 0xFFFFu);
-    const uint32_t hi = __reduce_add_sync(ACO_FULL_MASK, (uint32_t)(acc[i] >> 16));
-    sum[i] = (uint64_t)lo + ((uint64_t)hi << 16);
+  for (int i = 0; i < 5; ++i) {
+    const uint32_t lo = __reduce_add_sync(ACO_FULL_MASK, (uint32_t)wd[i] & 0xFFFFu);
+    const uint32_t hi = __reduce_add_sync(ACO_FULL_MASK, (uint32_t)(wd[i] >> 16));
+    wd[i] = (uint64_t)lo + ((uint64_t)hi << 16);
   }
   bad = __any_sync(ACO_FULL_MASK, bad);
-  if (W > 1) {
-    if (lane == 0) {
-#pragma unroll
-      for (int i = 0; i < kLenDigits; ++i) sacc[w * kLenDigits + i] = sum[i];
-      if (w == 0) sacc[W * kLenDigits] = 0ull;
-    }
-    __syncthreads();
-    if (lane == 0 && bad) atomicOr(sacc + W * kLenDigits, 1ull);
-    __syncthreads();
-    if (w != 0) return;
-#pragma unroll
-    for (int i = 0; i < kLenDigits; ++i) {
-      uint64_t v = 0ull;
-      for (int q = 0; q < W; ++q) v += sacc[q * kLenDigits + i];
-      sum[i] = v;
-    }
-    bad = sacc[W * kLenDigits] != 0ull;
-  }
   if (lane == 0) {
-    const double total = bad ? __longlong_as_double(0x7FF8000000000000ll) : len_acc_round(sum);
-    L[k] = total;
-    if (c) c[k] = __ddiv_rn((double)Q, total);
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      if (wd[i]) atomicAdd(sacc + kLenWin + i, (unsigned long long)wd[i]);
+    if (bad) atomicOr(sacc + kLenDigits, 1ull);
   }
+  if (W == 1)
+    __syncwarp();
+  else
+    __syncthreads();
+  if (w != 0 || lane != 0) return;
+  uint64_t acc[kLenDigits];
+#pragma unroll
+  for (int i = 0; i < kLenDigits; ++i) acc[i] = sacc[i];
+  const double total = sacc[kLenDigits] ? __longlong_as_double(0x7FF8000000000000ll) : len_acc_round(acc);
+  L[k] = total;
+  if (c) c[k] = __ddiv_rn((double)Q, total);
 }
 
 // ---------------------------------------------------------------------------

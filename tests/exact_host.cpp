@@ -53,9 +53,17 @@ int hx_tour_length(const double* d, int count, int groups, double* out) {
       if (i % groups != g) continue;
       const uint64_t b = aco::bits_of(d[i]);
       if (!aco::len_in_range(b)) return -1;
-      if (!aco::len_win_add(win, b)) aco::len_acc_add(acc, b);  // as the kernel adds them
+      if (!aco::len_win_add(win, b)) {  // as the kernel adds them: window, else its digits
+        uint32_t w0, w1, w2;
+        const int q = aco::len_digits(b, &w0, &w1, &w2);
+        acc[q] += w0;
+        acc[q + 1] += w1;
+        acc[q + 2] += w2;
+      }
     }
-    aco::len_win_merge(acc, win);
+    uint64_t wd[5];
+    aco::len_win_digits(win, wd);
+    for (int i = 0; i < 5; ++i) acc[aco::kLenWin + i] += wd[i];
     aco::len_acc_carry(acc);
     for (int q = 0; q < aco::kLenDigits; ++q) total[q] += acc[q];
   }

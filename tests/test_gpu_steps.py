@@ -157,8 +157,13 @@ def test_construct_adair_matrix_and_ties(orc):
     assert np.array_equal(host(tours), orc.construct(Pc, 4, 1, 0, m))
 
 
-@pytest.mark.parametrize("n,m", [(3, 2), (50, 50), (301, 77)])
+@pytest.mark.parametrize("n,m", [(3, 2), (50, 50), (301, 77), (2100, 7), (2100, 6), (5000, 8), (7168, 4),
+                                 (7200, 4)])
 def test_tour_length_neighbours_best(orc, n, m):
+    """Lengths, c, the index mapping and the best, for every kernel form: one
+    warp, two and four warps per ant, two ants per CTA with the mapping staged
+    in shared memory (2048 <= n <= 7168, m even), and four warps per ant
+    otherwise (m odd, or n beyond that)."""
     xy = instances.uniform(n, 3)
     Dr = orc.distances(xy)
     rng = np.random.default_rng(n)
