@@ -401,8 +401,8 @@ __device__ __forceinline__ int2 deposit_scale_block(const double* __restrict__ c
 //   3. each warp takes 32 ants at a time: lanes whose columns share a slot
 //      are grouped by __match_any_sync, their 24-bit weight chunks summed by
 //      one redux per chunk, and the group's leader adds the sums to the
-//      slot's carry-save words with shared 64-bit atomics (integer sums: any
-//      order gives the same bits)
+//      slot's carry-save words with shared atomics (integer sums: any order
+//      gives the same bits)
 //   4. one thread per slot rounds tau' + its sum once (into a shared table),
 //      then one coalesced pass over the row writes tau' or the slot's result
 // At most `cap` slots are summed per pass; rows with more touched columns
@@ -412,6 +412,15 @@ __device__ __forceinline__ int2 deposit_scale_block(const double* __restrict__ c
 // entry becomes NaN and the others tau'.
 // smem: deposit_smem_bytes(n, cap).
 // ---------------------------------------------------------------------------
+// w += v for a 64-bit shared word w kept as two 32-bit halves (w[0] low):
+// one 32-bit atomic add, and a second on the high half only when the low one
+// wraps -- every carry is counted once whatever the interleaving, and shared
+// 32-bit atomics run several times faster than 64-bit ones on this GPU.
+__device__ __forceinline__ void dep_add_u64(uint32_t* w, uint32_t v) {
+  const uint32_t old = atomicAdd(w, v);
+  if (old + v < old) atomicAdd(w + 1, 1u);
+}
+
 constexpr int kDepThreads = 256;
 constexpr int kDepCap = 512;  // 16 KB of slots: a row's touched columns are few once tours share edges
 
@@ -433,7 +442,9 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nthr = blockDim.x;
   const int nw = (n + 31) >> 5;
-  unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem);  // [cap][4]
+  // [cap][4]: per slot the carry-save words w0, w1, w2 (each as two 32-bit
+  // halves, see dep_add_u64) and the count of infinite weights
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem);
   uint32_t* bm = reinterpret_cast<uint32_t*>(acc + (size_t)cap * 4);      // [nw]
   uint32_t* base = bm + nw;                                                // [nw]
   int* sc = reinterpret_cast<int*>(base + nw);                             // [33]
@@ -534,11 +545,11 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
           uint32_t ri = 0u;
           if (mode == kDepInf) ri = __reduce_add_sync(grp, in ? qi : 0u);
           if (in && lane == __ffs(grp) - 1) {
-            unsigned long long* a = acc + 4 * sl;
-            if (r0) atomicAdd(a + 0, (unsigned long long)r0);
-            if (r1) atomicAdd(a + 1, (unsigned long long)r1);
-            if (r2) atomicAdd(a + 2, (unsigned long long)r2);
-            if (ri) atomicAdd(a + 3, (unsigned long long)ri);
+            uint32_t* a = reinterpret_cast<uint32_t*>(acc + 4 * sl);
+            if (r0) dep_add_u64(a + 0, r0);
+            if (r1) dep_add_u64(a + 2, r1);
+            if (r2) dep_add_u64(a + 4, r2);
+            if (ri) atomicAdd(a + 6, ri);
           }
         }
       }
@@ -567,12 +578,13 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
       for (int sl = tid; sl < used; sl += nthr) {
         const int j = tcol[sl];
         const float tp = __fmul_rn(keep, TB ? __uint_as_float((uint32_t)rowh[j] << 16) : row[j]);
-        const unsigned long long* a = acc + 4 * sl;
-        if (mode == kDepInf && a[3])
+        const uint32_t* a = reinterpret_cast<const uint32_t*>(acc + 4 * sl);
+        const uint64_t w0 = ((uint64_t)a[1] << 32) | a[0], w1 = ((uint64_t)a[3] << 32) | a[2];
+        const uint64_t w2 = ((uint64_t)a[5] << 32) | a[4];
+        if (mode == kDepInf && a[6])
           res[sl] = TB ? 0x7F80u : 0x7F800000u;
         else
-          res[sl] = TB ? round_sum_bf16(tp, a[0], a[1], a[2], E0)
-                       : __float_as_uint(round_sum_f32(tp, a[0], a[1], a[2], E0));
+          res[sl] = TB ? round_sum_bf16(tp, w0, w1, w2, E0) : __float_as_uint(round_sum_f32(tp, w0, w1, w2, E0));
       }
       __syncthreads();
     }
