@@ -35,8 +35,10 @@ namespace aco {
 
 constexpr int kDepSpan = 19;  // binades the weights of one iteration may span (53 + 19 = 72 bits)
 
-// deposit scaling modes
-enum { kDepFixed = 0, kDepInf = 1, kDepBad = 2 };
+// deposit scaling modes; kDepNarrow: fixed point with every weight's
+// exponent E0 or E0 + 1, so that a weight (at most 54 bits) is two 27-bit
+// chunks instead of three 24-bit ones (32 of them still sum below 2^32)
+enum { kDepFixed = 0, kDepInf = 1, kDepBad = 2, kDepNarrow = 3 };
 
 ACO_HD int clz64(uint64_t x) {
 #if defined(__CUDA_ARCH__)
@@ -102,6 +104,18 @@ ACO_HD void weight_chunks(double v, int E0, uint32_t* c0, uint32_t* c1, uint32_t
   *c0 = (uint32_t)(lo & 0xFFFFFFull);
   *c1 = (uint32_t)((lo >> 24) & 0xFFFFFFull);
   *c2 = (uint32_t)((lo >> 48) | (hi << 16));
+}
+
+// The two 27-bit chunks of weight v in units of 2^E0 (v positive finite,
+// exponent_of(v) - E0 in {0, 1}: at most 54 bits).  Chunk 1 counts units of
+// 2^(E0 + 27), i.e. (c1 << 3) units of 2^(E0 + 24) in the three-chunk form.
+ACO_HD void weight_chunks27(double v, int E0, uint32_t* c0, uint32_t* c1) {
+  uint64_t M;
+  int e;
+  split_double(v, &M, &e);
+  const uint64_t w = M << (e - E0);
+  *c0 = (uint32_t)(w & 0x7FFFFFFull);
+  *c1 = (uint32_t)(w >> 27);
 }
 
 // (hi, lo) += (bh, bl)

@@ -337,7 +337,8 @@ __device__ __forceinline__ void select_topk_block(const double* __restrict__ L, 
 // ---------------------------------------------------------------------------
 // Scaling of the deposit weights c[0..m) for the exact fixed-point sums
 // (exact.cuh): x = E0, the smallest exponent of a positive finite weight, and
-// y = mode: kDepFixed; kDepInf if some weight is +inf (a zero tour length:
+// y = mode: kDepNarrow if every weight's exponent is E0 or E0 + 1 (two
+// 27-bit chunks each), else kDepFixed; kDepInf if some weight is +inf (a zero tour length:
 // every city at one point); kDepBad if a weight is negative or NaN, or the
 // positive ones span more than kDepSpan binades (tour lengths of one planar
 // instance span at most log2(n) + 1).  All threads of the CTA; every thread
@@ -386,6 +387,7 @@ __device__ __forceinline__ int2 deposit_scale_block(const double* __restrict__ c
   __syncthreads();  // sred may be reused by the caller
   int mode = (flags & 2u) ? kDepBad : (flags & 1u) ? kDepInf : kDepFixed;
   if (emin != INT_MAX && emax - emin > kDepSpan) mode = kDepBad;
+  if (mode == kDepFixed && emin != INT_MAX && emax - emin <= 1) mode = kDepNarrow;
   return make_int2(emin == INT_MAX ? 0 : emin, mode);
 }
 
@@ -527,9 +529,12 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
         if (valid) {
           e = __ldg(nbr_row + k);
           const double v = __ldg(c + k);
-          if (v > 0.0 && v < INFINITY)
-            weight_chunks(v, E0, &q0, &q1, &q2);
-          else if (v == INFINITY)
+          if (v > 0.0 && v < INFINITY) {
+            if (mode == kDepNarrow)
+              weight_chunks27(v, E0, &q0, &q1);
+            else
+              weight_chunks(v, E0, &q0, &q1, &q2);
+          } else if (v == INFINITY)
             qi = 1u;
         }
 #pragma unroll
@@ -541,7 +546,8 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
           const unsigned grp = __match_any_sync(ACO_FULL_MASK, in ? sl : -1 - lane);
           const uint32_t r0 = __reduce_add_sync(grp, in ? q0 : 0u);
           const uint32_t r1 = __reduce_add_sync(grp, in ? q1 : 0u);
-          const uint32_t r2 = __reduce_add_sync(grp, in ? q2 : 0u);
+          uint32_t r2 = 0u;  // (no third chunk in the narrow form)
+          if (mode != kDepNarrow) r2 = __reduce_add_sync(grp, in ? q2 : 0u);
           uint32_t ri = 0u;
           if (mode == kDepInf) ri = __reduce_add_sync(grp, in ? qi : 0u);
           if (in && lane == __ffs(grp) - 1) {
@@ -579,8 +585,9 @@ __device__ __forceinline__ void deposit_row_exact(void* __restrict__ row_v, int 
         const int j = tcol[sl];
         const float tp = __fmul_rn(keep, TB ? __uint_as_float((uint32_t)rowh[j] << 16) : row[j]);
         const uint32_t* a = reinterpret_cast<const uint32_t*>(acc + 4 * sl);
-        const uint64_t w0 = ((uint64_t)a[1] << 32) | a[0], w1 = ((uint64_t)a[3] << 32) | a[2];
-        const uint64_t w2 = ((uint64_t)a[5] << 32) | a[4];
+        const uint64_t w0 = ((uint64_t)a[1] << 32) | a[0], w2 = ((uint64_t)a[5] << 32) | a[4];
+        uint64_t w1 = ((uint64_t)a[3] << 32) | a[2];
+        if (mode == kDepNarrow) w1 <<= 3;  // units of 2^27 -> 2^24 (w1 < 2m 2^27 <= 2^48)
         if (mode == kDepInf && a[6])
           res[sl] = TB ? 0x7F80u : 0x7F800000u;
         else

@@ -2,7 +2,8 @@
 //   - the deposit (csrc/exact.cuh, the integer code the deposit kernel runs):
 //     one touched pheromone entry, tau' + the exact sum of its paths' weights
 //     (Sec. 2.3, Eq. 3), formed the way the kernel forms it -- weights split
-//     into 24-bit chunks in units of 2^E0 (E0 the smallest weight exponent),
+//     into 24-bit chunks in units of 2^E0 (E0 the smallest weight exponent;
+//     two 27-bit chunks when every exponent is E0 or E0 + 1),
 //     the chunks summed per word in any order, then rounded once;
 //   - the tour length (csrc/exact_len.cuh, the tour-length kernel's code):
 //     the edge lengths dealt to `groups` partial sums the way lanes and warps
@@ -27,13 +28,18 @@ int hx_deposit_entry(float tp, const double* c, int k, int bf16, uint32_t* out) 
   }
   if (k < 1 || emax - e0 > aco::kDepSpan) return -1;
   uint64_t w0 = 0, w1 = 0, w2 = 0;
+  const bool narrow = emax - e0 <= 1;  // as the kernel splits them: two 27-bit chunks, else three 24-bit
   for (int i = k - 1; i >= 0; --i) {  // any order: integer sums
-    uint32_t a, b, d;
-    aco::weight_chunks(c[i], e0, &a, &b, &d);
+    uint32_t a, b, d = 0;
+    if (narrow)
+      aco::weight_chunks27(c[i], e0, &a, &b);
+    else
+      aco::weight_chunks(c[i], e0, &a, &b, &d);
     w0 += a;
     w1 += b;
     w2 += d;
   }
+  if (narrow) w1 <<= 3;
   *out = bf16 ? aco::round_sum_bf16(tp, w0, w1, w2, e0) : aco::bits_of(aco::round_sum_f32(tp, w0, w1, w2, e0));
   return 0;
 }
