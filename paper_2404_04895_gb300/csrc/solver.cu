@@ -236,6 +236,7 @@ static Layout layout_of(int n, int m) {
   L.c = take((size_t)m * 8);
   L.dep = take(8);
   L.nbr = take((size_t)n * m * 2 * 4);
+  // best_tour .. err adjacent: aco_solver_best reads them with one copy
   L.best_tour = take((size_t)n * 4);
   L.best_len = take(8);
   L.it = take(4);
@@ -338,6 +339,7 @@ struct aco_solver {
   bool use_graph;
   bool profiling;
   cudaEvent_t ev[7];           // probes around the iteration's kernels
+  unsigned char* stage;        // pinned host copy of best_tour .. err (aco_solver_best)
 
   template <class T>
   T* at(size_t off) { return reinterpret_cast<T*>(ws + off); }
@@ -535,6 +537,14 @@ int aco_create(aco_solver** out, const float* coords_host, const aco_params* p, 
     s->ws = static_cast<unsigned char*>(mem);
     s->own_ws = true;
   }
+  {
+    const cudaError_t e = cudaMallocHost(&s->stage, s->lay.err + 4 - s->lay.best_tour);
+    if (e != cudaSuccess) {
+      if (s->own_ws) cudaFree(s->ws);
+      delete s;
+      return cuda_error(e, "cudaMallocHost(result staging)");
+    }
+  }
   const Layout& L = s->lay;
   s->coords = s->at<float>(L.coords);
   s->D = s->at<double>(L.D);
@@ -559,7 +569,9 @@ int aco_create(aco_solver** out, const float* coords_host, const aco_params* p, 
   s->use_graph = s->stream != nullptr;
 
   auto fail = [&](int code) {
+    drop_graph(s);
     if (s->own_ws) cudaFree(s->ws);
+    cudaFreeHost(s->stage);
     delete s;
     return code;
   };
@@ -579,6 +591,10 @@ int aco_create(aco_solver** out, const float* coords_host, const aco_params* p, 
     return fail(cuda_error(cudaGetLastError(), "initialise state"));
   rc = upload_schedule(s);
   if (rc) return fail(rc);
+  if (s->use_graph) {  // capture the iteration on the host while the set-up kernels run
+    rc = build_graph(s);
+    if (rc) return fail(rc);
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "init sync"));
   *out = s;
   return ACO_OK;
@@ -591,6 +607,7 @@ int aco_destroy(aco_solver* s) {
   if (s->profiling)
     for (int q = 0; q < 7; ++q) cudaEventDestroy(s->ev[q]);
   if (s->own_ws) cudaFree(s->ws);
+  cudaFreeHost(s->stage);
   delete s;
   return ACO_OK;
 }
@@ -617,10 +634,19 @@ int aco_solver_iterate(aco_solver* s, int k) {
 int aco_solver_best(aco_solver* s, int32_t* tour_host, double* len_host) {
   if (!s || !tour_host || !len_host) return set_error(ACO_ERR_ARG, "NULL argument");
   if (s->it == 0) return set_error(ACO_ERR_STATE, "no iteration has run yet");
-  int rc = solver_sync_check(s);
-  if (rc) return rc;
-  ACO_CUDA_TRY(cudaMemcpy(len_host, s->best_len, 8, cudaMemcpyDeviceToHost));
-  ACO_CUDA_TRY(cudaMemcpy(tour_host, s->best_tour, sizeof(int32_t) * s->p.n, cudaMemcpyDeviceToHost));
+  // best tour, best length and the error word in one copy after the solver's work
+  const Layout& L = s->lay;
+  ACO_CUDA_TRY(cudaMemcpyAsync(s->stage, s->ws + L.best_tour, L.err + 4 - L.best_tour, cudaMemcpyDeviceToHost,
+                               s->stream));
+  ACO_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  int32_t err = 0;
+  std::memcpy(&err, s->stage + (L.err - L.best_tour), 4);
+  if (err) {  // reported once, as solver_sync_check does
+    ACO_CUDA_TRY(cudaMemset(s->err, 0, 4));
+    return kernel_check_error(err);
+  }
+  std::memcpy(len_host, s->stage + (L.best_len - L.best_tour), 8);
+  std::memcpy(tour_host, s->stage, sizeof(int32_t) * s->p.n);
   return ACO_OK;
 }
 
