@@ -67,16 +67,34 @@ __host__ __device__ inline int lean_max_n(int) { return 16384; }
 // overlapping, and either ant's rare slow path stalls both.
 constexpr int kLeanAnts = 1;
 
+// The first round of row `row`'s list (lane l: entry l) and the row's bound:
+// what every step needs.  Later rounds are loaded by lean_more_rounds, only
+// for the few steps the first round does not decide.
+struct ListHead {
+  uint2 e;
+  uint32_t lb;
+  int row;
+};
+
+__device__ __forceinline__ ListHead load_list_head(const uint2* __restrict__ lists, const uint32_t* __restrict__ lkey,
+                                                   int row) {
+  ListHead L;
+  L.e = __ldg(lists + (size_t)row * kListMax + (threadIdx.x & 31));
+  L.lb = __ldg(lkey + row);
+  L.row = row;
+  return L;
+}
+
 // Rounds 1, 2, ... of a step's list after an undecided first round whose last
 // entry was listed (so that more may follow); as list_rounds, with entries
 // loaded two rounds ahead.
-__device__ __forceinline__ int lean_more_rounds(const uint2* __restrict__ lists, const ListRow& L,
+__device__ __forceinline__ int lean_more_rounds(const uint2* __restrict__ lists, const ListHead& L,
                                                  const uint32_t* __restrict__ svis, const PhiloxKeys& ks,
                                                  uint32_t it, int k, int t, float& bs, int& bj) {
   const int lane = threadIdx.x & 31;
   constexpr int R = kListMax / 32;
   const uint2* __restrict__ lrow = lists + (size_t)L.row * kListMax;
-  uint2 e = L.e_next;
+  uint2 e = __ldg(lrow + 32 + lane);
   uint2 e2 = R > 2 ? __ldg(lrow + 64 + lane) : e;
   uint2 e3 = R > 3 ? __ldg(lrow + 96 + lane) : e;
   uint32_t lk = __reduce_max_sync(ACO_FULL_MASK, score_key(bs));
@@ -233,7 +251,7 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
   const PhiloxKeys ks = philox_keys(key);
 
   int cur[NA];
-  ListRow lr[NA], sp[NA][2];
+  ListHead lr[NA], sp[NA][2];
 #pragma unroll
   for (int q = 0; q < NA; ++q) {
     for (int w = lane; w < (int)(lean_flag_bytes(n) / 4); w += 32) svis[q][w] = 0u;
@@ -247,7 +265,7 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
       lean_mark(svis[q], cur[q]);
       tour[q][0] = cur[q];
     }
-    if (LISTS) lr[q] = load_list_row(lists, lkey, cur[q]);
+    if (LISTS) lr[q] = load_list_head(lists, lkey, cur[q]);
   }
   __syncwarp();
 
@@ -285,8 +303,8 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
         philox_round(xc, ks, 6);
         const int sj2 = __shfl_sync(ACO_FULL_MASK, j, __ffs(un2) - 1);
         philox_round(xc, ks, 7);
-        sp[q][0] = load_list_row(lists, lkey, sj);
-        sp[q][1] = load_list_row(lists, lkey, sj2);
+        sp[q][0] = load_list_head(lists, lkey, sj);
+        sp[q][1] = load_list_head(lists, lkey, sj2);
         if constexpr (PROBE) pr[3] = clock_after((uint32_t)sj2) - pr[0];
         if (!un) sp[q][0].row = -1;
         if (!un2) sp[q][1].row = -1;
@@ -357,7 +375,7 @@ __device__ __forceinline__ void construct_ants_lean(const void* __restrict__ Pv,
           lr[q] = sp[q][1];
           if constexpr (PROBE) pr[7] |= 16u;
         } else {
-          lr[q] = load_list_row(lists, lkey, next[q]);
+          lr[q] = load_list_head(lists, lkey, next[q]);
         }
       }
     }
