@@ -81,6 +81,30 @@ def test_weight_span_limit(orc, span, ok):
         _check_refused(got, tours, tau0, 0.3)
 
 
+@pytest.mark.parametrize("top", [1.0, 1.999, 2.0, 3.99, 4.0, 16.0])
+def test_two_and_three_chunk_weights(orc, top):
+    """Weights whose exponents differ by at most one are summed as two 27-bit
+    chunks, wider spans as three 24-bit ones: lengths from 1 up to `top`
+    (exponent spans 0, 1, 1, 2, 2 and 4), many ants sharing edges, each form
+    against the oracle bit for bit."""
+    rng = np.random.default_rng(int(top * 1000))
+    n, m = 300, 96
+    base = rng.permutation(n)
+    tours = []
+    for k in range(m):
+        t = base.copy()
+        if k % 2:
+            i, j = sorted(rng.integers(0, n, size=2))
+            t[i:j + 1] = t[i:j + 1][::-1]
+        tours.append(t)
+    tours = np.asarray(tours, np.int32)
+    L = rng.uniform(1.0, top, size=m)
+    L[0], L[-1] = 1.0, top
+    tau0 = rng.uniform(0.5, 2, size=(n, n)).astype(np.float32)
+    got, ref, err = _deposit(orc, tours, L, tau0, 0.1)
+    assert err == 0 and _same(got, ref)
+
+
 def _check_refused(got, tours, tau0, rho):
     """Every entry some path uses is NaN, every other one evaporated."""
     n = tau0.shape[0]
