@@ -364,7 +364,9 @@ int aco_op_construct_ex(const void* P_dev, int prec, int n, int ld, int m, uint6
  * tour k: nbr_dev[(a*m + k)*2 + {0,1}] = (predecessor, successor) (nbr_dev:
  * n*m*2 int32, nullable).  The exact sum holds edge lengths of 0 or in
  * [2^-149, 2^130) -- every distance of fp32 coordinates; a tour with any
- * other edge length gets L_k = c_k = NaN. */
+ * other edge length gets L_k = c_k = NaN.  Tours are permutations of 0..n-1;
+ * for a city some tour misses, that ant's nbr entry is -1 or left as it was
+ * (entries outside [0, n) are skipped by the deposit). */
 int aco_op_tour_length(const double* D_dev, int n, const int32_t* tours_dev, int m, float Q,
                        double* L_dev, double* c_dev, int32_t* nbr_dev, void* stream);
 
