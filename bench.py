@@ -430,7 +430,9 @@ def run_native(args, w, dist):
         "iters_per_s": round(1e3 / ms_per_step, 2),
         "roofline": roofline,
         "kernel_ms": kernel_ms,
-        "gpu_launches": args.steps * (6 if lists else 5),
+        # per iteration: M_p (with its lists when they are on), construction,
+        # tour lengths, best, deterministic deposit
+        "gpu_launches": args.steps * 5,
         "clocks": clocks,
         "best_len_after_steps": best_len,
     }
