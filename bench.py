@@ -430,9 +430,10 @@ def run_native(args, w, dist):
         "iters_per_s": round(1e3 / ms_per_step, 2),
         "roofline": roofline,
         "kernel_ms": kernel_ms,
-        # per iteration: M_p (with its lists when they are on), construction,
-        # tour lengths, best, deterministic deposit
-        "gpu_launches": args.steps * 5,
+        # per iteration: construction, tour lengths, best, and the deterministic
+        # deposit, which with lists also computes the next iteration's M_p and
+        # lists; without lists M_p is a launch of its own
+        "gpu_launches": args.steps * (4 if lists else 5),
         "clocks": clocks,
         "best_len_after_steps": best_len,
     }

@@ -116,6 +116,12 @@ int launch_fill_tau(void* tau, int tau_prec, int n, int ld, float v, cudaStream_
 int launch_build_P_lists(const void* tau, int tau_prec, const float* H, int n, int ld, int alpha, float inv_gamma,
                          const float* inv_gamma_dev, const uint32_t* it_dev, int n_sched, float rho, int prec, void* P,
                          uint2* lists, int* lcnt, uint32_t* lkey, cudaStream_t st);
+// the deterministic deposit, then the next iteration's M_p and lists, one
+// CTA per row (dep from the best kernel; *it_dev already advanced)
+int launch_deposit_P_lists(void* tau, int tau_prec, int n, int ld, const int32_t* nbr, const double* c, int m,
+                           float rho, const int2* dep, const float* H, int alpha, const float* inv_gamma_dev,
+                           const uint32_t* it_dev, int n_sched, int prec, void* P, uint2* lists, int* lcnt,
+                           uint32_t* lkey, cudaStream_t st);
 int prepare_tour_length();
 int launch_tour_length(const double* D, int n, const int32_t* tours, int m, float Q,
                        double* L, double* c, int32_t* nbr, cudaStream_t st);

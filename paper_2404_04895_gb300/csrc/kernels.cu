@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -233,6 +234,40 @@ __global__ void __launch_bounds__(kDepThreads) deposit_kernel(void* __restrict__
                         reinterpret_cast<const int2*>(nbr) + (size_t)a * m, c, m, keep, d.x, d.y, cap, smem);
 }
 
+// The deterministic deposit of row a followed, in the same CTA, by the next
+// iteration's M_p and candidate list of that row (build_P_lists_row) from
+// the tau row just written, read back through the L2.  *it_dev is the next
+// iteration's index by then (the best kernel advances it), so AdaIR's
+// exponent and the list's guess are those build_P_lists_kernel would use at
+// the start of that iteration; the tau row is not read from HBM a second
+// time.  Dynamic shared memory: the deposit's, reused as the list scratch.
+template <int PREC, bool TB>
+__global__ void __launch_bounds__(kDepThreads, 6) deposit_P_lists_kernel(
+    void* __restrict__ tau, int n, int ld, const int32_t* __restrict__ nbr, const double* __restrict__ c, int m,
+    float keep, const int2* __restrict__ dep, int cap, const float* __restrict__ H, int alpha,
+    const float* __restrict__ inv_gamma_dev, const uint32_t* __restrict__ it_dev, int n_sched,
+    void* __restrict__ Pv, uint2* __restrict__ lists, int* __restrict__ lcnt, uint32_t* __restrict__ lkey) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float red[32];
+  const int a = blockIdx.x;
+  const int2 d = *dep;
+  char* tau_row = static_cast<char*>(tau) + (size_t)a * ld * (TB ? 2 : 4);
+  deposit_row_exact<TB>(tau_row, n, reinterpret_cast<const int2*>(nbr) + (size_t)a * m, c, m, keep, d.x, d.y, cap,
+                        smem);  // ends with a block barrier: the row's stores are visible to the CTA
+  float inv_gamma = 1.0f, ig_prev = 1.0f;
+  if (inv_gamma_dev) {
+    const uint32_t it = *it_dev;
+    const uint32_t last = (uint32_t)(n_sched - 1);
+    inv_gamma = inv_gamma_dev[it < last ? it : last];
+    ig_prev = it > 0u ? inv_gamma_dev[it - 1u < last ? it - 1u : last] : 0.0f;
+  }
+  const uint32_t guess = list_guess(lkey[a], keep, alpha, inv_gamma, ig_prev);
+  const size_t eb = PREC == ACO_FP32 ? 4 : 2;
+  build_P_lists_row<PREC, TB, true>(tau_row, H + (size_t)a * ld, n, ld, a, alpha, inv_gamma,
+                                    static_cast<char*>(Pv) + (size_t)a * ld * eb, lists + (size_t)a * kListMax,
+                                    lcnt + a, lkey + a, guess, reinterpret_cast<uint32_t*>(smem), red);
+}
+
 // tau <- fl32(keep * tau), keep = fl32(1 - rho): evaporation in fp32
 __global__ void evaporate_kernel(float* __restrict__ tau, int n, int ld, float keep) {
   const int i = blockIdx.y;
@@ -437,12 +472,61 @@ int launch_select_topk(const double* L, int m, int k, double* c, cudaStream_t st
   return check_launch("select_topk_kernel");
 }
 
+// The fused kernel's dynamic shared memory: the deposit's, at least the list
+// scratch that reuses it.
+static size_t deposit_P_smem_bytes(int n, int cap) {
+  return std::max(deposit_smem_bytes(n, cap), (size_t)kListScratchWords * 4);
+}
+
 int prepare_deposit() {
-  ACO_CUDA_TRY(cudaFuncSetAttribute(deposit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)deposit_smem_bytes(ACO_MAX_N, kDepCap)));
-  ACO_CUDA_TRY(cudaFuncSetAttribute(deposit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)deposit_smem_bytes(ACO_MAX_N, kDepCap)));
+  const int most = (int)deposit_P_smem_bytes(ACO_MAX_N, kDepCap);
+  ACO_CUDA_TRY(cudaFuncSetAttribute(deposit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
+  ACO_CUDA_TRY(cudaFuncSetAttribute(deposit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
+  const void* fused[] = {(const void*)deposit_P_lists_kernel<ACO_FP32, false>,
+                         (const void*)deposit_P_lists_kernel<ACO_FP32, true>,
+                         (const void*)deposit_P_lists_kernel<ACO_BF16, false>,
+                         (const void*)deposit_P_lists_kernel<ACO_BF16, true>,
+                         (const void*)deposit_P_lists_kernel<ACO_FP16, false>,
+                         (const void*)deposit_P_lists_kernel<ACO_FP16, true>};
+  for (const void* f : fused)
+    ACO_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
   return ACO_OK;
+}
+
+int launch_deposit_P_lists(void* tau, int tau_prec, int n, int ld, const int32_t* nbr, const double* c, int m,
+                           float rho, const int2* dep, const float* H, int alpha, const float* inv_gamma_dev,
+                           const uint32_t* it_dev, int n_sched, int prec, void* P, uint2* lists, int* lcnt,
+                           uint32_t* lkey, cudaStream_t st) {
+  const int cap = deposit_cap(n, m);
+  const size_t smem = deposit_P_smem_bytes(n, cap);
+  const float keep = 1.0f - rho;
+  const bool tb = tau_prec == ACO_BF16;
+#define ACO_DEP_P(PR)                                                                                              \
+  do {                                                                                                             \
+    if (tb)                                                                                                        \
+      deposit_P_lists_kernel<PR, true><<<n, kDepThreads, smem, st>>>(tau, n, ld, nbr, c, m, keep, dep, cap, H,     \
+                                                                     alpha, inv_gamma_dev, it_dev, n_sched, P,    \
+                                                                     lists, lcnt, lkey);                          \
+    else                                                                                                           \
+      deposit_P_lists_kernel<PR, false><<<n, kDepThreads, smem, st>>>(tau, n, ld, nbr, c, m, keep, dep, cap, H,    \
+                                                                      alpha, inv_gamma_dev, it_dev, n_sched, P,   \
+                                                                      lists, lcnt, lkey);                         \
+  } while (0)
+  switch (prec) {
+    case ACO_FP32:
+      ACO_DEP_P(ACO_FP32);
+      break;
+    case ACO_BF16:
+      ACO_DEP_P(ACO_BF16);
+      break;
+    case ACO_FP16:
+      ACO_DEP_P(ACO_FP16);
+      break;
+    default:
+      return set_error(ACO_ERR_ARG, "unknown precision %d", prec);
+  }
+#undef ACO_DEP_P
+  return check_launch("deposit_P_lists_kernel");
 }
 
 int launch_deposit(void* tau, int tau_prec, int n, int ld, const int32_t* nbr, const double* c, int m,

@@ -337,6 +337,7 @@ struct aco_solver {
   cudaGraphExec_t exec;
   bool graph_ok;
   bool use_graph;
+  bool P_cur;                  // M_p and its lists are those of the current tau and iteration
   bool profiling;
   cudaEvent_t ev[7];           // probes around the iteration's kernels
   unsigned char* stage;        // pinned host copy of best_tour .. err (aco_solver_best)
@@ -359,12 +360,24 @@ static int upload_schedule(aco_solver* s) {
   return ACO_OK;
 }
 
+// Every change of a solver's parameters or state drops its graph; M_p is
+// then no longer assumed current either.
 static void drop_graph(aco_solver* s) {
   if (s->exec) cudaGraphExecDestroy(s->exec);
   if (s->graph) cudaGraphDestroy(s->graph);
   s->exec = nullptr;
   s->graph = nullptr;
   s->graph_ok = false;
+  s->P_cur = false;
+}
+
+// With candidate lists and the deterministic deposit, an iteration's M_p and
+// lists are computed at the end of the iteration before it, by the fused
+// deposit (deposit_P_lists_kernel), which re-reads each tau row right after
+// writing it; the first iteration after creation or any change computes
+// them first (ensure_P).
+static bool fused_P(const aco_solver* s) {
+  return s->p.cand_lists != 0 && s->p.roulette != ACO_RW && s->p.deposit == ACO_DEPOSIT_DET;
 }
 
 // The launches of one iteration (a)-(d); the iteration number and AdaIR's
@@ -382,13 +395,16 @@ static int enqueue_iteration(aco_solver* s) {
   probe(0);
   const bool rw = p.roulette == ACO_RW;
   const bool lists = p.cand_lists != 0 && !rw;
+  const bool fused = fused_P(s);
   const float* sched = p.roulette == ACO_ADAIR ? s->sched : nullptr;
   // with lists: M_p and its lists in one pass (the probe between them then
-  // gives the list step 0 ms)
-  int rc = lists ? launch_build_P_lists(s->tau, p.tau_prec, s->H, n, s->ld, p.alpha, 1.0f, sched, s->it_dev, n_sched,
-                                        p.rho, p.prec, s->P_f, s->lists, s->lcnt, s->lkey, st)
-                 : launch_build_P(s->tau, p.tau_prec, s->H, n, s->ld, p.alpha, 1.0f, sched, s->it_dev, n_sched, p.prec,
-                                  s->P_f, st);
+  // gives the list step 0 ms); fused: computed by the iteration before
+  int rc = ACO_OK;
+  if (!fused)
+    rc = lists ? launch_build_P_lists(s->tau, p.tau_prec, s->H, n, s->ld, p.alpha, 1.0f, sched, s->it_dev, n_sched,
+                                      p.rho, p.prec, s->P_f, s->lists, s->lcnt, s->lkey, st)
+               : launch_build_P(s->tau, p.tau_prec, s->H, n, s->ld, p.alpha, 1.0f, sched, s->it_dev, n_sched, p.prec,
+                                s->P_f, st);
   if (rc) return rc;
   probe(1);
   probe(2);
@@ -408,12 +424,29 @@ static int enqueue_iteration(aco_solver* s) {
                    det ? s->dep : nullptr, s->err, st);
   if (rc) return rc;
   probe(5);
-  if (det)
+  if (fused)  // the deposit, then the next iteration's M_p and lists
+    rc = launch_deposit_P_lists(s->tau, p.tau_prec, n, s->ld, s->nbr, s->c, m, p.rho, s->dep, s->H, p.alpha, sched,
+                                s->it_dev, n_sched, p.prec, s->P_f, s->lists, s->lcnt, s->lkey, st);
+  else if (det)
     rc = launch_deposit(s->tau, p.tau_prec, n, s->ld, s->nbr, s->c, m, p.rho, s->dep, s->err, st);
   else
     rc = launch_deposit_atomic(s->tau, n, s->ld, s->tours, s->c, m, p.rho, st);
   if (rc) return rc;
   probe(6);
+  return ACO_OK;
+}
+
+// M_p and its lists for the current tau and iteration, when the fused
+// deposit did not leave them (fused mode only; queued on the solver's stream).
+static int ensure_P(aco_solver* s) {
+  if (!fused_P(s) || s->P_cur) return ACO_OK;
+  const aco_params& p = s->p;
+  const int n_sched = std::min(p.gamma_T + 1, kSchedCap);
+  const float* sched = p.roulette == ACO_ADAIR ? s->sched : nullptr;
+  const int rc = launch_build_P_lists(s->tau, p.tau_prec, s->H, p.n, s->ld, p.alpha, 1.0f, sched, s->it_dev, n_sched,
+                                      p.rho, p.prec, s->P_f, s->lists, s->lcnt, s->lkey, s->stream);
+  if (rc) return rc;
+  s->P_cur = true;
   return ACO_OK;
 }
 
@@ -621,9 +654,12 @@ int aco_solver_iterate(aco_solver* s, int k) {
         int rc = build_graph(s);
         if (rc) return rc;
       }
+      int rc = ensure_P(s);
+      if (rc) return rc;
       ACO_CUDA_TRY(cudaGraphLaunch(s->exec, s->stream));
     } else {
-      int rc = enqueue_iteration(s);
+      int rc = ensure_P(s);
+      if (!rc) rc = enqueue_iteration(s);
       if (rc) return rc;
     }
     s->it += 1;

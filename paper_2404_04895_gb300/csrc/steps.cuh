@@ -29,11 +29,13 @@ __device__ __forceinline__ float p_entry(float tau, float h, int i, int j, int n
 }
 
 // Columns 4q .. 4q+3 of a tau row stored in fp32 (TB false) or bfloat16 (TB
-// true), widened to fp32 (exact).
-template <bool TB>
+// true), widened to fp32 (exact).  COH: the row was written earlier by the
+// same kernel, so it is read through the L2 (not the read-only path).
+template <bool TB, bool COH = false>
 __device__ __forceinline__ float4 load_tau4(const void* __restrict__ row, int q) {
-  if (!TB) return __ldg(reinterpret_cast<const float4*>(row) + q);
-  const uint2 u = __ldg(reinterpret_cast<const uint2*>(row) + q);
+  if (!TB)
+    return COH ? __ldcg(reinterpret_cast<const float4*>(row) + q) : __ldg(reinterpret_cast<const float4*>(row) + q);
+  const uint2 u = COH ? __ldcg(reinterpret_cast<const uint2*>(row) + q) : __ldg(reinterpret_cast<const uint2*>(row) + q);
   return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
                      __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
 }
@@ -949,9 +951,10 @@ __device__ __forceinline__ void build_list_row(const void* __restrict__ P_row, i
 // none) falls back to build_list_row's radix select on the stored row.  The
 // result is the same either way; the guess only decides the cost.
 // guess: 0xFFFFFFFF for none.  scratch: kListScratchWords shared words plus
-// `red` (32 floats) for the FP16 row maximum.
+// `red` (32 floats) for the FP16 row maximum.  COH: the tau row was written
+// earlier by the same kernel (load_tau4).
 // ---------------------------------------------------------------------------
-template <int PREC, bool TB = false>
+template <int PREC, bool TB = false, bool COH = false>
 __device__ __forceinline__ void build_P_lists_row(const void* __restrict__ tau_row, const float* __restrict__ H_row,
                                                   int n, int ld, int i, int alpha, float inv_gamma,
                                                   void* __restrict__ P_row, uint2* __restrict__ list,
@@ -967,7 +970,7 @@ __device__ __forceinline__ void build_P_lists_row(const void* __restrict__ tau_r
   if (PREC == ACO_FP16) {
     float mx = 0.0f;
     for (int q = tid; q < nq; q += nt) {
-      const float4 a = load_tau4<TB>(tau_row, q), b = __ldg(h4 + q);
+      const float4 a = load_tau4<TB, COH>(tau_row, q), b = __ldg(h4 + q);
       const int j = 4 * q;
       mx = fmaxf(mx, p_entry(a.x, b.x, i, j, n, alpha, inv_gamma));
       mx = fmaxf(mx, p_entry(a.y, b.y, i, j + 1, n, alpha, inv_gamma));
@@ -996,7 +999,7 @@ __device__ __forceinline__ void build_P_lists_row(const void* __restrict__ tau_r
     }
   };
   for (int q = tid; q < nq; q += nt) {
-    const float4 a = load_tau4<TB>(tau_row, q), b = __ldg(h4 + q);
+    const float4 a = load_tau4<TB, COH>(tau_row, q), b = __ldg(h4 + q);
     const int j = 4 * q;
     const float x0 = p_entry(a.x, b.x, i, j, n, alpha, inv_gamma);
     const float x1 = p_entry(a.y, b.y, i, j + 1, n, alpha, inv_gamma);
