@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) batch_tour_length_kernel(const InstDev* _
   const int i = find_instance(ant_off, count, item);
   const InstDev& I = insts[i];
   const int k = item - __ldg(ant_off + i);
-  tour_length_exact<1>(I.D, I.n, I.tours + (size_t)k * I.n, k, I.Q, I.L, I.c,
+  tour_length_exact<1, false, true>(I.D, I.n, I.tours + (size_t)k * I.n, k, I.Q, I.L, I.c,
                        I.nbr ? static_cast<void*>(reinterpret_cast<int2*>(I.nbr) + k) : nullptr, I.m, 0,
                        sacc + wid * (kLenDigits + 1));
 }

@@ -17,7 +17,7 @@ struct InstDev {
   float* tau;                     // n x ld, fp32 (tau_bf16: bf16 bit patterns, n x ld x 2 bytes)
   int tau_bf16;                   // M_tau stored in bfloat16
   void* P;                        // M_p, n x ld at the batch precision
-  const double* D;                // n x n
+  const double* D;                // strictly upper triangle, tri_index
   int32_t* tours;                 // m x n
   double* L;                      // m
   double* c;                      // m

@@ -103,7 +103,9 @@ int prepare_construct_f16();
 int prepare_deposit();
 int prepare_kernels();  // once per process: shared-memory opt-ins (not during capture)
 
-int launch_heuristic(const float* xy, int n, int beta, double* D, float* H, int ld,
+// packed: D is the strictly upper triangle (tri_index; the solvers' and
+// batches' own layout), else n x n (the step-level calls' layout)
+int launch_heuristic(const float* xy, int n, int beta, double* D, float* H, int ld, bool packed,
                      cudaStream_t st);
 int launch_fill(float* a, int n, int ld, float v, cudaStream_t st);
 // tau stored in fp32 (tau_prec ACO_FP32) or bfloat16 (ACO_BF16), leading dimension ld
@@ -124,7 +126,7 @@ int launch_deposit_P_lists(void* tau, int tau_prec, int n, int ld, const int32_t
                            uint32_t* lkey, cudaStream_t st);
 int prepare_tour_length();
 int launch_tour_length(const double* D, int n, const int32_t* tours, int m, float Q,
-                       double* L, double* c, int32_t* nbr, cudaStream_t st);
+                       double* L, double* c, int32_t* nbr, bool packed, cudaStream_t st);
 // best also keeps only the topk shortest paths' weights in c (c non-null,
 // 0 < topk < m) and derives the deposit weights' scale into *dep (non-null)
 int launch_best(const double* L, const int32_t* tours, int n, int m, int32_t* best_tour,

@@ -24,8 +24,11 @@ namespace aco {
 // (I, J) with I <= J, computes each entry once (1/d by the correctly rounded
 // reciprocal, the same value as a correctly rounded 1.0 / d), writes it
 // row-wise at (i, j) and, through shared memory, row-wise at (j, i).
-// Grid (T, T), T = ceil(n / 32); blocks with I > J return at once.
+// PACKED: D is the strictly upper triangle (tri_index), written at (i, j),
+// i < j, only.  Grid (T, T), T = ceil(n / 32); blocks with I > J return at
+// once.
 // ---------------------------------------------------------------------------
+template <bool PACKED>
 __global__ void __launch_bounds__(256) heuristic_kernel(const float* __restrict__ xy, int n, int beta,
                                                         double* __restrict__ D, float* __restrict__ H, int ld) {
   __shared__ double sd[32][33];
@@ -49,7 +52,12 @@ __global__ void __launch_bounds__(256) heuristic_kernel(const float* __restrict_
       const double dy = __dsub_rn((double)xy[2 * i + 1], yj);
       d = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
       if (i != j) h = __double2float_rn(powi_f64(__drcp_rn(d > 1e-9 ? d : 1e-9), beta));
-      if (D) D[(size_t)i * n + j] = d;
+      if (D) {
+        if (!PACKED)
+          D[(size_t)i * n + j] = d;
+        else if (i < j)
+          D[tri_index(n, i, j)] = d;
+      }
       H[(size_t)i * ld + j] = h;
     }
     sd[r][tx] = d;
@@ -64,7 +72,7 @@ __global__ void __launch_bounds__(256) heuristic_kernel(const float* __restrict_
     const int r = ty + 8 * k;  // row 32J + r of the mirrored tile, column 32I + tx
     const int jr = 32 * J + r, ic = 32 * I + tx;
     if (jr < n && ic < n) {
-      if (D) D[(size_t)jr * n + ic] = sd[tx][r];
+      if (D && !PACKED) D[(size_t)jr * n + ic] = sd[tx][r];
       H[(size_t)jr * ld + ic] = sh[tx][r];
     }
   }
@@ -143,8 +151,9 @@ __global__ void __launch_bounds__(256, 6) build_P_lists_kernel(const void* __res
                               lists + (size_t)i * kListMax, lcnt + i, lkey + i, guess, scratch, red);
 }
 
-// One CTA of W warps per ant (W = 1: 8 ants per CTA, one warp each).
-template <int W>
+// One CTA of W warps per ant (W = 1: 8 ants per CTA, one warp each); PACKED
+// as tour_length_exact.
+template <int W, bool PACKED>
 __global__ void __launch_bounds__(256) tour_length_kernel(const double* __restrict__ D, int n,
                                                           const int32_t* __restrict__ tours,
                                                           int m, float Q, double* __restrict__ L,
@@ -154,7 +163,7 @@ __global__ void __launch_bounds__(256) tour_length_kernel(const double* __restri
   const int wid = (int)(threadIdx.x >> 5);
   const int k = W == 1 ? blockIdx.x * (blockDim.x >> 5) + wid : blockIdx.x;
   if (k >= m) return;
-  tour_length_exact<W>(D, n, tours + (size_t)k * n, k, Q, L, c,
+  tour_length_exact<W, false, PACKED>(D, n, tours + (size_t)k * n, k, Q, L, c,
                        nbr ? static_cast<void*>(reinterpret_cast<int2*>(nbr) + k) : nullptr, m, W == 1 ? 0 : wid,
                        sacc + (W == 1 ? wid * (kLenDigits + 1) : 0));
 }
@@ -167,7 +176,7 @@ __global__ void __launch_bounds__(256) tour_length_kernel(const double* __restri
 // 2 blockIdx.x and 2 blockIdx.x + 1; m even (rows of nbr 16-byte aligned),
 // nbr 16-byte aligned,
 // n <= kTourPairMaxN.  Dynamic shared memory: 8 n bytes.
-template <int W>
+template <int W, bool PACKED>
 __global__ void __launch_bounds__(64 * W) tour_length_pair_kernel(const double* __restrict__ D, int n,
                                                                   const int32_t* __restrict__ tours,
                                                                   int m, float Q, double* __restrict__ L,
@@ -180,7 +189,7 @@ __global__ void __launch_bounds__(64 * W) tour_length_pair_kernel(const double* 
   const int k = 2 * (int)blockIdx.x + a;
   for (int q = threadIdx.x; q < n; q += blockDim.x) stage[q] = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
   __syncthreads();
-  tour_length_exact<W, true>(D, n, tours + (size_t)k * n, k, Q, L, c, reinterpret_cast<uint32_t*>(stage) + a, 2,
+  tour_length_exact<W, true, PACKED>(D, n, tours + (size_t)k * n, k, Q, L, c, reinterpret_cast<uint32_t*>(stage) + a, 2,
                              wid - a * W, sacc + a * (kLenDigits + 1));
   __syncthreads();
   auto wide = [](uint32_t h) { return h == 0xFFFFu ? -1 : (int)h; };
@@ -320,11 +329,14 @@ static int check_launch(const char* what) {
   return e == cudaSuccess ? ACO_OK : cuda_error(e, what);
 }
 
-int launch_heuristic(const float* xy, int n, int beta, double* D, float* H, int ld,
+int launch_heuristic(const float* xy, int n, int beta, double* D, float* H, int ld, bool packed,
                      cudaStream_t st) {
   const int T = (n + 31) / 32;
   dim3 grid(T, T);
-  heuristic_kernel<<<grid, 256, 0, st>>>(xy, n, beta, D, H, ld);
+  if (packed)
+    heuristic_kernel<true><<<grid, 256, 0, st>>>(xy, n, beta, D, H, ld);
+  else
+    heuristic_kernel<false><<<grid, 256, 0, st>>>(xy, n, beta, D, H, ld);
   return check_launch("heuristic_kernel");
 }
 
@@ -433,30 +445,40 @@ constexpr int kTourPairW = 8;
 constexpr int kTourPairMaxN = 7168;
 
 int prepare_tour_length() {
-  ACO_CUDA_TRY(cudaFuncSetAttribute(tour_length_pair_kernel<kTourPairW>,
+  ACO_CUDA_TRY(cudaFuncSetAttribute(tour_length_pair_kernel<kTourPairW, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kTourPairMaxN * 8));
+  ACO_CUDA_TRY(cudaFuncSetAttribute(tour_length_pair_kernel<kTourPairW, true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kTourPairMaxN * 8));
   return ACO_OK;
 }
 
 int launch_tour_length(const double* D, int n, const int32_t* tours, int m, float Q, double* L,
-                       double* c, int32_t* nbr, cudaStream_t st) {
+                       double* c, int32_t* nbr, bool packed, cudaStream_t st) {
   const int W = tour_length_warps(n);
-  // pairs write 16-byte halves of nbr's rows: m even keeps every row aligned
-  if (nbr && W == 4 && n <= kTourPairMaxN && m % 2 == 0 && aligned16(nbr)) {
-    tour_length_pair_kernel<kTourPairW><<<m / 2, 64 * kTourPairW, (size_t)n * 8, st>>>(D, n, tours, m, Q, L, c,
-                                                                                       nbr);
-    return check_launch("tour_length_pair_kernel");
-  }
-  switch (W) {
-    case 4:
-      tour_length_kernel<4><<<m, 128, 0, st>>>(D, n, tours, m, Q, L, c, nbr);
-      break;
-    case 2:
-      tour_length_kernel<2><<<m, 64, 0, st>>>(D, n, tours, m, Q, L, c, nbr);
-      break;
-    default:
-      tour_length_kernel<1><<<(m + 7) / 8, 256, 0, st>>>(D, n, tours, m, Q, L, c, nbr);
-  }
+#define ACO_TOUR_LENGTH(PK)                                                                                        \
+  do {                                                                                                             \
+    /* pairs write 16-byte halves of nbr's rows: m even keeps every row aligned */                                \
+    if (nbr && W == 4 && n <= kTourPairMaxN && m % 2 == 0 && aligned16(nbr)) {                                     \
+      tour_length_pair_kernel<kTourPairW, PK><<<m / 2, 64 * kTourPairW, (size_t)n * 8, st>>>(D, n, tours, m, Q, L, \
+                                                                                             c, nbr);              \
+      return check_launch("tour_length_pair_kernel");                                                              \
+    }                                                                                                              \
+    switch (W) {                                                                                                   \
+      case 4:                                                                                                      \
+        tour_length_kernel<4, PK><<<m, 128, 0, st>>>(D, n, tours, m, Q, L, c, nbr);                                \
+        break;                                                                                                     \
+      case 2:                                                                                                      \
+        tour_length_kernel<2, PK><<<m, 64, 0, st>>>(D, n, tours, m, Q, L, c, nbr);                                 \
+        break;                                                                                                     \
+      default:                                                                                                     \
+        tour_length_kernel<1, PK><<<(m + 7) / 8, 256, 0, st>>>(D, n, tours, m, Q, L, c, nbr);                      \
+    }                                                                                                              \
+  } while (0)
+  if (packed)
+    ACO_TOUR_LENGTH(true);
+  else
+    ACO_TOUR_LENGTH(false);
+#undef ACO_TOUR_LENGTH
   return check_launch("tour_length_kernel");
 }
 

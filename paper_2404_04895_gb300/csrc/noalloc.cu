@@ -81,7 +81,7 @@ extern "C" int aco_op_deposit_tours_noalloc(float* tau_dev, int n, int ld, const
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // -1 everywhere: an entry no tour writes is skipped by the deposit
   ACO_CUDA_TRY(cudaMemsetAsync(nbr, 0xFF, nbr_bytes, st));
-  rc = launch_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c, nbr, st);
+  rc = launch_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c, nbr, false, st);
   if (rc) return rc;
   return launch_deposit(tau_dev, ACO_FP32, n, ld, nbr, c, m, rho, nullptr, err_dev, st);
 }

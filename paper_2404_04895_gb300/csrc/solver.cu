@@ -227,7 +227,7 @@ static Layout layout_of(int n, int m) {
     return at;
   };
   L.coords = take((size_t)n * 2 * 4);
-  L.D = take((size_t)n * n * 8);
+  L.D = take((size_t)n * (n - 1) / 2 * 8);  // strictly upper triangle (tri_index)
   L.H = take((size_t)n * ld * 4);
   L.tau = take((size_t)n * ld * 4);
   L.P = take((size_t)n * ld * 4);
@@ -293,7 +293,7 @@ int instance_bind(const aco_params& p, unsigned char* ws, InstDev* d, cudaStream
   x.lcnt = reinterpret_cast<int*>(ws + L.lcnt);
   x.lkey = reinterpret_cast<uint32_t*>(ws + L.lkey);
   ACO_CUDA_TRY(cudaMemcpyAsync(coords, coords_host, sizeof(float) * 2 * p.n, cudaMemcpyHostToDevice, st));
-  rc = launch_heuristic(coords, p.n, p.beta, const_cast<double*>(x.D), const_cast<float*>(x.H), ld, st);
+  rc = launch_heuristic(coords, p.n, p.beta, const_cast<double*>(x.D), const_cast<float*>(x.H), ld, true, st);
   if (!rc) rc = launch_fill_tau(x.tau, p.tau_prec, p.n, ld, p.tau0, st);
   if (rc) return rc;
   const double inf = INFINITY;
@@ -417,7 +417,7 @@ static int enqueue_iteration(aco_solver* s) {
   if (rc) return rc;
   probe(3);
   const bool det = p.deposit == ACO_DEPOSIT_DET;
-  rc = launch_tour_length(s->D, n, s->tours, m, p.Q, s->L, s->c, det ? s->nbr : nullptr, st);
+  rc = launch_tour_length(s->D, n, s->tours, m, p.Q, s->L, s->c, det ? s->nbr : nullptr, true, st);
   if (rc) return rc;
   probe(4);
   rc = launch_best(s->L, s->tours, n, m, s->best_tour, s->best_len, s->it_dev, s->c, p.topk,
@@ -612,7 +612,7 @@ int aco_create(aco_solver** out, const float* coords_host, const aco_params* p, 
   cudaStream_t st = s->stream;
   if (cudaMemcpyAsync(s->coords, coords_host, sizeof(float) * 2 * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return fail(cuda_error(cudaGetLastError(), "copy coords"));
-  rc = launch_heuristic(s->coords, n, p->beta, s->D, s->H, s->ld, st);
+  rc = launch_heuristic(s->coords, n, p->beta, s->D, s->H, s->ld, true, st);
   if (!rc) rc = launch_fill_tau(s->tau, p->tau_prec, n, s->ld, p->tau0, st);
   if (rc) return fail(rc);
   const double inf = INFINITY;
@@ -1134,7 +1134,7 @@ int aco_op_heuristic(const float* coords_dev, int n, int beta, double* D_dev, fl
   if (rc) return rc;
   if (!coords_dev) return set_error(ACO_ERR_ARG, "coords is NULL");
   if (beta < 0 || beta > 8) return set_error(ACO_ERR_UNSUPPORTED, "beta must be an integer in [0, 8]");
-  return launch_heuristic(coords_dev, n, beta, D_dev, H_dev, ld, static_cast<cudaStream_t>(stream));
+  return launch_heuristic(coords_dev, n, beta, D_dev, H_dev, ld, false, static_cast<cudaStream_t>(stream));
 }
 
 int aco_op_fill(float* dev, int n, int ld, float value, void* stream) {
@@ -1241,7 +1241,8 @@ int aco_op_tour_length(const double* D_dev, int n, const int32_t* tours_dev, int
   if (nbr_dev && ((uintptr_t)nbr_dev & 7)) return set_error(ACO_ERR_ARG, "nbr must be 8-byte aligned");
   const int rc = prepare_kernels();
   if (rc) return rc;
-  return launch_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c_dev, nbr_dev, static_cast<cudaStream_t>(stream));
+  return launch_tour_length(D_dev, n, tours_dev, m, Q, L_dev, c_dev, nbr_dev, false,
+                            static_cast<cudaStream_t>(stream));
 }
 
 int aco_op_best(const double* L_dev, const int32_t* tours_dev, int n, int m, int32_t* best_tour_dev,

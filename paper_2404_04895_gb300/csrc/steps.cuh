@@ -114,8 +114,9 @@ __device__ __forceinline__ void build_P_row(const void* __restrict__ tau_row,
 // word (pred | succ << 16) of a shared staging area.  sacc: kLenDigits + 1
 // shared words for this ant (one area per warp when W == 1, per W-warp group
 // when W > 1).  W > 1: every warp of the CTA calls this (its block barriers).
+// PACKED: D holds the strictly upper triangle (tri_index), else all n x n.
 // ---------------------------------------------------------------------------
-template <int W, bool PACK16 = false>
+template <int W, bool PACK16 = false, bool PACKED = false>
 __device__ __forceinline__ void tour_length_exact(const double* __restrict__ D, int n,
                                                   const int32_t* __restrict__ p, int k,
                                                   float Q, double* __restrict__ L,
@@ -143,7 +144,11 @@ __device__ __forceinline__ void tour_length_exact(const double* __restrict__ D, 
         // tours come from the construction kernel; an entry out of range
         // (only after a failed construction, which the host reports) is skipped
         if ((unsigned)cur < (unsigned)n && (unsigned)nx < (unsigned)n) {
-          db[u] = (uint64_t)__double_as_longlong(__ldg(D + (size_t)cur * n + nx));
+          if (!PACKED)
+            db[u] = (uint64_t)__double_as_longlong(__ldg(D + (size_t)cur * n + nx));
+          else if (cur != nx)  // d(a, a) = 0 (only a repeated city gives such an edge)
+            db[u] = (uint64_t)__double_as_longlong(
+                __ldg(D + (cur < nx ? tri_index(n, cur, nx) : tri_index(n, nx, cur))));
           if (nb) {
             const int pv = __ldg(p + (t > 0 ? t - 1 : n - 1));
             if (PACK16)
