@@ -87,13 +87,6 @@ __device__ __forceinline__ int start_city(uint2 key, uint32_t it, uint32_t k, in
   return (int)(((uint64_t)w.x * (uint64_t)(uint32_t)n) >> 32);
 }
 
-// Entry (a, b), a < b, of the strictly upper triangle of an n x n symmetric
-// matrix stored row by row (row a holds columns a + 1 .. n - 1): the solvers'
-// distance matrix, n (n - 1) / 2 fp64 values.  a (2n - a - 1) is always even.
-__host__ __device__ __forceinline__ size_t tri_index(int n, int a, int b) {
-  return (size_t)a * (size_t)(2 * n - a - 1) / 2 + (size_t)(b - a - 1);
-}
-
 // Integer power by left-to-right multiplication (a >= 0), each product rounded.
 __device__ __forceinline__ float powi_f32(float x, int a) {
   if (a == 0) return 1.0f;

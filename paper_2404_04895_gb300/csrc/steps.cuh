@@ -28,6 +28,13 @@ __device__ __forceinline__ float p_entry(float tau, float h, int i, int j, int n
   return x;
 }
 
+// Entry (a, b), a < b, of the strictly upper triangle of an n x n symmetric
+// matrix stored row by row (row a holds columns a + 1 .. n - 1): the solvers'
+// distance matrix, n (n - 1) / 2 fp64 values.  a (2n - a - 1) is always even.
+__host__ __device__ __forceinline__ size_t tri_index(int n, int a, int b) {
+  return (size_t)a * (size_t)(2 * n - a - 1) / 2 + (size_t)(b - a - 1);
+}
+
 // Columns 4q .. 4q+3 of a tau row stored in fp32 (TB false) or bfloat16 (TB
 // true), widened to fp32 (exact).  COH: the row was written earlier by the
 // same kernel, so it is read through the L2 (not the read-only path).
